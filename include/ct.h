@@ -1,0 +1,193 @@
+/*
+ * ct.h -- C ABI of the GB300 sparse-operator CT reconstruction library (libct.so).
+ *
+ * Method: R. C. Barnard and R. Archibald, "Accelerating optimization-based
+ * computed tomography via sparse matrix approximations" (arXiv 1705.07497).
+ * The library evaluates the parallel-beam Radon transform restricted to the
+ * measured angles, A = M R (Sec. 1, Eq. objmin), and its adjoint A^T as
+ * precomputed sparse matrices (Sec. 3: geometry-dependent matrices are built
+ * once, offline, and reused), and applies them inside conjugate-gradient
+ * solves of
+ *      (c_id I + c_ata A^T A + c_grad grad^T grad) u = rhs
+ * which covers Eq. KKT (p = 2), Eq. PD_resolve (Chambolle-Pock resolvent)
+ * and Eq. SB_solve (split Bregman), nested in anisotropic-TV split Bregman
+ * (Sec. 4).  The sparse surrogate T of Sec. 3.2 (Eq. def_sparse_surr,
+ * Eq. surr_SBupd) can replace A^T A.
+ *
+ * Conventions shared by every call
+ *   image      N x N pixels of side 1, row-major: pixel (i, j) is element
+ *              p = i*N + j and covers x in [j-N/2, j-N/2+1], y in [i-N/2, i-N/2+1].
+ *   angles     theta_k = k*pi/n_angles_total, k = 0 .. n_angles_total-1; the row
+ *              selector M keeps k % keep_every == 0 (kept angle k' = k/keep_every).
+ *   detector   n_bins bins of width 1; bin b sits at s_b = b - (n_bins-1)/2.
+ *   ray (k,b)  the line x cos(theta_k) + y sin(theta_k) = s_b; row q = k'*n_bins + b.
+ *   A entries  exact intersection length of ray q with pixel p (Siddon
+ *              lengths, computed in FP64 from a closed form); a ray lying on a
+ *              pixel edge gives half its length to each of the two pixels;
+ *              theta exactly 0 or pi/2 use exact direction cosines; lengths
+ *              below 1e-12 are dropped.
+ *   batches    a batch of B images is laid out [N*N][B] and a batch of B
+ *              sinograms [rows][B]: the slice index is innermost.
+ *   pointers   vector arguments are plain pointers to float32 data, owned by
+ *              the caller.  Device pointers are used in place and the call is
+ *              asynchronous on `cuda_stream` (a cudaStream_t; NULL = legacy
+ *              default stream).  Host pointers (pageable or pinned) are
+ *              staged through library-owned device buffers and the call
+ *              returns after the results have been copied back (synchronous).
+ *              All vector arguments of one call must be of the same kind.
+ *   errors     every int-returning call returns CT_OK (0) or a negative
+ *              CT_ERR_* code; nothing aborts or exits.  ct_last_error()
+ *              returns a per-thread message for the last failure.
+ *   threads    a matrix handle owns workspace used by ct_cg_solve and
+ *              ct_split_bregman; concurrent solver calls on one handle must be
+ *              serialised by the caller (same stream, or external ordering).
+ */
+#ifndef CT_H
+#define CT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    CT_OK = 0,
+    CT_ERR_ARG = -1,         /* invalid argument, size or pointer               */
+    CT_ERR_CUDA = -2,        /* a CUDA runtime call failed                       */
+    CT_ERR_OOM = -3,         /* device or host allocation failed                 */
+    CT_ERR_BREAKDOWN = -4,   /* CG saw p^T Op p <= 0 with a nonzero residual     */
+    CT_ERR_NONFINITE = -5,   /* NaN or Inf met in a residual, dot or update      */
+    CT_ERR_TIMEOUT = -6,     /* a bounded device-side wait expired               */
+    CT_ERR_UNSUPPORTED = -7  /* option not available for this matrix / build     */
+};
+
+/* Matrix storage flags for ct_build_matrix (Sec. 3: precomputed sparse form). */
+enum {
+    CT_VAL_FP32 = 0,          /* FP32 values, int32 column indices (CSR)         */
+    CT_VAL_FP16_ROWSCALE = 1, /* A = diag(s) Q: Q in FP16 (|Q| <= 1), s FP32 per
+                                 row; A^T is applied as Q^T (s .* y), so the
+                                 quantised normal operator stays symmetric     */
+    CT_KEEP_FP32_COPY = 4     /* with FP16 storage, also keep FP32 values for
+                                 residual refreshes (ct_cg_params.refresh_every) */
+};
+
+typedef struct {
+    int32_t n;              /* image size N (N x N pixels of side 1)              */
+    int32_t n_angles_total; /* theta_k = k*pi/n_angles_total                      */
+    int32_t keep_every;     /* M keeps k % keep_every == 0 (Sec. 1)               */
+    int32_t n_bins;         /* detector bins of width 1, centred                  */
+} ct_geometry;
+
+typedef struct ct_matrix *ct_matrix_t; /* opaque, library-owned, device-resident */
+
+/* Builds A = M R and A^T for geometry *g on the current CUDA device, as
+ * row-sorted CSR (rows padded so that each starts on a 16-byte boundary; the
+ * padding entries hold value 0).  Both matrices are computed from the same
+ * closed-form chord length, so A^T holds exactly the values of A.
+ * Errors: CT_ERR_ARG (n <= 0, n*n >= 2^31, counts <= 0, NULL out),
+ * CT_ERR_OOM, CT_ERR_CUDA.  *out receives the handle (NULL on failure). */
+int ct_build_matrix(const ct_geometry *g, uint32_t flags, ct_matrix_t *out);
+
+/* rows = n_kept*n_bins, cols = N*N, nnz = number of stored nonzeros (no
+ * padding).  Any output pointer may be NULL. */
+int ct_matrix_info(ct_matrix_t A, int64_t *rows, int64_t *cols, int64_t *nnz);
+
+/* Frees the handle, its matrices, workspace and captured graphs (NULL is a no-op). */
+void ct_destroy_matrix(ct_matrix_t A);
+
+/* y[rows][batch] = A x[N*N][batch]  (Sec. 1: the data term's M R).
+ * With FP16 storage: y = s .* (Q x).  batch >= 1. */
+int ct_forward(ct_matrix_t A, const float *x, float *y, int32_t batch, void *cuda_stream);
+
+/* x[N*N][batch] = A^T y[rows][batch]  (the adjoint R* M* of Eq. KKT).
+ * With FP16 storage: x = Q^T (s .* y). */
+int ct_adjoint(ct_matrix_t A, const float *y, float *x, int32_t batch, void *cuda_stream);
+
+typedef struct {
+    double c_id, c_ata, c_grad; /* Op = c_id I + c_ata A^T A (or T) + c_grad grad^T grad.
+                                   SB (Eq. SB_solve): (0, alpha, lambda);
+                                   CP resolvent (Eq. PD_resolve): (1, tau*alpha, 0);
+                                   p = 2 normal equations (Eq. KKT): (0, alpha, 1). */
+    int32_t max_iters;          /* CG steps (Sec. 4: a small fixed count)              */
+    double rel_tol;             /* also stop once ||r|| <= rel_tol ||rhs||; 0 = off    */
+    int32_t surrogate_r;        /* 0: exact A^T A; > 0: surrogate T of radius r (Sec. 3.2) */
+    int32_t refresh_every;      /* FP16 storage: recompute r = rhs - Op(u) with the FP32
+                                   matrices every k steps (needs CT_KEEP_FP32_COPY); 0 = off */
+    int32_t surrogate_square;   /* 0: disc window |d|_2 <= r; 1: square |d|_inf <= r */
+} ct_cg_params;
+
+typedef struct {
+    int32_t iters;        /* CG steps taken (max over the batch)                   */
+    double final_rel_res; /* ||r||/||rhs|| of the recursively updated residual
+                             (max over the batch)                                  */
+    int32_t status;       /* CT_OK, CT_ERR_BREAKDOWN or CT_ERR_NONFINITE           */
+} ct_cg_stats;
+
+/* Solves Op u = rhs per slice with conjugate gradients (Sec. 2: no closed-form
+ * solution exists), warm-started from u.  rhs, u: [N*N][batch]; u is
+ * overwritten with the iterate.  FP32 vectors, FP64 dot products.  stats
+ * (host pointer) may be NULL; when given, the call synchronises the stream
+ * to fill it and returns its status.  Without stats a breakdown is reported
+ * only through a later call's status. */
+int ct_cg_solve(ct_matrix_t A, const ct_cg_params *params, const float *rhs, float *u,
+                int32_t batch, ct_cg_stats *stats, void *cuda_stream);
+
+typedef struct {
+    double alpha, lambda;   /* Eq. objmin's alpha; split-Bregman penalty lambda     */
+    int32_t outer_iters;    /* Bregman updates                                       */
+    int32_t inner_cg_iters; /* CG steps per update (warm-started)                    */
+    double stop_rel_update; /* Sec. 4: stop once ||u^{k+1}-u^k||_1 < tol * first; 0 = off */
+    int32_t surrogate_r;    /* 0: exact A^T A; > 0: surrogate T (Eq. surr_SBupd)    */
+    int32_t refresh_every;  /* as in ct_cg_params                                    */
+    int32_t surrogate_square;
+} ct_sb_params;
+
+typedef struct {
+    int32_t outer_done;     /* Bregman updates performed (min over the batch)       */
+    double first_update_l1; /* ||u^1 - u^0||_1 (slice 0)                            */
+    double last_update_l1;  /* ||u^K - u^{K-1}||_1 (slice 0)                        */
+    int32_t status;
+} ct_sb_stats;
+
+/* Anisotropic-TV split Bregman for min alpha/2 ||A u - f||^2 + ||grad u||_1
+ * (Eq. objmin with p = 1, K = grad; Sec. 4), one independent problem per slice:
+ *   rhs = alpha A^T f + lambda grad^T (d - b)
+ *   u   = CG_{inner}(alpha A^T A (or T) + lambda grad^T grad, rhs, warm start u)
+ *   d   = shrink(grad u + b, 1/lambda);  b = b + grad u - d
+ * with d = b = 0 at the start.  f: [rows][batch] measured data (already
+ * restricted by M); u: [N*N][batch], in = initial guess, out = reconstruction.
+ * stats may be NULL (then the call does not synchronise). */
+int ct_split_bregman(ct_matrix_t A, const ct_sb_params *params, const float *f, float *u,
+                     int32_t batch, ct_sb_stats *stats, void *cuda_stream);
+
+/* Copies A (which = 0) or A^T (which = 1) to host memory as unpadded CSR:
+ * row_ptr[rows+1] (int64), cols[nnz] (int32), vals[nnz] (FP32; with FP16
+ * storage, the dequantised s_q * Q_qp).  Pass NULL arrays to query sizes
+ * through ct_matrix_info.  Synchronous. */
+int ct_matrix_export(ct_matrix_t A, int32_t which, int64_t *row_ptr, int32_t *cols, float *vals);
+
+/* Copies the FP16 storage form to host memory: q_bits[nnz] (IEEE binary16
+ * bit patterns of Q in the row order of A) and scale[rows] (s, FP32).
+ * CT_ERR_UNSUPPORTED without CT_VAL_FP16_ROWSCALE.  Synchronous. */
+int ct_matrix_export_fp16(ct_matrix_t A, uint16_t *q_bits, float *scale);
+
+/* Surrogate stencil of Sec. 3.2: s(d) = (A^T A e_c)[c + d] for c = (N/2, N/2)
+ * (0-based) and offsets d = (di, dj) in the window (disc |d|_2 <= r, or square
+ * when square != 0), averaged with s(-d) so that T is symmetric; computed in
+ * FP64.  Writes up to `capacity` taps (di[], dj[], val[], host arrays) and the
+ * number of taps to *count.  Synchronous. */
+int ct_surrogate_stencil(ct_matrix_t A, int32_t r, int32_t square, int32_t capacity,
+                         int32_t *di, int32_t *dj, double *val, int32_t *count);
+
+/* Short description of a status code. */
+const char *ct_status_string(int status);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *ct_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CT_H */

@@ -1,0 +1,53 @@
+"""Builds and loads the oracle's C part (``siddon.c``) with gcc.
+
+Test infrastructure only (see the package docstring).
+"""
+
+import ctypes
+import fcntl
+import os
+import subprocess
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "siddon.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_OUT_DIR, "liboracle_siddon.so")
+
+_lib = None
+
+
+def build(force=False):
+    """Compiles ``siddon.c`` into ``_build/liboracle_siddon.so`` (plain gcc)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    with open(os.path.join(_OUT_DIR, ".lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        fresh = os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)
+        if force or not fresh:
+            tmp = _LIB + ".tmp%d" % os.getpid()
+            subprocess.check_call(
+                ["gcc", "-O2", "-std=c11", "-Wall", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+            )
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        L.oracle_siddon_count.restype = ctypes.c_int64
+        L.oracle_siddon_count.argtypes = [ctypes.c_int] * 4 + [i64p]
+        L.oracle_siddon_fill.restype = ctypes.c_int
+        L.oracle_siddon_fill.argtypes = [ctypes.c_int] * 4 + [
+            i64p,
+            ctypes.POINTER(ctypes.c_int32),
+            ctypes.POINTER(ctypes.c_double),
+        ]
+        L.oracle_directions.restype = None
+        L.oracle_directions.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.POINTER(ctypes.c_double)] * 2
+        L.oracle_num_kept.restype = ctypes.c_int
+        L.oracle_num_kept.argtypes = [ctypes.c_int, ctypes.c_int]
+        _lib = L
+    return _lib

@@ -1,0 +1,229 @@
+"""Pins of the FP64 solver oracle: gradient, CG, split Bregman, surrogate T.
+
+Each pin checks the oracle against an independent construction or a
+mathematical fact: Kronecker-product difference matrices, a dense Cholesky
+solve, the Krylov-subspace optimality of CG iterates, the 1-D TV optimality
+certificate, KKT conditions of the TV problem, and the sum-of-translates
+definition of T (Sec. 3.2, Eq. def_sparse_surr) against a library
+correlation.
+"""
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.signal as ssig
+import scipy.sparse as sp
+
+from oracle import radon, tv
+from paper_1705_07497_gb300 import inputs
+
+
+def _diff_matrix(n):
+    """1-D forward difference with a zero last row (Neumann)."""
+    D = sp.lil_matrix((n, n))
+    for j in range(n - 1):
+        D[j, j] = -1.0
+        D[j, j + 1] = 1.0
+    return D.tocsr()
+
+
+def _grad_matrices(ny, nx):
+    Gx = sp.kron(sp.identity(ny), _diff_matrix(nx))
+    Gy = sp.kron(_diff_matrix(ny), sp.identity(nx))
+    return Gx.tocsr(), Gy.tocsr()
+
+
+def test_grad_matches_kronecker_construction():
+    ny, nx = 7, 9
+    u = inputs.random_vector(ny * nx, 5).reshape(ny, nx)
+    w = inputs.random_vector(2 * ny * nx, 6).reshape(2, ny, nx)
+    Gx, Gy = _grad_matrices(ny, nx)
+    gx, gy = tv.grad(u)
+    np.testing.assert_allclose(gx.ravel(), Gx @ u.ravel(), atol=1e-15)
+    np.testing.assert_allclose(gy.ravel(), Gy @ u.ravel(), atol=1e-15)
+    got = tv.grad_adj(w[0], w[1]).ravel()
+    np.testing.assert_allclose(got, Gx.T @ w[0].ravel() + Gy.T @ w[1].ravel(), atol=1e-14)
+
+
+def test_grad_adjoint_identity():
+    u = inputs.random_vector(64 * 64, 7).reshape(64, 64)
+    w = inputs.random_vector(2 * 64 * 64, 8).reshape(2, 64, 64)
+    gx, gy = tv.grad(u)
+    lhs = float((gx * w[0]).sum() + (gy * w[1]).sum())
+    rhs = float((u * tv.grad_adj(w[0], w[1])).sum())
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def _small_problem(n=16, nt=24, keep=1):
+    A = radon.siddon_matrix(n, nt, keep, inputs.n_bins_for(n))
+    return A
+
+
+def _dense_op(A, n, c_id, c_ata, c_grad):
+    Gx, Gy = _grad_matrices(n, n)
+    Ad = A.toarray()
+    L = (Gx.T @ Gx + Gy.T @ Gy).toarray()
+    return c_id * np.eye(n * n) + c_ata * Ad.T @ Ad + c_grad * L
+
+
+def test_cg_converges_to_dense_cholesky_solve():
+    n = 16
+    A = _small_problem(n)
+    M = _dense_op(A, n, 0.0, 1.0, 0.5)
+    rhs = inputs.random_vector(n * n, 9)
+    Lc = np.linalg.cholesky(M)
+    want = sla.solve_triangular(Lc.T, sla.solve_triangular(Lc, rhs, lower=True), lower=False)
+    op = tv.make_operator(A, (n, n), 0.0, 1.0, 0.5)
+    got, st = tv.cg(op, rhs, np.zeros(n * n), 2000, rel_tol=1e-13)
+    assert st["rel_res"] <= 1e-13
+    assert np.linalg.norm(got - want) <= 1e-9 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 8])
+def test_cg_iterate_minimises_energy_over_krylov_space(k):
+    """After k steps from x0, CG's iterate minimises the Op-energy of the
+    error over x0 + span{r0, Op r0, ..., Op^{k-1} r0}."""
+    n = 16
+    A = _small_problem(n)
+    M = _dense_op(A, n, 0.0, 1.0, 0.3)
+    rhs = inputs.random_vector(n * n, 10)
+    x0 = inputs.random_vector(n * n, 11)
+    r0 = rhs - M @ x0
+    V = [r0]
+    for _ in range(k - 1):
+        V.append(M @ V[-1])
+    Qb, _ = np.linalg.qr(np.stack(V, axis=1))
+    y = np.linalg.solve(Qb.T @ M @ Qb, Qb.T @ r0)
+    want = x0 + Qb @ y
+    op = tv.make_operator(A, (n, n), 0.0, 1.0, 0.3)
+    got, st = tv.cg(op, rhs, x0, k)
+    assert st["iters"] == k
+    assert np.linalg.norm(got - want) <= 1e-8 * np.linalg.norm(want)
+
+
+def test_sb_1d_tv_denoising_satisfies_optimality_certificate():
+    """A = I on an n x 1 image: SB must reach the 1-D TV-denoising minimiser of
+    alpha/2 ||u - f||^2 + sum |u_{k+1} - u_k|.  Its certificate is
+    z_k = alpha sum_{i<=k} (u_i - f_i), with |z_k| <= 1, z_k = sign(u_{k+1}-u_k)
+    wherever u jumps, and sum_i (u_i - f_i) = 0."""
+    n, alpha = 40, 2.0
+    rng = np.random.Generator(np.random.PCG64(12))
+    f = np.repeat(rng.uniform(0, 3, 5), 8) + 0.4 * rng.standard_normal(n)
+    A = sp.identity(n, format="csr")
+    res = tv.split_bregman(A, f, (n, 1), alpha, 0.5, outer=3000, inner=200, cg_tol=1e-14)
+    u = res["u"].ravel()
+    z = alpha * np.cumsum(u - f)
+    assert abs(z[-1]) <= 1e-8
+    z = z[:-1]
+    du = np.diff(u)
+    assert np.all(np.abs(z) <= 1.0 + 1e-7)
+    jumps = np.abs(du) > 1e-8
+    assert jumps.any() and not jumps.all()
+    np.testing.assert_allclose(z[jumps], np.sign(du[jumps]), atol=1e-6)
+
+
+def test_sb_constant_image_is_a_fixed_point():
+    n = 16
+    A = _small_problem(n)
+    u_true = np.full((n, n), 0.7)
+    f = A @ u_true.ravel()
+    res = tv.split_bregman(A, f, (n, n), 1.0, 1.0, outer=5, inner=10, u0=u_true)
+    np.testing.assert_allclose(res["u"], u_true, atol=1e-13)
+    for key in ("dx", "dy", "bx", "by"):
+        assert np.abs(res[key]).max() <= 1e-13
+
+
+def test_sb_limit_satisfies_tv_kkt_conditions():
+    """At convergence z = lambda b certifies optimality of u for
+    min alpha/2 ||A u - f||^2 + ||grad u||_1: |z| <= 1, z = sign(grad u) where
+    grad u != 0, alpha A^T (A u - f) + grad^T z = 0; and u beats nearby points."""
+    n, alpha, lam = 8, 0.3, 2.0
+    A = radon.siddon_matrix(n, 12, 1, inputs.n_bins_for(n))
+    truth = inputs.ellipse_phantom(n, 3)
+    f = A @ truth.ravel() + 0.3 * inputs.standard_normal(A.shape[0], 4)
+    res = tv.split_bregman(A, f, (n, n), alpha, lam, outer=1500, inner=300, cg_tol=1e-14)
+    u = res["u"]
+    assert res["updates"][-1] <= 1e-10 * res["updates"][0]
+    zx, zy = lam * res["bx"], lam * res["by"]
+    gx, gy = tv.grad(u)
+    assert max(np.abs(zx).max(), np.abs(zy).max()) <= 1.0 + 1e-8
+    for g, z in ((gx, zx), (gy, zy)):
+        nz = np.abs(g) > 1e-7
+        np.testing.assert_allclose(z[nz], np.sign(g[nz]), atol=1e-6)
+    stat = alpha * (A.T @ (A @ u.ravel() - f)) + tv.grad_adj(zx, zy).ravel()
+    assert np.abs(stat).max() <= 1e-7
+    F0 = tv.tv_objective(A, f, u, alpha)
+    rng = np.random.Generator(np.random.PCG64(13))
+    for eps in (1e-3, 1e-5):
+        for _ in range(20):
+            v = rng.standard_normal(u.shape)
+            assert tv.tv_objective(A, f, u + eps * v, alpha) >= F0 - 1e-12 * abs(F0)
+
+
+def test_resolvent_identity_case_and_dense_solve():
+    n = 16
+    A = _small_problem(n)
+    ut = inputs.random_vector(n * n, 14).reshape(n, n)
+    g = inputs.random_vector(A.shape[0], 15)
+    # tau alpha = 0: the resolvent is the identity, the solution is u_tilde
+    u, _ = tv.resolvent(A, (n, n), 0.0, 1.0, ut, g, 3, u0=np.zeros(n * n))
+    np.testing.assert_allclose(u, ut.ravel(), atol=1e-14)
+    tau, alpha = 0.02, 1.0
+    u, st = tv.resolvent(A, (n, n), tau, alpha, ut, g, 500)
+    M = _dense_op(A, n, 1.0, tau * alpha, 0.0)
+    want = np.linalg.solve(M, ut.ravel() + tau * alpha * (A.T @ g))
+    assert np.linalg.norm(u - want) <= 1e-9 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("r,shape,ntaps", [(1, "disc", 5), (3, "disc", 29), (2, "square", 25)])
+def test_surrogate_matrix_is_sum_of_translates(r, shape, ntaps):
+    n = 32
+    A = radon.siddon_matrix(n, 40, 1, inputs.n_bins_for(n))
+    h = tv.point_response(A, n)
+    taps = tv.surrogate_stencil(h, r, shape)
+    assert len(taps) == ntaps
+    T = tv.surrogate_matrix(taps, n)
+    # symmetric to the last bit
+    assert (T - T.T).count_nonzero() == 0
+    # column c holds the truncated, symmetrised point response
+    c = (n // 2) * n + n // 2
+    col = T[:, c].toarray().ravel().reshape(n, n)
+    for (di, dj), v in taps.items():
+        assert col[n // 2 + di, n // 2 + dj] == v
+        assert v == 0.5 * (h[n // 2 + di, n // 2 + dj] + h[n // 2 - di, n // 2 - dj])
+    assert np.count_nonzero(col) <= ntaps
+    # T u equals a zero-padded correlation with the stencil (independent library path)
+    K = np.zeros((2 * r + 1, 2 * r + 1))
+    for (di, dj), v in taps.items():
+        K[r + di, r + dj] = v
+    u = inputs.random_vector(n * n, 16).reshape(n, n)
+    want = ssig.correlate2d(u, K[::-1, ::-1], mode="same", boundary="fill")
+    np.testing.assert_allclose((T @ u.ravel()).reshape(n, n), want, atol=1e-11)
+
+
+def test_point_response_is_column_of_normal_matrix():
+    n = 16
+    A = _small_problem(n)
+    h = tv.point_response(A, n)
+    Ad = A.toarray()
+    np.testing.assert_allclose(h.ravel(), (Ad.T @ Ad)[:, (n // 2) * n + n // 2], atol=1e-13)
+
+
+def test_surrogate_reconstruction_is_less_accurate_and_improves_with_r():
+    """Sec. 4 (Tables of fixed-iteration error, and the r = 3 remark): after a
+    fixed number of updates the surrogate reconstruction is further from the
+    exact-operator one, and a larger r brings it closer."""
+    n = 64
+    A = radon.siddon_matrix(n, 90, 3, 91)
+    truth = inputs.ellipse_phantom(n, 0)
+    f = A @ truth.ravel()
+    exact = tv.split_bregman(A, f, (n, n), 1.0, 1.0, outer=20, inner=10)["u"]
+    h = tv.point_response(A, n)
+    errs = []
+    for r in (1, 3):
+        T = tv.surrogate_matrix(tv.surrogate_stencil(h, r), n)
+        u = tv.split_bregman(A, f, (n, n), 1.0, 1.0, outer=20, inner=10, normal=lambda x: T @ x)["u"]
+        errs.append(np.abs(u - truth).sum() / np.abs(truth).sum())
+    err_exact = np.abs(exact - truth).sum() / np.abs(truth).sum()
+    assert errs[0] > err_exact and errs[1] > err_exact
+    assert errs[1] < errs[0]
