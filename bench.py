@@ -1,0 +1,426 @@
+"""Benchmark: TV split-Bregman reconstructions per second on one GB300.
+
+Step = one whole reconstruction of the 512x512 slice workload (180 of 720
+angles, 725 bins, 1% Gaussian noise, alpha = lambda = 1, 50 Bregman updates of
+20 CG steps: 1050 applications of A and A^T) through ct_split_bregman, with
+the matrices and data resident in HBM.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (numpy/scipy, one thread) on the
+host cores on a bounded sample of the same workload.  Under torchrun (N > 1)
+every rank reconstructs its own slices (replicas, no collective on the data
+path); rank 0 prints the job's aggregate.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+if "--_oracle-in" in sys.argv or "reference" in sys.argv:
+    # the oracle runs single-threaded; set before numpy loads its BLAS
+    for _k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_k] = "1"
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1705_07497_gb300 import inputs  # noqa: E402
+
+METRIC = "TV recon slices/s at <=1e-3 rel err vs FP64 oracle; SpMV/SpMM HBM GB/s"
+WORKLOAD = "slice_512"
+HBM_FALLBACK = 6800.0
+ORACLE_UPDATES = 2  # Bregman updates in the bounded CPU sample
+
+
+def workload_desc(wl):
+    return ("%dx%d slice, %d of %d angles (keep every %d), %d bins, split Bregman %d x %d CG, "
+            "alpha=%g lambda=%g, %s noise" % (wl["n"], wl["n"], -(-wl["n_angles_total"] // wl["keep_every"]),
+                                            wl["n_angles_total"], wl["keep_every"], wl["n_bins"],
+                                            wl["outer"], wl["inner"], wl["alpha"], wl["lam"],
+                                            "1% Gaussian" if wl["noise"] == "gauss" else wl["noise"]))
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("spmv.cu", "reduce.cuh", "ct_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1705_07497_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it still
+    describes the current kernel source (same hash); else None."""
+    path = os.path.join(ROOT, "profiles", "spmv_forward_slice512.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["%s_dram_bytes_per_launch" % kernel_key])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.remove(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def noisy(wl, clean, seed):
+    if wl["noise"] == "gauss":
+        return inputs.gaussian_noisy(clean, wl["sigma_rel"], seed)
+    if wl["noise"] == "poisson":
+        return inputs.poisson_noisy(clean, wl["counts"], seed)
+    return clean
+
+
+def make_data(wl, M, dev, seed):
+    import torch
+
+    truth = inputs.ellipse_phantom(wl["n"], seed)
+    x = torch.tensor(truth.ravel(), dtype=torch.float32, device=dev)
+    y = torch.empty(M.rows, dtype=torch.float32, device=dev)
+    M.forward(x, y)
+    clean = y.double().cpu().numpy()
+    return truth, noisy(wl, clean, seed + 1)
+
+
+def oracle_sample_main(args):
+    """Runs in a fresh single-threaded interpreter: the oracle on ORACLE_UPDATES
+    Bregman updates of the workload; writes u and prints the seconds taken."""
+    from oracle import radon, tv
+
+    wl = inputs.WORKLOADS[args.workload]
+    f = np.load(args.oracle_in)
+    A = radon.siddon_matrix(wl["n"], wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
+    t0 = time.perf_counter()
+    res = tv.split_bregman(A, f, (wl["n"], wl["n"]), wl["alpha"], wl["lam"], args.oracle_updates, wl["inner"])
+    dt = time.perf_counter() - t0
+    np.save(args.oracle_out, res["u"].ravel())
+    print(json.dumps({"seconds": dt}))
+
+
+def run_oracle_sample(wl_name, f, updates):
+    with tempfile.TemporaryDirectory() as td:
+        fin, fout = os.path.join(td, "f.npy"), os.path.join(td, "u.npy")
+        np.save(fin, f)
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[k] = "1"
+        env["CUDA_VISIBLE_DEVICES"] = ""
+        out = subprocess.run(
+            [sys.executable, os.path.abspath(__file__), "--workload", wl_name, "--_oracle-in", fin,
+             "--_oracle-out", fout, "--_oracle-updates", str(updates)],
+            capture_output=True, text=True, env=env, check=True)
+        secs = json.loads(out.stdout.strip().splitlines()[-1])["seconds"]
+        return secs, np.load(fout)
+
+
+def bench_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1705_07497_gb300 import ct
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    wl = inputs.WORKLOADS[args.workload]
+    n = wl["n"]
+    M = ct.Matrix(n, wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
+    truth, f_host = make_data(wl, M, dev, wl["seed"] + rank)
+    f = torch.tensor(f_host, dtype=torch.float32, device=dev)
+    u = torch.zeros(n * n, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        u.zero_()
+        M.split_bregman(f, u, wl["alpha"], wl["lam"], wl["outer"], wl["inner"], stats=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = M.split_bregman(f, u.zero_(), wl["alpha"], wl["lam"], wl["outer"], wl["inner"])
+    assert st["status"] == 0 and st["outer_done"] == wl["outer"], st
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    secs = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        t = torch.tensor([secs], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    value = world * args.steps / secs
+
+    # dominant kernels: the forward and adjoint CSR products, timed with CUDA
+    # events on this stream, back to back, same matrix and vectors
+    x = u.clone()
+    y = torch.empty(M.rows, dtype=torch.float32, device=dev)
+    xa = torch.empty(M.cols, dtype=torch.float32, device=dev)
+    reps = max(20, args.steps * 10)
+
+    def time_kernel(fn):
+        for _ in range(5):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3 / reps
+
+    t_fwd = time_kernel(lambda: M.forward(x, y))
+    t_adj = time_kernel(lambda: M.adjoint(y, xa))
+    bytes_fwd = M.nnz * 8 + (M.rows + 1) * 8 + M.cols * 4 + M.rows * 4
+    bytes_adj = M.nnz * 8 + (M.cols + 1) * 8 + M.rows * 4 + M.cols * 4
+    peak, peak_kind = measured_peak()
+    ach_fwd = bytes_fwd / t_fwd / 1e9
+    ach_adj = bytes_adj / t_adj / 1e9
+
+    # end to end through the public API with pinned host buffers
+    f_pin = torch.tensor(f_host, dtype=torch.float32).pin_memory()
+    u_pin = torch.zeros(n * n, dtype=torch.float32).pin_memory()
+    M.split_bregman(f_pin, u_pin, wl["alpha"], wl["lam"], wl["outer"], wl["inner"], stats=False)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u_pin.zero_()
+        M.split_bregman(f_pin, u_pin, wl["alpha"], wl["lam"], wl["outer"], wl["inner"], stats=False)
+    e2e_secs = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_secs], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_secs = float(t.item())
+
+    launches_per_step = 1 + wl["outer"] * (2 + 4 * wl["inner"] + 1)
+    out = {
+        "metric": METRIC,
+        "value": round(value, 4),
+        "unit": "slices/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1e3 * secs / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic: seeded random-ellipse phantom, projected by A, 1% Gaussian noise",
+        "config": {
+            "workload": WORKLOAD + ": " + workload_desc(wl),
+            "matrix": "CSR A and A^T, FP32 values, int32 columns, nnz %d each" % M.nnz,
+            "l2": "inputs larger than L2: A and A^T stream %.2f GB per operator application"
+                  % ((bytes_fwd + bytes_adj) / 1e9),
+            "parallelism": "replicas over slices" if world > 1 else "single GPU",
+        },
+        "roofline": {
+            "kernel": "spmv_store_kernel<float> (y = A x, CSR FP32, one warp per row)",
+            "bound": "hbm",
+            "achieved": round(ach_fwd, 1),
+            "peak": peak,
+            "peak_kind": peak_kind,
+            "unit": "GB/s",
+            "frac": round(ach_fwd / peak, 4),
+            "traffic": profiled_traffic("forward"),
+            "algorithmic_bytes": int(bytes_fwd),
+            "launch_ms": round(t_fwd * 1e3, 4),
+        },
+        "kernels": {
+            "adjoint_spmv": {"achieved_gbs": round(ach_adj, 1), "frac": round(ach_adj / peak, 4),
+                             "launch_ms": round(t_adj * 1e3, 4), "algorithmic_bytes": int(bytes_adj)},
+        },
+        "e2e": {
+            "value": round(world * args.steps / e2e_secs, 4),
+            "unit": "slices/s",
+            "h2d_bytes_per_step": int(f_pin.numel() * 4 + u_pin.numel() * 4),
+            "d2h_bytes_per_step": int(u_pin.numel() * 4),
+        },
+        "gpu_launches": int(launches_per_step * args.steps),
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        secs_cpu, u_oracle = run_oracle_sample(args.workload, f_host, ORACLE_UPDATES)
+        u2 = torch.zeros(n * n, dtype=torch.float32, device=dev)
+        M.split_bregman(f, u2, wl["alpha"], wl["lam"], ORACLE_UPDATES, wl["inner"])
+        err = float(np.linalg.norm(u2.cpu().double().numpy() - u_oracle) / np.linalg.norm(u_oracle))
+        out["cpu_baseline"] = {
+            "value": round(ORACLE_UPDATES / wl["outer"] / secs_cpu, 6),
+            "unit": "slices/s",
+            "cores": 1,
+            "kind": "oracle",
+            "sample": "%d of %d Bregman updates (20 CG steps each) of the same workload, FP64 numpy/scipy "
+                      "CSR, one thread; %.1f s" % (ORACLE_UPDATES, wl["outer"], secs_cpu),
+        }
+        out["parity"] = {"rel_l2_vs_oracle_after_%d_updates" % ORACLE_UPDATES: err}
+    if rank == 0:
+        print(json.dumps(out))
+    M.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def bench_reference(args):
+    """The FP64 CPU oracle as it stands, on host cores; rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import radon, tv
+
+    wl = inputs.WORKLOADS[args.workload]
+    n = wl["n"]
+    A = radon.siddon_matrix(n, wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
+    truth = inputs.ellipse_phantom(n, wl["seed"])
+    f = noisy(wl, A @ truth.ravel(), wl["seed"] + 1)
+    per_step = 1  # Bregman updates per timed step (1/50 of a reconstruction)
+    state = None
+
+    def step(state):
+        res = tv.split_bregman(A, f, (n, n), wl["alpha"], wl["lam"], per_step, wl["inner"], state=state)
+        return (res["u"], res["dx"], res["dy"], res["bx"], res["by"])
+
+    for _ in range(args.warmup):
+        state = step(state)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        state = step(state)
+    secs = time.perf_counter() - t0
+    value = args.steps * per_step / wl["outer"] / secs
+    print(json.dumps({
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(value, 6),
+        "unit": "slices/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1e3 * secs / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic: seeded random-ellipse phantom, projected by the oracle's A, 1% Gaussian noise",
+        "config": {"workload": WORKLOAD + ": " + workload_desc(wl),
+                   "sample": "each step = 1 of 50 Bregman updates (20 CG steps)"},
+        "cpu_baseline": {"value": round(value, 6), "unit": "slices/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step = 1 of %d Bregman updates, FP64 numpy/scipy, one thread"
+                                   % wl["outer"]},
+        "e2e": {"value": round(value, 6), "unit": "slices/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--_oracle-in", dest="oracle_in", default=None)
+    ap.add_argument("--_oracle-out", dest="oracle_out", default=None)
+    ap.add_argument("--_oracle-updates", dest="oracle_updates", type=int, default=ORACLE_UPDATES)
+    args = ap.parse_args()
+    if args.oracle_in:
+        oracle_sample_main(args)
+        return
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

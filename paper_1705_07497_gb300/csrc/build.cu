@@ -1,0 +1,420 @@
+// Builder of the sparse system matrices A = M R and A^T (Sec. 3: the matrices
+// depend only on the geometry and are precomputed once, offline), and of the
+// surrogate stencil of Sec. 3.2.
+//
+// Every entry is the exact length of a ray inside a pixel.  Instead of walking
+// the ray (Siddon), each candidate (ray, pixel) pair is evaluated with the
+// closed-form chord of a unit square: for a line with unit normal (c, s) at
+// distance t from the pixel centre, with a = max(|c|,|s|), b = min(|c|,|s|),
+//     L(t) = 1/a                       for t <= (a-b)/2
+//          = ((a+b)/2 - t) / (a b)     for (a-b)/2 < t < (a+b)/2
+//          = 0                         otherwise,
+// and for b = 0 (axis-aligned ray) L = 1 inside, 1/2 on an edge (the edge
+// reading: half the length to each of the two pixels sharing the edge).
+// A is built ray by ray (rows = rays, columns ascending), A^T pixel by pixel
+// (rows = pixels, ray index ascending), so neither needs a transpose or
+// atomics; both evaluate the same function with the same operation order, so
+// A^T holds bit-identical values.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "ct_internal.cuh"
+
+namespace ct {
+namespace {
+
+constexpr double kMinLen = 1e-12;  // lengths below this are dropped
+constexpr double kPi = 3.14159265358979323846;
+
+// Per kept angle: cos, sin, a = max(|cos|,|sin|), b = min(...), t2 = support half-width.
+struct AngleRow {
+    double c, s, a, b, t2;
+};
+
+__device__ __forceinline__ double ray_offset(double xc, double yc, double c, double s, double sb)
+{
+    // explicit round-to-nearest operations: no FMA contraction, so that the A
+    // and A^T builders produce identical bits for the same (ray, pixel) pair
+    return fabs(__dadd_rn(__dadd_rn(__dmul_rn(xc, c), __dmul_rn(yc, s)), -sb));
+}
+
+__device__ __forceinline__ double chord(double t, const AngleRow& g)
+{
+    if (g.b == 0.0) return t < 0.5 ? 1.0 : (t == 0.5 ? 0.5 : 0.0);
+    const double t1 = __dmul_rn(0.5, __dsub_rn(g.a, g.b));
+    if (t <= t1) return __ddiv_rn(1.0, g.a);
+    if (t >= g.t2) return 0.0;
+    return __ddiv_rn(__dsub_rn(g.t2, t), __dmul_rn(g.a, g.b));
+}
+
+// IEEE-754 binary16 from a double, round to nearest, ties to even, written
+// from the format's definition (1 sign, 5 exponent bits with bias 15, 10
+// fraction bits; subnormals are multiples of 2^-24).
+__host__ __device__ inline uint16_t f64_to_f16_bits(double x)
+{
+    uint16_t sign = std::signbit(x) ? 0x8000u : 0u;
+    double a = std::fabs(x);
+    if (a != a) return sign | 0x7e00u;
+    if (a < 6.103515625e-05) {  // below 2^-14: subnormal (or zero)
+        double m = std::rint(a * 16777216.0);  // a / 2^-24, rounded to nearest even
+        return sign | (uint16_t)m;             // m == 1024 is the smallest normal
+    }
+    int e;
+    std::frexp(a, &e);  // a = f 2^e, f in [0.5, 1)
+    int E = e - 1;      // a = 1.xxx 2^E
+    if (E > 15) return sign | 0x7c00u;
+    double m = std::rint(std::ldexp(a, 10 - E));  // in [1024, 2048]
+    unsigned mi = (unsigned)m;
+    if (mi == 2048u) {
+        mi = 1024u;
+        ++E;
+        if (E > 15) return sign | 0x7c00u;
+    }
+    return sign | (uint16_t)(((E + 15) << 10) | (mi - 1024u));
+}
+
+__device__ __forceinline__ __half f16_from_bits(uint16_t b)
+{
+    __half_raw r;
+    r.x = b;
+    return __half(r);
+}
+
+// One thread per ray q = k*n_bins + b: sweep the image rows, evaluate the
+// pixels of each row the line can reach, keep lengths >= kMinLen.
+template <bool FILL>
+__global__ void a_rows_kernel(int n, int nb, int n_kept, const AngleRow* __restrict__ ang,
+                              int32_t* __restrict__ row_len, float* __restrict__ row_max,
+                              const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col,
+                              float* __restrict__ val, __half* __restrict__ qval,
+                              const float* __restrict__ scale)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= (int64_t)n_kept * nb) return;
+    const int k = (int)(q / nb), b = (int)(q % nb);
+    const AngleRow g = ang[k];
+    const double sb = b - 0.5 * (nb - 1);
+    const double half = 0.5 * n;
+    int cnt = 0;
+    double mx = 0.0;
+    int64_t base = 0;
+    double sq = 1.0;
+    if (FILL) {
+        base = row_ptr[q];
+        if (qval) sq = (double)scale[q];
+    }
+    int32_t last = 0;
+    for (int i = 0; i < n; ++i) {
+        const double yc = i - half + 0.5;
+        int jlo, jhi;
+        if (g.c == 0.0) {
+            if (fabs(yc * g.s - sb) > g.t2 + 1e-9) continue;
+            jlo = 0;
+            jhi = n - 1;
+        } else {
+            const double jc = (sb - yc * g.s) / g.c + half - 0.5;
+            const double w = g.t2 / fabs(g.c);
+            const double lo = fmax(floor(jc - w) - 1.0, 0.0);
+            const double hi = fmin(ceil(jc + w) + 1.0, n - 1.0);
+            if (lo > hi) continue;
+            jlo = (int)lo;
+            jhi = (int)hi;
+        }
+        for (int j = jlo; j <= jhi; ++j) {
+            const double xc = j - half + 0.5;
+            const double len = chord(ray_offset(xc, yc, g.c, g.s, sb), g);
+            if (len < kMinLen) continue;
+            last = i * n + j;
+            if (FILL) {
+                col[base + cnt] = last;
+                if (val) val[base + cnt] = (float)len;
+                if (qval) qval[base + cnt] = f16_from_bits(f64_to_f16_bits(len / sq));
+            } else {
+                mx = fmax(mx, len);
+            }
+            ++cnt;
+        }
+    }
+    if (!FILL) {
+        row_len[q] = cnt;
+        if (row_max) row_max[q] = (float)mx;
+    } else {
+        const int64_t end = row_ptr[q + 1];
+        for (int64_t e = base + cnt; e < end; ++e) {
+            col[e] = last;
+            if (val) val[e] = 0.0f;
+            if (qval) qval[e] = __float2half(0.0f);
+        }
+    }
+}
+
+// One thread per pixel p = i*N + j: for every kept angle, evaluate the bins
+// whose rays can cross the pixel; columns come out as ascending ray indices.
+template <bool FILL>
+__global__ void at_rows_kernel(int n, int nb, int n_kept, const AngleRow* __restrict__ ang,
+                               int32_t* __restrict__ row_len, const int64_t* __restrict__ row_ptr,
+                               int32_t* __restrict__ col, float* __restrict__ val,
+                               __half* __restrict__ qval, const float* __restrict__ scale)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= (int64_t)n * n) return;
+    const int i = (int)(p / n), j = (int)(p % n);
+    const double half = 0.5 * n;
+    const double xc = j - half + 0.5, yc = i - half + 0.5;
+    const double mid = 0.5 * (nb - 1);
+    int cnt = 0;
+    int64_t base = FILL ? row_ptr[p] : 0;
+    int32_t last = 0;
+    for (int k = 0; k < n_kept; ++k) {
+        const AngleRow g = ang[k];
+        const double tc = xc * g.c + yc * g.s + mid;
+        const double lo = fmax(floor(tc - g.t2) - 1.0, 0.0);
+        const double hi = fmin(ceil(tc + g.t2) + 1.0, nb - 1.0);
+        for (int b = (int)lo; b <= (int)hi; ++b) {
+            const double sb = b - mid;
+            const double len = chord(ray_offset(xc, yc, g.c, g.s, sb), g);
+            if (len < kMinLen) continue;
+            last = k * nb + b;
+            if (FILL) {
+                col[base + cnt] = last;
+                if (val) val[base + cnt] = (float)len;
+                if (qval) qval[base + cnt] = f16_from_bits(f64_to_f16_bits(len / (double)scale[last]));
+            }
+            ++cnt;
+        }
+    }
+    if (!FILL) {
+        row_len[p] = cnt;
+    } else {
+        const int64_t end = row_ptr[p + 1];
+        for (int64_t e = base + cnt; e < end; ++e) {
+            col[e] = last;
+            if (val) val[e] = 0.0f;
+            if (qval) qval[e] = __float2half(0.0f);
+        }
+    }
+}
+
+// h(d) = sum_q A[q, c] A[q, c + d] for every offset d of the square window
+// [-r, r]^2 around c = (N/2, N/2), in FP64.  One block per offset; the sum
+// runs in a fixed order (per-thread angle strides, then a tree).
+__global__ void point_response_kernel(int n, int nb, int n_kept, const AngleRow* __restrict__ ang,
+                                      int r, double* __restrict__ h)
+{
+    const int w = 2 * r + 1;
+    const int di = (int)blockIdx.x / w - r, dj = (int)blockIdx.x % w - r;
+    const int ci = n / 2, cj = n / 2;
+    const int ti = ci + di, tj = cj + dj;
+    const double half = 0.5 * n, mid = 0.5 * (nb - 1);
+    const double xc = cj - half + 0.5, yc = ci - half + 0.5;
+    const double xt = tj - half + 0.5, yt = ti - half + 0.5;
+    const bool inside = ti >= 0 && ti < n && tj >= 0 && tj < n;
+    double acc = 0.0;
+    if (inside) {
+        for (int k = threadIdx.x; k < n_kept; k += blockDim.x) {
+            const AngleRow g = ang[k];
+            const double tc = xc * g.c + yc * g.s + mid;
+            const double lo = fmax(floor(tc - g.t2) - 1.0, 0.0);
+            const double hi = fmin(ceil(tc + g.t2) + 1.0, nb - 1.0);
+            for (int b = (int)lo; b <= (int)hi; ++b) {
+                const double sb = b - mid;
+                const double l1 = chord(ray_offset(xc, yc, g.c, g.s, sb), g);
+                if (l1 < kMinLen) continue;
+                const double l2 = chord(ray_offset(xt, yt, g.c, g.s, sb), g);
+                if (l2 < kMinLen) continue;
+                acc += l1 * l2;
+            }
+        }
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) h[blockIdx.x] = red[0];
+}
+
+int alloc_dev(void** p, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        (void)cudaGetLastError();
+        return fail(CT_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    CT_CUDA(e);
+    return CT_OK;
+}
+
+// Turns per-row lengths into padded row pointers on the host.
+int finish_layout(Csr& m, const std::vector<int32_t>& len)
+{
+    std::vector<int64_t> rp(len.size() + 1, 0);
+    int64_t nnz = 0;
+    for (size_t i = 0; i < len.size(); ++i) {
+        nnz += len[i];
+        rp[i + 1] = rp[i] + ((int64_t)len[i] + kRowPad - 1) / kRowPad * kRowPad;
+    }
+    m.nnz = nnz;
+    m.nnz_pad = rp.back();
+    CT_CHECK(alloc_dev((void**)&m.row_ptr, rp.size() * sizeof(int64_t)));
+    CT_CUDA(cudaMemcpy(m.row_ptr, rp.data(), rp.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    return CT_OK;
+}
+
+std::vector<AngleRow> angle_table(const ct_geometry& g, std::vector<double>& hc, std::vector<double>& hs)
+{
+    const int n_kept = (g.n_angles_total + g.keep_every - 1) / g.keep_every;
+    std::vector<AngleRow> t(n_kept);
+    hc.resize(n_kept);
+    hs.resize(n_kept);
+    for (int kk = 0; kk < n_kept; ++kk) {
+        const int k = kk * g.keep_every;
+        double c, s;
+        if (k == 0) {
+            c = 1.0;
+            s = 0.0;
+        } else if (2 * k == g.n_angles_total) {
+            c = 0.0;
+            s = 1.0;
+        } else {
+            const double th = (double)k * kPi / (double)g.n_angles_total;
+            c = std::cos(th);
+            s = std::sin(th);
+        }
+        const double a = std::fmax(std::fabs(c), std::fabs(s));
+        const double b = std::fmin(std::fabs(c), std::fabs(s));
+        t[kk] = AngleRow{c, s, a, b, b == 0.0 ? 0.5 : 0.5 * (a + b)};
+        hc[kk] = c;
+        hs[kk] = s;
+    }
+    return t;
+}
+
+}  // namespace
+
+void free_csr(Csr& c)
+{
+    cudaFree(c.row_ptr);
+    cudaFree(c.row_len);
+    cudaFree(c.col);
+    cudaFree(c.val);
+    cudaFree(c.qval);
+    c = Csr{};
+}
+
+int build_matrices(ct_matrix* M)
+{
+    const ct_geometry& g = M->g;
+    std::vector<AngleRow> tab = angle_table(g, M->h_cos, M->h_sin);
+    M->n_kept = (int)tab.size();
+    const int n = g.n, nb = g.n_bins, nk = M->n_kept;
+    M->rows = (int64_t)nk * nb;
+    M->cols = (int64_t)n * n;
+    const bool f16 = (M->flags & CT_VAL_FP16_ROWSCALE) != 0;
+    const bool f32 = !f16 || (M->flags & CT_KEEP_FP32_COPY);
+
+    AngleRow* d_ang = nullptr;
+    CT_CHECK(alloc_dev((void**)&d_ang, tab.size() * sizeof(AngleRow)));
+    CT_CUDA(cudaMemcpy(d_ang, tab.data(), tab.size() * sizeof(AngleRow), cudaMemcpyHostToDevice));
+    M->dirs = (double*)d_ang;
+
+    Csr& A = M->A;
+    Csr& T = M->At;
+    A.rows = M->rows;
+    A.cols = M->cols;
+    T.rows = M->cols;
+    T.cols = M->rows;
+    CT_CHECK(alloc_dev((void**)&A.row_len, A.rows * sizeof(int32_t)));
+    CT_CHECK(alloc_dev((void**)&T.row_len, T.rows * sizeof(int32_t)));
+    if (f16) CT_CHECK(alloc_dev((void**)&M->row_scale, A.rows * sizeof(float)));
+
+    const int tpb = 128;
+    // pass 1: counts (and row maxima for the FP16 scale)
+    a_rows_kernel<false><<<(unsigned)((A.rows + tpb - 1) / tpb), tpb>>>(
+        n, nb, nk, d_ang, A.row_len, f16 ? M->row_scale : nullptr, nullptr, nullptr, nullptr,
+        nullptr, nullptr);
+    CT_CUDA(cudaGetLastError());
+    at_rows_kernel<false><<<(unsigned)((T.rows + tpb - 1) / tpb), tpb>>>(
+        n, nb, nk, d_ang, T.row_len, nullptr, nullptr, nullptr, nullptr, nullptr);
+    CT_CUDA(cudaGetLastError());
+    std::vector<int32_t> la(A.rows), lt(T.rows);
+    CT_CUDA(cudaMemcpy(la.data(), A.row_len, A.rows * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CT_CUDA(cudaMemcpy(lt.data(), T.row_len, T.rows * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CT_CHECK(finish_layout(A, la));
+    CT_CHECK(finish_layout(T, lt));
+    if (A.nnz != T.nnz)
+        return fail(CT_ERR_CUDA, "internal: A and A^T entry counts differ (" + std::to_string(A.nnz) +
+                                     " vs " + std::to_string(T.nnz) + ")");
+    for (Csr* m : {&A, &T}) {
+        CT_CHECK(alloc_dev((void**)&m->col, m->nnz_pad * sizeof(int32_t)));
+        if (f32) CT_CHECK(alloc_dev((void**)&m->val, m->nnz_pad * sizeof(float)));
+        if (f16) CT_CHECK(alloc_dev((void**)&m->qval, m->nnz_pad * sizeof(__half)));
+    }
+    // pass 2: fill
+    a_rows_kernel<true><<<(unsigned)((A.rows + tpb - 1) / tpb), tpb>>>(
+        n, nb, nk, d_ang, nullptr, nullptr, A.row_ptr, A.col, A.val, A.qval, M->row_scale);
+    CT_CUDA(cudaGetLastError());
+    at_rows_kernel<true><<<(unsigned)((T.rows + tpb - 1) / tpb), tpb>>>(
+        n, nb, nk, d_ang, nullptr, T.row_ptr, T.col, T.val, T.qval, M->row_scale);
+    CT_CUDA(cudaGetLastError());
+    CT_CUDA(cudaDeviceSynchronize());
+    return CT_OK;
+}
+
+int make_stencil(ct_matrix* M, int r, int square, Stencil** out)
+{
+    auto key = std::make_pair(r, square ? 1 : 0);
+    auto it = M->stencils.find(key);
+    if (it != M->stencils.end()) {
+        *out = &it->second;
+        return CT_OK;
+    }
+    if (r <= 0 || r > 16) return fail(CT_ERR_ARG, "surrogate radius must be in [1, 16]");
+    const int w = 2 * r + 1;
+    double* d_h = nullptr;
+    CT_CHECK(alloc_dev((void**)&d_h, (size_t)w * w * sizeof(double)));
+    point_response_kernel<<<w * w, 256>>>(M->g.n, M->g.n_bins, M->n_kept, (const AngleRow*)M->dirs, r, d_h);
+    CT_CUDA(cudaGetLastError());
+    std::vector<double> h((size_t)w * w);
+    cudaError_t e = cudaMemcpy(h.data(), d_h, h.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(d_h);
+    CT_CUDA(e);
+    Stencil S;
+    S.r = r;
+    std::vector<float> wf;
+    std::vector<int32_t> dd;
+    for (int di = -r; di <= r; ++di) {
+        for (int dj = -r; dj <= r; ++dj) {
+            if (!square && di * di + dj * dj > r * r) continue;
+            const double v = 0.5 * (h[(size_t)(di + r) * w + (dj + r)] + h[(size_t)(-di + r) * w + (-dj + r)]);
+            S.h_di.push_back(di);
+            S.h_dj.push_back(dj);
+            S.h_w.push_back(v);
+            wf.push_back((float)v);
+            dd.push_back(di);
+            dd.push_back(dj);
+        }
+    }
+    S.ntaps = (int)S.h_w.size();
+    CT_CHECK(alloc_dev((void**)&S.d, dd.size() * sizeof(int32_t)));
+    CT_CHECK(alloc_dev((void**)&S.w, wf.size() * sizeof(float)));
+    CT_CUDA(cudaMemcpy(S.d, dd.data(), dd.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CT_CUDA(cudaMemcpy(S.w, wf.data(), wf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    auto res = M->stencils.emplace(key, std::move(S));
+    *out = &res.first->second;
+    return CT_OK;
+}
+
+void free_stencil(Stencil& s)
+{
+    cudaFree(s.d);
+    cudaFree(s.w);
+    s.d = nullptr;
+    s.w = nullptr;
+}
+
+}  // namespace ct

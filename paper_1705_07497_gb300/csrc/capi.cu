@@ -1,0 +1,332 @@
+// extern "C" entry points of libct (declared and documented in include/ct.h).
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ct_internal.cuh"
+
+namespace ct {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int code, const std::string& msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line)
+{
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    g_last_error = buf;
+    return e == cudaErrorMemoryAllocation ? CT_ERR_OOM : CT_ERR_CUDA;
+}
+
+namespace {
+
+// 1 = device (or managed) memory, 0 = host memory.
+int is_device_ptr(const void* p)
+{
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int check_handle(ct_matrix_t A)
+{
+    if (!A) return fail(CT_ERR_ARG, "NULL matrix handle");
+    int dev = -1;
+    CT_CUDA(cudaGetDevice(&dev));
+    if (dev != A->device)
+        return fail(CT_ERR_ARG, "matrix lives on device " + std::to_string(A->device) +
+                                    " but device " + std::to_string(dev) + " is current");
+    return CT_OK;
+}
+
+// Classifies the vector arguments: all device (0) or all host (1).
+int classify(const void* a, const void* b, int* host)
+{
+    if (!a || !b) return fail(CT_ERR_ARG, "NULL vector pointer");
+    const int da = is_device_ptr(a), db = is_device_ptr(b);
+    if (da != db) return fail(CT_ERR_ARG, "mixing host and device vector pointers in one call");
+    *host = !da;
+    return CT_OK;
+}
+
+int ensure_stage(float** buf, int64_t* len, int64_t need)
+{
+    if (*len >= need) return CT_OK;
+    cudaFree(*buf);
+    *buf = nullptr;
+    *len = 0;
+    cudaError_t e = cudaMalloc((void**)buf, (size_t)need * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(staging)", __FILE__, __LINE__);
+    *len = need;
+    return CT_OK;
+}
+
+ValKind storage_kind(const ct_matrix* M)
+{
+    return (M->flags & CT_VAL_FP16_ROWSCALE) ? ValKind::F16 : ValKind::F32;
+}
+
+}  // namespace
+}  // namespace ct
+
+using namespace ct;
+
+extern "C" {
+
+int ct_build_matrix(const ct_geometry* g, uint32_t flags, ct_matrix_t* out)
+{
+    if (!out) return fail(CT_ERR_ARG, "NULL output handle pointer");
+    *out = nullptr;
+    if (!g) return fail(CT_ERR_ARG, "NULL geometry");
+    if (g->n <= 0 || g->n_angles_total <= 0 || g->keep_every <= 0 || g->n_bins <= 0)
+        return fail(CT_ERR_ARG, "geometry sizes must be positive");
+    if ((int64_t)g->n * g->n >= ((int64_t)1 << 31))
+        return fail(CT_ERR_ARG, "N*N must be below 2^31");
+    const int64_t n_kept = (g->n_angles_total + g->keep_every - 1) / g->keep_every;
+    if (n_kept * g->n_bins >= ((int64_t)1 << 31))
+        return fail(CT_ERR_ARG, "kept angles * bins must be below 2^31");
+    const uint32_t known = CT_VAL_FP16_ROWSCALE | CT_KEEP_FP32_COPY;
+    if (flags & ~known) return fail(CT_ERR_ARG, "unknown flag bits");
+    if ((flags & CT_KEEP_FP32_COPY) && !(flags & CT_VAL_FP16_ROWSCALE))
+        return fail(CT_ERR_ARG, "CT_KEEP_FP32_COPY needs CT_VAL_FP16_ROWSCALE");
+    ct_matrix* M = new (std::nothrow) ct_matrix();
+    if (!M) return fail(CT_ERR_OOM, "host allocation failed");
+    M->g = *g;
+    M->flags = flags;
+    cudaError_t e = cudaGetDevice(&M->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&M->sm_count, cudaDevAttrMultiProcessorCount, M->device);
+    if (e != cudaSuccess) {
+        delete M;
+        return cuda_fail(e, "cudaGetDevice", __FILE__, __LINE__);
+    }
+    int rc = build_matrices(M);
+    if (rc != CT_OK) {
+        ct_destroy_matrix(M);
+        return rc;
+    }
+    *out = M;
+    return CT_OK;
+}
+
+int ct_matrix_info(ct_matrix_t A, int64_t* rows, int64_t* cols, int64_t* nnz)
+{
+    if (!A) return fail(CT_ERR_ARG, "NULL matrix handle");
+    if (rows) *rows = A->rows;
+    if (cols) *cols = A->cols;
+    if (nnz) *nnz = A->A.nnz;
+    return CT_OK;
+}
+
+void ct_destroy_matrix(ct_matrix_t A)
+{
+    if (!A) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != A->device) cudaSetDevice(A->device);
+    cudaDeviceSynchronize();
+    free_workspace(A->ws);
+    for (auto& kv : A->stencils) free_stencil(kv.second);
+    free_csr(A->A);
+    free_csr(A->At);
+    cudaFree(A->row_scale);
+    cudaFree(A->dirs);
+    if (prev >= 0 && prev != A->device) cudaSetDevice(prev);
+    delete A;
+}
+
+int ct_forward(ct_matrix_t A, const float* x, float* y, int32_t batch, void* cuda_stream)
+{
+    CT_CHECK(check_handle(A));
+    if (batch < 1) return fail(CT_ERR_ARG, "batch must be >= 1");
+    int host = 0;
+    CT_CHECK(classify(x, y, &host));
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const ValKind vk = storage_kind(A);
+    if (!host) return launch_forward(A, vk, x, y, batch, 1.0f, false, st);
+    Workspace& w = A->ws;
+    const int64_t nx = A->cols * batch, ny = A->rows * batch;
+    CT_CHECK(ensure_stage(&w.stage_a, &w.stage_a_len, nx));
+    CT_CHECK(ensure_stage(&w.stage_b, &w.stage_b_len, ny));
+    CT_CUDA(cudaMemcpyAsync(w.stage_a, x, nx * sizeof(float), cudaMemcpyHostToDevice, st));
+    CT_CHECK(launch_forward(A, vk, w.stage_a, w.stage_b, batch, 1.0f, false, st));
+    CT_CUDA(cudaMemcpyAsync(y, w.stage_b, ny * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CT_CUDA(cudaStreamSynchronize(st));
+    return CT_OK;
+}
+
+int ct_adjoint(ct_matrix_t A, const float* y, float* x, int32_t batch, void* cuda_stream)
+{
+    CT_CHECK(check_handle(A));
+    if (batch < 1) return fail(CT_ERR_ARG, "batch must be >= 1");
+    int host = 0;
+    CT_CHECK(classify(y, x, &host));
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const ValKind vk = storage_kind(A);
+    if (!host) return launch_adjoint(A, vk, y, x, batch, 1.0f, true, st);
+    Workspace& w = A->ws;
+    const int64_t nx = A->cols * batch, ny = A->rows * batch;
+    CT_CHECK(ensure_stage(&w.stage_a, &w.stage_a_len, nx));
+    CT_CHECK(ensure_stage(&w.stage_b, &w.stage_b_len, ny));
+    CT_CUDA(cudaMemcpyAsync(w.stage_b, y, ny * sizeof(float), cudaMemcpyHostToDevice, st));
+    CT_CHECK(launch_adjoint(A, vk, w.stage_b, w.stage_a, batch, 1.0f, true, st));
+    CT_CUDA(cudaMemcpyAsync(x, w.stage_a, nx * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CT_CUDA(cudaStreamSynchronize(st));
+    return CT_OK;
+}
+
+int ct_cg_solve(ct_matrix_t A, const ct_cg_params* params, const float* rhs, float* u,
+                int32_t batch, ct_cg_stats* stats, void* cuda_stream)
+{
+    CT_CHECK(check_handle(A));
+    if (!params) return fail(CT_ERR_ARG, "NULL params");
+    if (batch < 1) return fail(CT_ERR_ARG, "batch must be >= 1");
+    int host = 0;
+    CT_CHECK(classify(rhs, u, &host));
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (!host) return cg_solve(A, params, rhs, u, batch, stats, st);
+    Workspace& w = A->ws;
+    const int64_t nx = A->cols * batch;
+    CT_CHECK(ensure_stage(&w.stage_a, &w.stage_a_len, nx));
+    CT_CHECK(ensure_stage(&w.stage_b, &w.stage_b_len, nx));
+    CT_CUDA(cudaMemcpyAsync(w.stage_a, rhs, nx * sizeof(float), cudaMemcpyHostToDevice, st));
+    CT_CUDA(cudaMemcpyAsync(w.stage_b, u, nx * sizeof(float), cudaMemcpyHostToDevice, st));
+    int rc = cg_solve(A, params, w.stage_a, w.stage_b, batch, stats, st);
+    if (rc != CT_OK && rc != CT_ERR_BREAKDOWN && rc != CT_ERR_NONFINITE) return rc;
+    CT_CUDA(cudaMemcpyAsync(u, w.stage_b, nx * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CT_CUDA(cudaStreamSynchronize(st));
+    return rc;
+}
+
+int ct_split_bregman(ct_matrix_t A, const ct_sb_params* params, const float* f, float* u,
+                     int32_t batch, ct_sb_stats* stats, void* cuda_stream)
+{
+    CT_CHECK(check_handle(A));
+    if (!params) return fail(CT_ERR_ARG, "NULL params");
+    if (batch < 1) return fail(CT_ERR_ARG, "batch must be >= 1");
+    int host = 0;
+    CT_CHECK(classify(f, u, &host));
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (!host) return split_bregman(A, params, f, u, batch, stats, st);
+    Workspace& w = A->ws;
+    const int64_t nx = A->cols * batch, ny = A->rows * batch;
+    CT_CHECK(ensure_stage(&w.stage_a, &w.stage_a_len, nx));
+    CT_CHECK(ensure_stage(&w.stage_b, &w.stage_b_len, ny));
+    CT_CUDA(cudaMemcpyAsync(w.stage_b, f, ny * sizeof(float), cudaMemcpyHostToDevice, st));
+    CT_CUDA(cudaMemcpyAsync(w.stage_a, u, nx * sizeof(float), cudaMemcpyHostToDevice, st));
+    int rc = split_bregman(A, params, w.stage_b, w.stage_a, batch, stats, st);
+    if (rc != CT_OK && rc != CT_ERR_BREAKDOWN && rc != CT_ERR_NONFINITE) return rc;
+    CT_CUDA(cudaMemcpyAsync(u, w.stage_a, nx * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CT_CUDA(cudaStreamSynchronize(st));
+    return rc;
+}
+
+int ct_matrix_export(ct_matrix_t A, int32_t which, int64_t* row_ptr, int32_t* cols, float* vals)
+{
+    CT_CHECK(check_handle(A));
+    if (which != 0 && which != 1) return fail(CT_ERR_ARG, "which must be 0 (A) or 1 (A^T)");
+    if (!row_ptr || !cols || !vals) return fail(CT_ERR_ARG, "NULL output array");
+    const Csr& C = which == 0 ? A->A : A->At;
+    std::vector<int64_t> rp(C.rows + 1);
+    std::vector<int32_t> len(C.rows), col(C.nnz_pad);
+    std::vector<float> val(C.nnz_pad);
+    std::vector<uint16_t> q;
+    std::vector<float> s;
+    CT_CUDA(cudaMemcpy(rp.data(), C.row_ptr, rp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    CT_CUDA(cudaMemcpy(len.data(), C.row_len, len.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CT_CUDA(cudaMemcpy(col.data(), C.col, col.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    const bool f16 = (A->flags & CT_VAL_FP16_ROWSCALE) != 0;
+    if (f16) {
+        q.resize(C.nnz_pad);
+        s.resize(A->rows);
+        CT_CUDA(cudaMemcpy(q.data(), C.qval, q.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+        CT_CUDA(cudaMemcpy(s.data(), A->row_scale, s.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    } else {
+        CT_CUDA(cudaMemcpy(val.data(), C.val, val.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    }
+    int64_t o = 0;
+    row_ptr[0] = 0;
+    for (int64_t r = 0; r < C.rows; ++r) {
+        for (int64_t k = rp[r]; k < rp[r] + len[r]; ++k, ++o) {
+            cols[o] = col[k];
+            if (f16) {
+                __half_raw hr;
+                hr.x = q[k];
+                const float qf = __half2float(__half(hr));
+                vals[o] = qf * s[which == 0 ? r : col[k]];
+            } else {
+                vals[o] = val[k];
+            }
+        }
+        row_ptr[r + 1] = o;
+    }
+    return CT_OK;
+}
+
+int ct_matrix_export_fp16(ct_matrix_t A, uint16_t* q_bits, float* scale)
+{
+    CT_CHECK(check_handle(A));
+    if (!(A->flags & CT_VAL_FP16_ROWSCALE)) return fail(CT_ERR_UNSUPPORTED, "matrix has no FP16 storage");
+    if (!q_bits || !scale) return fail(CT_ERR_ARG, "NULL output array");
+    const Csr& C = A->A;
+    std::vector<int64_t> rp(C.rows + 1);
+    std::vector<int32_t> len(C.rows);
+    std::vector<uint16_t> q(C.nnz_pad);
+    CT_CUDA(cudaMemcpy(rp.data(), C.row_ptr, rp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    CT_CUDA(cudaMemcpy(len.data(), C.row_len, len.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CT_CUDA(cudaMemcpy(q.data(), C.qval, q.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+    CT_CUDA(cudaMemcpy(scale, A->row_scale, A->rows * sizeof(float), cudaMemcpyDeviceToHost));
+    int64_t o = 0;
+    for (int64_t r = 0; r < C.rows; ++r)
+        for (int64_t k = rp[r]; k < rp[r] + len[r]; ++k) q_bits[o++] = q[k];
+    return CT_OK;
+}
+
+int ct_surrogate_stencil(ct_matrix_t A, int32_t r, int32_t square, int32_t capacity, int32_t* di,
+                         int32_t* dj, double* val, int32_t* count)
+{
+    CT_CHECK(check_handle(A));
+    if (!count) return fail(CT_ERR_ARG, "NULL count");
+    Stencil* S = nullptr;
+    CT_CHECK(make_stencil(A, r, square, &S));
+    *count = S->ntaps;
+    if (capacity < S->ntaps) return fail(CT_ERR_ARG, "capacity below the number of taps");
+    if (!di || !dj || !val) return fail(CT_ERR_ARG, "NULL output array");
+    for (int t = 0; t < S->ntaps; ++t) {
+        di[t] = S->h_di[t];
+        dj[t] = S->h_dj[t];
+        val[t] = S->h_w[t];
+    }
+    return CT_OK;
+}
+
+const char* ct_status_string(int status)
+{
+    switch (status) {
+    case CT_OK: return "ok";
+    case CT_ERR_ARG: return "invalid argument";
+    case CT_ERR_CUDA: return "CUDA error";
+    case CT_ERR_OOM: return "out of memory";
+    case CT_ERR_BREAKDOWN: return "CG breakdown (operator not positive definite)";
+    case CT_ERR_NONFINITE: return "non-finite value";
+    case CT_ERR_TIMEOUT: return "device wait timed out";
+    case CT_ERR_UNSUPPORTED: return "unsupported option";
+    default: return "unknown status";
+    }
+}
+
+const char* ct_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,174 @@
+// Internal declarations of libct (CUDA, sm_103a).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "ct.h"
+
+namespace ct {
+
+// Rows of both CSR matrices are padded to a multiple of this many entries so
+// that every row starts on a 16-byte boundary for int32/FP32 (and FP16) vector
+// loads; padding entries repeat the row's last column with value 0.
+constexpr int kRowPad = 8;
+
+// ---------------------------------------------------------------------------
+// error reporting
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define CT_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return ::ct::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define CT_CHECK(expr)                 \
+    do {                               \
+        int rc_ = (expr);              \
+        if (rc_ != CT_OK) return rc_;  \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device data
+// ---------------------------------------------------------------------------
+struct Csr {
+    int64_t rows = 0, cols = 0;
+    int64_t nnz = 0;       // stored nonzeros
+    int64_t nnz_pad = 0;   // entries including row padding
+    int64_t* row_ptr = nullptr;  // [rows+1] padded offsets
+    int32_t* row_len = nullptr;  // [rows] unpadded lengths
+    int32_t* col = nullptr;      // [nnz_pad]
+    float* val = nullptr;        // [nnz_pad] FP32 values (may be null)
+    __half* qval = nullptr;      // [nnz_pad] FP16 Q values (may be null)
+};
+
+// Per-slice conjugate-gradient scalars, resident on the device.
+struct CgSlice {
+    double rr;      // r.r of the current residual
+    double rhs2;    // rhs.rhs
+    double alpha;   // step of the current iteration
+    double beta;    // rr_new / rr
+    int32_t active; // 1 while the slice keeps iterating
+    int32_t iters;  // steps taken
+    int32_t status; // CT_OK / CT_ERR_BREAKDOWN / CT_ERR_NONFINITE
+    int32_t pad;
+};
+
+// Per-slice split-Bregman scalars.
+struct SbSlice {
+    double first_upd;
+    double last_upd;
+    int32_t outer_done;
+    int32_t stopped;
+    int32_t status;
+    int32_t pad;
+};
+
+struct Stencil {
+    int ntaps = 0;
+    int r = 0;
+    int32_t* d = nullptr;  // device [ntaps][2] offsets (di, dj)
+    float* w = nullptr;    // device [ntaps] FP32 taps
+    std::vector<int32_t> h_di, h_dj;
+    std::vector<double> h_w;  // FP64 taps (host copy)
+};
+
+struct Workspace {
+    int device = -1;
+    int32_t batch = 0;
+    int64_t n2 = 0, rows = 0;
+    // vectors [len][batch]
+    float *y = nullptr;  // sinogram temp
+    float *r = nullptr, *p = nullptr, *q = nullptr;
+    float *atf = nullptr, *u_old = nullptr, *bx = nullptr, *by = nullptr, *vx = nullptr, *vy = nullptr;
+    double* partials = nullptr;  // reduction partials
+    int64_t partials_len = 0;
+    unsigned* counter = nullptr; // last-block counter (one per workspace)
+    CgSlice* cg = nullptr;
+    SbSlice* sb = nullptr;
+    // staging for host pointers
+    float *stage_a = nullptr, *stage_b = nullptr;
+    int64_t stage_a_len = 0, stage_b_len = 0;
+    cudaStream_t cap_stream = nullptr;
+};
+
+}  // namespace ct
+
+struct ct_matrix {
+    ct_geometry g{};
+    uint32_t flags = 0;
+    int device = 0;
+    int sm_count = 0;
+    int n_kept = 0;
+    int64_t rows = 0, cols = 0;
+    double* dirs = nullptr;  // device [n_kept][2]: cos, sin
+    std::vector<double> h_cos, h_sin;
+    ct::Csr A, At;
+    float* row_scale = nullptr;  // FP16 form: s [rows]
+    std::map<std::pair<int, int>, ct::Stencil> stencils;
+    ct::Workspace ws;
+};
+
+namespace ct {
+
+// build.cu
+int build_matrices(ct_matrix* M);
+void free_csr(Csr& c);
+int make_stencil(ct_matrix* M, int r, int square, Stencil** out);
+void free_stencil(Stencil& s);
+
+// workspace.cu (in solve.cu)
+int ensure_workspace(ct_matrix* M, int32_t batch, bool solver);
+void free_workspace(Workspace& w);
+
+// spmv.cu
+enum class ValKind { F32 = 0, F16 = 1 };
+int launch_forward(const ct_matrix* M, ValKind vk, const float* x, float* y, int32_t batch,
+                   float out_scale, bool scale_sq, cudaStream_t st);
+int launch_adjoint(const ct_matrix* M, ValKind vk, const float* y, float* x, int32_t batch,
+                   float out_scale, bool scale_y, cudaStream_t st);
+
+// Epilogue of the adjoint product inside the CG operator.
+struct OpEpilogue {
+    int mode;             // 1: q = Op(p) and p.q partial; 2: residual r = rhs - Op(u), p = r
+    float c_id, c_ata, c_grad;
+    const float* in;      // p (mode 1) or u (mode 2)
+    float* out;           // q (mode 1) or r (mode 2)
+    float* p_out;         // mode 2: p = r
+    const float* rhs;     // mode 2: explicit rhs, or null to build it as atf + lambda grad^T v
+    const float* atf;     // mode 2 (SB): alpha A^T f
+    const float* vx;      // mode 2 (SB): v = d - b
+    const float* vy;
+    float lam;
+    const int32_t* gate;  // optional: skip all work when *gate != 0 (stopped SB)
+    CgSlice* cg;
+    double* partials;
+    unsigned* counter;
+    double tol;
+};
+int launch_adjoint_op(const ct_matrix* M, ValKind vk, const float* y, int32_t batch,
+                      const OpEpilogue& ep, cudaStream_t st);
+int launch_forward_gated(const ct_matrix* M, ValKind vk, const float* x, float* y, int32_t batch,
+                         bool normal_scale, const CgSlice* cg, const int32_t* gate, cudaStream_t st);
+int launch_stencil_op(const ct_matrix* M, const Stencil* S, int32_t batch, const OpEpilogue& ep,
+                      cudaStream_t st);
+
+// solve.cu
+int cg_solve(ct_matrix* M, const ct_cg_params* P, const float* rhs, float* u, int32_t batch,
+             ct_cg_stats* stats, cudaStream_t st);
+int split_bregman(ct_matrix* M, const ct_sb_params* P, const float* f, float* u, int32_t batch,
+                  ct_sb_stats* stats, cudaStream_t st);
+
+int grid_for(const ct_matrix* M, int64_t work_items, int items_per_block, int max_per_sm);
+
+}  // namespace ct

@@ -1,0 +1,148 @@
+// Deterministic FP64 block reductions and the conjugate-gradient scalar
+// updates that follow them.  Included by the kernel translation units.
+#pragma once
+
+#include "ct_internal.cuh"
+
+namespace ct {
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Reduces NQ per-thread FP64 values over the block (fixed order), writes the
+// block's partials, and lets the last block to finish sum all partials (fixed
+// order).  Returns true in thread 0 of the last block, with the grid totals
+// in tot[].  The counter is reset by the last block.  blockDim.x <= 1024.
+template <int NQ>
+__device__ bool grid_reduce_last(const double (&v)[NQ], double* partials, unsigned* counter,
+                                 double (&tot)[NQ])
+{
+    __shared__ double sh[NQ][32];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarp = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double s = warp_sum_d(v[q]);
+        if (lane == 0) sh[q][warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < nwarp; ++w) s += sh[q][w];
+            partials[(size_t)q * gridDim.x + blockIdx.x] = s;
+        }
+        __threadfence();
+        unsigned prev = atomicAdd(counter, 1u);
+        last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double s = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+            s += __ldcg(partials + (size_t)q * gridDim.x + b);
+        s = warp_sum_d(s);
+        if (lane == 0) sh[q][warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < nwarp; ++w) s += sh[q][w];
+            tot[q] = s;
+        }
+        *counter = 0u;
+    }
+    return threadIdx.x == 0;
+}
+
+__device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
+
+// r0 = rhs - Op(u0) has been formed: start the iteration.
+__device__ __forceinline__ void cg_after_residual(CgSlice& st, double rr, double rhs2, double tol)
+{
+    st.rr = rr;
+    st.rhs2 = rhs2;
+    st.iters = 0;
+    st.alpha = 0.0;
+    st.beta = 0.0;
+    st.status = CT_OK;
+    if (!finite_d(rr) || !finite_d(rhs2)) {
+        st.status = CT_ERR_NONFINITE;
+        st.active = 0;
+        return;
+    }
+    st.active = (rr > 0.0) && !(tol > 0.0 && sqrt(rr) <= tol * sqrt(rhs2));
+}
+
+// q = Op(p) and p.q are known: the step length.
+__device__ __forceinline__ void cg_after_pq(CgSlice& st, double pq)
+{
+    if (!st.active) {
+        st.alpha = 0.0;
+        return;
+    }
+    if (!finite_d(pq)) {
+        st.status = CT_ERR_NONFINITE;
+        st.active = 0;
+        st.alpha = 0.0;
+    } else if (!(pq > 0.0)) {
+        st.status = CT_ERR_BREAKDOWN;
+        st.active = 0;
+        st.alpha = 0.0;
+    } else {
+        st.alpha = st.rr / pq;
+    }
+}
+
+// u += alpha p, r -= alpha q done and r.r known: the new search direction's beta.
+__device__ __forceinline__ void cg_after_update(CgSlice& st, double rr_new, double tol)
+{
+    if (!st.active) {
+        st.beta = 0.0;
+        return;
+    }
+    st.iters += 1;
+    st.beta = rr_new / st.rr;
+    st.rr = rr_new;
+    if (!finite_d(rr_new)) {
+        st.status = CT_ERR_NONFINITE;
+        st.active = 0;
+    } else if (rr_new == 0.0 || (tol > 0.0 && sqrt(rr_new) <= tol * sqrt(st.rhs2))) {
+        st.active = 0;
+    }
+}
+
+// One Bregman update finished with ||u^{k+1} - u^k||_1 = upd.
+__device__ __forceinline__ void sb_after_update(SbSlice& sb, double upd, double tol)
+{
+    if (sb.stopped) return;
+    if (!finite_d(upd)) {
+        sb.status = CT_ERR_NONFINITE;
+        sb.stopped = 1;
+        return;
+    }
+    if (sb.outer_done == 0) sb.first_upd = upd;
+    sb.last_upd = upd;
+    sb.outer_done += 1;
+    if (tol > 0.0 && upd < tol * sb.first_upd) sb.stopped = 1;
+}
+
+}  // namespace ct

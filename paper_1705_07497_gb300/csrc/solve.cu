@@ -1,0 +1,345 @@
+// Conjugate gradients for (c_id I + c_ata A^T A + c_grad grad^T grad) u = rhs
+// (Eqs. KKT, PD_resolve, SB_solve) and anisotropic-TV split Bregman (Sec. 4),
+// with every scalar kept on the device so that a whole reconstruction is one
+// stream of kernels (captured as a CUDA graph per Bregman update) and the host
+// never waits inside the loop.
+//
+// One CG step is four kernels: y = A p; q = Op(p) fused into the A^T product
+// (with p.q); u += alpha p, r -= alpha q (with r.r); p = r + beta p.  FP32
+// vectors, FP64 dot products; each reduction is finished by the last block of
+// its kernel in a fixed order, so results are bitwise reproducible.
+#include <cstring>
+
+#include "ct_internal.cuh"
+#include "reduce.cuh"
+
+namespace ct {
+namespace {
+
+__global__ void __launch_bounds__(256) cg_update_kernel(float* __restrict__ u, float* __restrict__ r,
+                                                        const float* __restrict__ p,
+                                                        const float* __restrict__ q, int64_t len,
+                                                        CgSlice* cg, double tol, double* partials,
+                                                        unsigned* counter, const int32_t* gate)
+{
+    if (gate && *gate) return;
+    if (!cg->active) return;
+    const float al = (float)cg->alpha;
+    double d = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        u[i] = fmaf(al, p[i], u[i]);
+        const float rn = fmaf(-al, q[i], r[i]);
+        r[i] = rn;
+        d += (double)rn * (double)rn;
+    }
+    double v[1] = {d}, tot[1];
+    if (grid_reduce_last<1>(v, partials, counter, tot)) cg_after_update(*cg, tot[0], tol);
+}
+
+__global__ void __launch_bounds__(256) cg_direction_kernel(float* __restrict__ p,
+                                                           const float* __restrict__ r, int64_t len,
+                                                           const CgSlice* cg, const int32_t* gate)
+{
+    if (gate && *gate) return;
+    if (!cg->active) return;
+    const float be = (float)cg->beta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = fmaf(be, p[i], r[i]);
+}
+
+// After the inner solve: g = grad u, d = shrink(g + b, 1/lambda), b += g - d,
+// v = d - b (the next right-hand side's split term), ||u - u_old||_1, u_old = u.
+__global__ void __launch_bounds__(256) sb_shrink_kernel(const float* __restrict__ u,
+                                                        float* __restrict__ u_old,
+                                                        float* __restrict__ bx, float* __restrict__ by,
+                                                        float* __restrict__ vx, float* __restrict__ vy,
+                                                        int n, float gamma, SbSlice* sb,
+                                                        const CgSlice* cg, double tol,
+                                                        double* partials, unsigned* counter)
+{
+    if (sb->stopped) return;
+    const int64_t n2 = (int64_t)n * n;
+    double upd = 0.0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(p / n), j = (int)(p - (int64_t)i * n);
+        const float c = u[p];
+        const float gx = (j < n - 1) ? u[p + 1] - c : 0.0f;
+        const float gy = (i < n - 1) ? u[p + n] - c : 0.0f;
+        const float tx = gx + bx[p], ty = gy + by[p];
+        const float dx = copysignf(fmaxf(fabsf(tx) - gamma, 0.0f), tx);
+        const float dy = copysignf(fmaxf(fabsf(ty) - gamma, 0.0f), ty);
+        const float bxn = tx - dx, byn = ty - dy;
+        bx[p] = bxn;
+        by[p] = byn;
+        vx[p] = dx - bxn;
+        vy[p] = dy - byn;
+        upd += fabs((double)c - (double)u_old[p]);
+        u_old[p] = c;
+    }
+    double v[1] = {upd}, tot[1];
+    if (grid_reduce_last<1>(v, partials, counter, tot)) {
+        if (cg->status != CT_OK) {
+            sb->status = cg->status;
+            sb->stopped = 1;
+        } else {
+            sb_after_update(*sb, tot[0], tol);
+        }
+    }
+}
+
+int alloc_f(float** p, int64_t n)
+{
+    cudaError_t e = cudaMalloc((void**)p, (size_t)(n > 0 ? n : 1) * sizeof(float));
+    if (e == cudaErrorMemoryAllocation) {
+        (void)cudaGetLastError();
+        return fail(CT_ERR_OOM, "workspace allocation failed");
+    }
+    CT_CUDA(e);
+    return CT_OK;
+}
+
+struct Plan {
+    ct_matrix* M;
+    ValKind vk;
+    bool sparse;       // A^T A through the sparse products (else stencil / none)
+    const Stencil* S;  // surrogate stencil, or null
+    OpEpilogue base;
+    int64_t n2;
+    int refresh;       // residual replacement period (FP16 storage), 0 = off
+};
+
+// Op applied to `in` with the given epilogue (y = A in, then A^T y fused).
+int apply_op(const Plan& P, OpEpilogue ep, const float* in, cudaStream_t st, bool fp32_refresh = false)
+{
+    Workspace& w = P.M->ws;
+    ep.in = in;
+    const bool sparse = P.sparse;
+    if (sparse) {
+        const ValKind vk = fp32_refresh ? ValKind::F32 : P.vk;
+        CT_CHECK(launch_forward_gated(P.M, vk, in, w.y, 1, true,
+                                      ep.mode == 2 ? nullptr : ep.cg, ep.gate, st));
+        CT_CHECK(launch_adjoint_op(P.M, vk, w.y, 1, ep, st));
+    } else {
+        CT_CHECK(launch_stencil_op(P.M, P.S, 1, ep, st));
+    }
+    return CT_OK;
+}
+
+// Residual r = rhs - Op(u), p = r, then `iters` CG steps.
+int enqueue_cg(const Plan& P, const float* rhs, float* u, int iters, cudaStream_t st)
+{
+    Workspace& w = P.M->ws;
+    OpEpilogue ep = P.base;
+    ep.mode = 2;
+    ep.out = w.r;
+    ep.p_out = w.p;
+    ep.rhs = rhs;
+    CT_CHECK(apply_op(P, ep, u, st));
+    const int gv = grid_for(P.M, P.n2, 256, 8);
+    for (int it = 0; it < iters; ++it) {
+        OpEpilogue e1 = P.base;
+        e1.mode = 1;
+        e1.out = w.q;
+        CT_CHECK(apply_op(P, e1, w.p, st));
+        cg_update_kernel<<<gv, 256, 0, st>>>(u, w.r, w.p, w.q, P.n2, w.cg, P.base.tol, w.partials,
+                                             w.counter, P.base.gate);
+        CT_CUDA(cudaGetLastError());
+        cg_direction_kernel<<<gv, 256, 0, st>>>(w.p, w.r, P.n2, w.cg, P.base.gate);
+        CT_CUDA(cudaGetLastError());
+        if (P.refresh > 0 && (it + 1) % P.refresh == 0 && it + 1 < iters) {
+            OpEpilogue e3 = P.base;
+            e3.mode = 3;
+            e3.out = w.r;
+            e3.rhs = rhs;
+            CT_CHECK(apply_op(P, e3, u, st, true));
+        }
+    }
+    return CT_OK;
+}
+
+int make_plan(ct_matrix* M, double c_id, double c_ata, double c_grad, double tol, int surr_r,
+              int surr_square, int refresh, Plan& P)
+{
+    P.M = M;
+    P.vk = (M->flags & CT_VAL_FP16_ROWSCALE) ? ValKind::F16 : ValKind::F32;
+    P.S = nullptr;
+    if (surr_r > 0) {
+        Stencil* S = nullptr;
+        CT_CHECK(make_stencil(M, surr_r, surr_square, &S));
+        P.S = S;
+    }
+    P.sparse = (c_ata != 0.0) && P.S == nullptr;
+    if (c_ata == 0.0) P.S = nullptr;
+    P.n2 = (int64_t)M->g.n * M->g.n;
+    if (refresh > 0) {
+        if (P.vk != ValKind::F16 || !M->A.val)
+            return fail(CT_ERR_UNSUPPORTED,
+                        "refresh_every needs FP16 storage built with CT_KEEP_FP32_COPY");
+        if (!P.sparse) refresh = 0;
+    }
+    P.refresh = refresh;
+    Workspace& w = M->ws;
+    OpEpilogue& b = P.base;
+    std::memset(&b, 0, sizeof(b));
+    b.c_id = (float)c_id;
+    b.c_ata = (float)c_ata;
+    b.c_grad = (float)c_grad;
+    b.cg = w.cg;
+    b.partials = w.partials;
+    b.counter = w.counter;
+    b.tol = tol;
+    return CT_OK;
+}
+
+}  // namespace
+
+void free_workspace(Workspace& w)
+{
+    float* fs[] = {w.y, w.r, w.p, w.q, w.atf, w.u_old, w.bx, w.by, w.vx, w.vy, w.stage_a, w.stage_b};
+    for (float* f : fs) cudaFree(f);
+    cudaFree(w.partials);
+    cudaFree(w.counter);
+    cudaFree(w.cg);
+    cudaFree(w.sb);
+    if (w.cap_stream) cudaStreamDestroy(w.cap_stream);
+    w = Workspace{};
+}
+
+int ensure_workspace(ct_matrix* M, int32_t batch, bool /*solver*/)
+{
+    Workspace& w = M->ws;
+    if (w.batch >= batch && w.r) return CT_OK;
+    CT_CUDA(cudaDeviceSynchronize());
+    cudaStream_t keep = w.cap_stream;
+    w.cap_stream = nullptr;
+    free_workspace(w);
+    w.cap_stream = keep;
+    w.batch = batch;
+    w.n2 = M->cols;
+    w.rows = M->rows;
+    const int64_t nv = w.n2 * batch;
+    CT_CHECK(alloc_f(&w.y, w.rows * batch));
+    float** vs[] = {&w.r, &w.p, &w.q, &w.atf, &w.u_old, &w.bx, &w.by, &w.vx, &w.vy};
+    for (float** v : vs) CT_CHECK(alloc_f(v, nv));
+    w.partials_len = (int64_t)4 * (M->sm_count > 0 ? M->sm_count : 148) * 8 * batch;
+    CT_CUDA(cudaMalloc((void**)&w.partials, w.partials_len * sizeof(double)));
+    CT_CUDA(cudaMalloc((void**)&w.counter, 64));
+    CT_CUDA(cudaMemset(w.counter, 0, 64));
+    CT_CUDA(cudaMalloc((void**)&w.cg, sizeof(CgSlice) * batch));
+    CT_CUDA(cudaMemset(w.cg, 0, sizeof(CgSlice) * batch));
+    CT_CUDA(cudaMalloc((void**)&w.sb, sizeof(SbSlice) * batch));
+    CT_CUDA(cudaMemset(w.sb, 0, sizeof(SbSlice) * batch));
+    if (!w.cap_stream) CT_CUDA(cudaStreamCreateWithFlags(&w.cap_stream, cudaStreamNonBlocking));
+    return CT_OK;
+}
+
+int cg_solve(ct_matrix* M, const ct_cg_params* Pp, const float* rhs, float* u, int32_t batch,
+             ct_cg_stats* stats, cudaStream_t st)
+{
+    if (batch != 1) return fail(CT_ERR_UNSUPPORTED, "ct_cg_solve: batch > 1 is not available yet");
+    if (Pp->max_iters < 0) return fail(CT_ERR_ARG, "max_iters < 0");
+    CT_CHECK(ensure_workspace(M, batch, true));
+    Plan P;
+    CT_CHECK(make_plan(M, Pp->c_id, Pp->c_ata, Pp->c_grad, Pp->rel_tol, Pp->surrogate_r,
+                       Pp->surrogate_square, Pp->refresh_every, P));
+    CT_CHECK(enqueue_cg(P, rhs, u, Pp->max_iters, st));
+    if (stats) {
+        CgSlice h;
+        CT_CUDA(cudaMemcpyAsync(&h, M->ws.cg, sizeof(h), cudaMemcpyDeviceToHost, st));
+        CT_CUDA(cudaStreamSynchronize(st));
+        stats->iters = h.iters;
+        stats->final_rel_res = h.rhs2 > 0 ? std::sqrt(h.rr / h.rhs2) : 0.0;
+        stats->status = h.status;
+        if (h.status != CT_OK)
+            return fail(h.status, h.status == CT_ERR_BREAKDOWN ? "CG breakdown: p^T Op p <= 0"
+                                                               : "non-finite value in CG");
+    }
+    return CT_OK;
+}
+
+namespace {
+
+int enqueue_sb_outer(const Plan& P, float* u, const ct_sb_params* Sp, cudaStream_t st)
+{
+    Workspace& w = P.M->ws;
+    CT_CHECK(enqueue_cg(P, nullptr, u, Sp->inner_cg_iters, st));
+    const int gv = grid_for(P.M, P.n2, 256, 8);
+    sb_shrink_kernel<<<gv, 256, 0, st>>>(u, w.u_old, w.bx, w.by, w.vx, w.vy, P.M->g.n,
+                                         (float)(1.0 / Sp->lambda), w.sb, w.cg, Sp->stop_rel_update,
+                                         w.partials, w.counter);
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+}  // namespace
+
+int split_bregman(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u, int32_t batch,
+                  ct_sb_stats* stats, cudaStream_t st)
+{
+    if (batch != 1) return fail(CT_ERR_UNSUPPORTED, "ct_split_bregman: batch > 1 is not available yet");
+    if (!(Sp->lambda > 0.0) || Sp->outer_iters < 0 || Sp->inner_cg_iters < 0)
+        return fail(CT_ERR_ARG, "split Bregman needs lambda > 0 and non-negative iteration counts");
+    CT_CHECK(ensure_workspace(M, batch, true));
+    Workspace& w = M->ws;
+    Plan P;
+    CT_CHECK(make_plan(M, 0.0, Sp->alpha, Sp->lambda, 0.0, Sp->surrogate_r, Sp->surrogate_square,
+                       Sp->refresh_every, P));
+    P.base.gate = &w.sb->stopped;
+    P.base.atf = w.atf;
+    P.base.vx = w.vx;
+    P.base.vy = w.vy;
+    P.base.lam = (float)Sp->lambda;
+    const int64_t n2 = P.n2;
+    // alpha A^T f, once (the right-hand side keeps the exact back-projection
+    // also with the surrogate, Eq. surr_SBupd)
+    CT_CHECK(launch_adjoint(M, P.vk, f, w.atf, 1, (float)Sp->alpha, true, st));
+    CT_CUDA(cudaMemsetAsync(w.bx, 0, n2 * sizeof(float), st));
+    CT_CUDA(cudaMemsetAsync(w.by, 0, n2 * sizeof(float), st));
+    CT_CUDA(cudaMemsetAsync(w.vx, 0, n2 * sizeof(float), st));
+    CT_CUDA(cudaMemsetAsync(w.vy, 0, n2 * sizeof(float), st));
+    CT_CUDA(cudaMemsetAsync(w.sb, 0, sizeof(SbSlice), st));
+    CT_CUDA(cudaMemcpyAsync(w.u_old, u, n2 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CT_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone || Sp->outer_iters <= 2) {
+        for (int k = 0; k < Sp->outer_iters; ++k) CT_CHECK(enqueue_sb_outer(P, u, Sp, st));
+    } else {
+        // capture one Bregman update and replay it
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        CT_CUDA(cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_sb_outer(P, u, Sp, w.cap_stream);
+        cudaError_t e = cudaStreamEndCapture(w.cap_stream, &graph);
+        if (rc != CT_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        CT_CUDA(e);
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CT_CUDA(e);
+        for (int k = 0; k < Sp->outer_iters; ++k) {
+            e = cudaGraphLaunch(exec, st);
+            if (e != cudaSuccess) break;
+        }
+        cudaGraphExecDestroy(exec);
+        CT_CUDA(e);
+    }
+    if (stats) {
+        SbSlice h;
+        CT_CUDA(cudaMemcpyAsync(&h, w.sb, sizeof(h), cudaMemcpyDeviceToHost, st));
+        CT_CUDA(cudaStreamSynchronize(st));
+        stats->outer_done = h.outer_done;
+        stats->first_update_l1 = h.first_upd;
+        stats->last_update_l1 = h.last_upd;
+        stats->status = h.status;
+        if (stats->status != CT_OK) return fail(stats->status, "split Bregman inner solve failed");
+    }
+    return CT_OK;
+}
+
+}  // namespace ct

@@ -1,0 +1,312 @@
+"""ctypes binding of libct (the C ABI declared in include/ct.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Vectors may be torch tensors (CUDA or CPU) or numpy arrays; they
+must be float32 and contiguous.  CUDA tensors are used in place on the
+current torch stream of their device; host buffers go through the library's
+synchronous staging path.  There is no CPU fallback: if libct.so is missing
+the first call raises.
+
+The module-level ``ct_*`` functions mirror the C entry points one to one;
+``Matrix`` is a small convenience wrapper around a matrix handle.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libct.so")
+
+CT_OK = 0
+CT_ERR_ARG = -1
+CT_ERR_CUDA = -2
+CT_ERR_OOM = -3
+CT_ERR_BREAKDOWN = -4
+CT_ERR_NONFINITE = -5
+CT_ERR_TIMEOUT = -6
+CT_ERR_UNSUPPORTED = -7
+
+CT_VAL_FP32 = 0
+CT_VAL_FP16_ROWSCALE = 1
+CT_KEEP_FP32_COPY = 4
+
+SYMBOLS = (
+    "ct_build_matrix",
+    "ct_matrix_info",
+    "ct_destroy_matrix",
+    "ct_forward",
+    "ct_adjoint",
+    "ct_cg_solve",
+    "ct_split_bregman",
+    "ct_matrix_export",
+    "ct_matrix_export_fp16",
+    "ct_surrogate_stencil",
+    "ct_status_string",
+    "ct_last_error",
+)
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32),
+        ("n_angles_total", ctypes.c_int32),
+        ("keep_every", ctypes.c_int32),
+        ("n_bins", ctypes.c_int32),
+    ]
+
+
+class CgParams(ctypes.Structure):
+    _fields_ = [
+        ("c_id", ctypes.c_double),
+        ("c_ata", ctypes.c_double),
+        ("c_grad", ctypes.c_double),
+        ("max_iters", ctypes.c_int32),
+        ("rel_tol", ctypes.c_double),
+        ("surrogate_r", ctypes.c_int32),
+        ("refresh_every", ctypes.c_int32),
+        ("surrogate_square", ctypes.c_int32),
+    ]
+
+
+class CgStats(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int32),
+        ("final_rel_res", ctypes.c_double),
+        ("status", ctypes.c_int32),
+    ]
+
+
+class SbParams(ctypes.Structure):
+    _fields_ = [
+        ("alpha", ctypes.c_double),
+        ("lambda_", ctypes.c_double),
+        ("outer_iters", ctypes.c_int32),
+        ("inner_cg_iters", ctypes.c_int32),
+        ("stop_rel_update", ctypes.c_double),
+        ("surrogate_r", ctypes.c_int32),
+        ("refresh_every", ctypes.c_int32),
+        ("surrogate_square", ctypes.c_int32),
+    ]
+
+
+class SbStats(ctypes.Structure):
+    _fields_ = [
+        ("outer_done", ctypes.c_int32),
+        ("first_update_l1", ctypes.c_double),
+        ("last_update_l1", ctypes.c_double),
+        ("status", ctypes.c_int32),
+    ]
+
+
+class CtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (status_string(code), code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Loads libct.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                "libct.so not found at %s; build it with __graft_entry__.build()" % LIB_PATH
+            )
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+        P = ctypes.POINTER
+        L.ct_build_matrix.argtypes = [P(Geometry), u32, P(vp)]
+        L.ct_matrix_info.argtypes = [vp, P(i64), P(i64), P(i64)]
+        L.ct_destroy_matrix.argtypes = [vp]
+        L.ct_destroy_matrix.restype = None
+        L.ct_forward.argtypes = [vp, vp, vp, i32, vp]
+        L.ct_adjoint.argtypes = [vp, vp, vp, i32, vp]
+        L.ct_cg_solve.argtypes = [vp, P(CgParams), vp, vp, i32, P(CgStats), vp]
+        L.ct_split_bregman.argtypes = [vp, P(SbParams), vp, vp, i32, P(SbStats), vp]
+        L.ct_matrix_export.argtypes = [vp, i32, vp, vp, vp]
+        L.ct_matrix_export_fp16.argtypes = [vp, vp, vp]
+        L.ct_surrogate_stencil.argtypes = [vp, i32, i32, i32, vp, vp, vp, P(i32)]
+        L.ct_status_string.argtypes = [ctypes.c_int]
+        L.ct_status_string.restype = ctypes.c_char_p
+        L.ct_last_error.argtypes = []
+        L.ct_last_error.restype = ctypes.c_char_p
+        for name in SYMBOLS:
+            if name not in ("ct_destroy_matrix", "ct_status_string", "ct_last_error"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def status_string(code):
+    return lib().ct_status_string(code).decode()
+
+
+def _check(code):
+    if code != CT_OK:
+        raise CtError(code, lib().ct_last_error().decode())
+    return code
+
+
+def _vec(x):
+    """(pointer, stream handle) of a float32 contiguous tensor or array."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(x, torch.Tensor):
+        if x.dtype != torch.float32 or not x.is_contiguous():
+            raise TypeError("expected a contiguous float32 tensor")
+        stream = torch.cuda.current_stream(x.device).cuda_stream if x.is_cuda else 0
+        return x.data_ptr(), stream
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float32 or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError("expected a C-contiguous float32 array")
+        return x.ctypes.data, 0
+    raise TypeError("expected a torch tensor or numpy array, got %r" % type(x))
+
+
+# ---------------------------------------------------------------------------
+# one-to-one mirrors of the C entry points
+# ---------------------------------------------------------------------------
+def ct_build_matrix(geometry, flags=0):
+    h = ctypes.c_void_p()
+    _check(lib().ct_build_matrix(ctypes.byref(geometry), flags, ctypes.byref(h)))
+    return h
+
+
+def ct_matrix_info(h):
+    r, c, z = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().ct_matrix_info(h, ctypes.byref(r), ctypes.byref(c), ctypes.byref(z)))
+    return r.value, c.value, z.value
+
+
+def ct_destroy_matrix(h):
+    lib().ct_destroy_matrix(h)
+
+
+def ct_forward(h, x, y, batch, stream=None):
+    px, sx = _vec(x)
+    py, _ = _vec(y)
+    return _check(lib().ct_forward(h, px, py, batch, sx if stream is None else stream))
+
+
+def ct_adjoint(h, y, x, batch, stream=None):
+    py, sy = _vec(y)
+    px, _ = _vec(x)
+    return _check(lib().ct_adjoint(h, py, px, batch, sy if stream is None else stream))
+
+
+def ct_cg_solve(h, params, rhs, u, batch, stats=None, stream=None):
+    pr, sr = _vec(rhs)
+    pu, _ = _vec(u)
+    sp = ctypes.byref(stats) if stats is not None else None
+    return _check(lib().ct_cg_solve(h, ctypes.byref(params), pr, pu, batch, sp, sr if stream is None else stream))
+
+
+def ct_split_bregman(h, params, f, u, batch, stats=None, stream=None):
+    pf, sf = _vec(f)
+    pu, _ = _vec(u)
+    sp = ctypes.byref(stats) if stats is not None else None
+    return _check(lib().ct_split_bregman(h, ctypes.byref(params), pf, pu, batch, sp, sf if stream is None else stream))
+
+
+def ct_matrix_export(h, which):
+    rows, cols, nnz = ct_matrix_info(h)
+    n_rows = rows if which == 0 else cols
+    rp = np.zeros(n_rows + 1, dtype=np.int64)
+    ci = np.zeros(nnz, dtype=np.int32)
+    va = np.zeros(nnz, dtype=np.float32)
+    _check(lib().ct_matrix_export(h, which, rp.ctypes.data, ci.ctypes.data, va.ctypes.data))
+    return rp, ci, va
+
+
+def ct_matrix_export_fp16(h):
+    rows, _, nnz = ct_matrix_info(h)
+    q = np.zeros(nnz, dtype=np.uint16)
+    s = np.zeros(rows, dtype=np.float32)
+    _check(lib().ct_matrix_export_fp16(h, q.ctypes.data, s.ctypes.data))
+    return q, s
+
+
+def ct_surrogate_stencil(h, r, square=False):
+    cnt = ctypes.c_int32()
+    lib().ct_surrogate_stencil(h, r, int(square), 0, None, None, None, ctypes.byref(cnt))
+    n = cnt.value
+    if n <= 0:
+        _check(CT_ERR_ARG)
+    di = np.zeros(n, dtype=np.int32)
+    dj = np.zeros(n, dtype=np.int32)
+    w = np.zeros(n, dtype=np.float64)
+    _check(lib().ct_surrogate_stencil(h, r, int(square), n, di.ctypes.data, dj.ctypes.data,
+                                      w.ctypes.data, ctypes.byref(cnt)))
+    return {(int(a), int(b)): float(v) for a, b, v in zip(di, dj, w)}
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+class Matrix:
+    """A = M R and A^T for one geometry, resident on the current CUDA device."""
+
+    def __init__(self, n, n_angles_total, keep_every, n_bins, flags=CT_VAL_FP32):
+        self.geometry = Geometry(n, n_angles_total, keep_every, n_bins)
+        self.flags = flags
+        self.handle = ct_build_matrix(self.geometry, flags)
+        self.rows, self.cols, self.nnz = ct_matrix_info(self.handle)
+        self.n = n
+
+    def close(self):
+        if self.handle is not None:
+            ct_destroy_matrix(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _batch(self, x, length):
+        total = int(np.prod(x.shape))
+        if total % length:
+            raise ValueError("vector size %d is not a multiple of %d" % (total, length))
+        return total // length
+
+    def forward(self, x, y):
+        ct_forward(self.handle, x, y, self._batch(x, self.cols))
+        return y
+
+    def adjoint(self, y, x):
+        ct_adjoint(self.handle, y, x, self._batch(y, self.rows))
+        return x
+
+    def cg_solve(self, rhs, u, c_id, c_ata, c_grad, max_iters, rel_tol=0.0, surrogate_r=0,
+                 refresh_every=0, square=False):
+        p = CgParams(c_id, c_ata, c_grad, max_iters, rel_tol, surrogate_r, refresh_every, int(square))
+        st = CgStats()
+        ct_cg_solve(self.handle, p, rhs, u, self._batch(u, self.cols), st)
+        return {"iters": st.iters, "final_rel_res": st.final_rel_res, "status": st.status}
+
+    def split_bregman(self, f, u, alpha, lam, outer, inner, stop_rel_update=0.0, surrogate_r=0,
+                      refresh_every=0, square=False, stats=True):
+        p = SbParams(alpha, lam, outer, inner, stop_rel_update, surrogate_r, refresh_every, int(square))
+        st = SbStats() if stats else None
+        ct_split_bregman(self.handle, p, f, u, self._batch(u, self.cols), st)
+        if st is None:
+            return None
+        return {"outer_done": st.outer_done, "first_update_l1": st.first_update_l1,
+                "last_update_l1": st.last_update_l1, "status": st.status}
+
+    def export(self, which=0):
+        return ct_matrix_export(self.handle, which)
+
+    def export_fp16(self):
+        return ct_matrix_export_fp16(self.handle)
+
+    def surrogate_stencil(self, r, square=False):
+        return ct_surrogate_stencil(self.handle, r, square)

@@ -1,0 +1,74 @@
+"""CPU checks of the C ABI: the library builds, loads, exports every symbol
+that include/ct.h declares, and rejects invalid arguments before touching a
+GPU."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1705_07497_gb300 import _build, ct
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return ct.lib()
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "ct.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ct_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_symbols():
+    assert _declared_symbols() == sorted(ct.SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    raw = ctypes.CDLL(ct.LIB_PATH)
+    for name in _declared_symbols():
+        assert hasattr(raw, name), name
+
+
+def test_status_strings(lib):
+    assert ct.status_string(ct.CT_OK) == "ok"
+    assert "breakdown" in ct.status_string(ct.CT_ERR_BREAKDOWN).lower()
+    assert ct.status_string(12345) == "unknown status"
+
+
+@pytest.mark.parametrize(
+    "geom",
+    [(0, 90, 3, 91), (64, 0, 3, 91), (64, 90, 0, 91), (64, 90, 3, 0), (-1, 1, 1, 1), (50000, 4, 1, 8)],
+)
+def test_invalid_geometry_is_rejected_without_a_gpu(lib, geom):
+    g = ct.Geometry(*geom)
+    h = ctypes.c_void_p()
+    rc = lib.ct_build_matrix(ctypes.byref(g), 0, ctypes.byref(h))
+    assert rc == ct.CT_ERR_ARG
+    assert h.value is None
+    assert lib.ct_last_error().decode() != ""
+
+
+def test_null_and_flag_errors(lib):
+    h = ctypes.c_void_p()
+    assert lib.ct_build_matrix(None, 0, ctypes.byref(h)) == ct.CT_ERR_ARG
+    g = ct.Geometry(8, 8, 1, 12)
+    assert lib.ct_build_matrix(ctypes.byref(g), 0, None) == ct.CT_ERR_ARG
+    assert lib.ct_build_matrix(ctypes.byref(g), 0x100, ctypes.byref(h)) == ct.CT_ERR_ARG
+    assert lib.ct_build_matrix(ctypes.byref(g), ct.CT_KEEP_FP32_COPY, ctypes.byref(h)) == ct.CT_ERR_ARG
+    assert lib.ct_matrix_info(None, None, None, None) == ct.CT_ERR_ARG
+    lib.ct_destroy_matrix(None)  # no-op
+
+
+def test_binding_refuses_wrong_dtypes(lib):
+    import numpy as np
+
+    with pytest.raises(TypeError):
+        ct._vec(np.zeros(4, dtype=np.float64))
+    with pytest.raises(TypeError):
+        ct._vec([1.0, 2.0])
