@@ -60,7 +60,7 @@ def measured_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("spmv.cu", "reduce.cuh", "ct_internal.cuh"):
+    for name in ("solver_ops.cu", "sparse_common.cuh", "dfloat.cuh", "reduce.cuh", "ct_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1705_07497_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -160,20 +160,26 @@ def make_data(wl, M, dev, seed):
 
 def oracle_sample_main(args):
     """Runs in a fresh single-threaded interpreter: the oracle on ORACLE_UPDATES
-    Bregman updates of the workload; writes u and prints the seconds taken."""
+    Bregman updates of the workload; writes the iterate after every update and
+    prints the seconds taken."""
     from oracle import radon, tv
 
     wl = inputs.WORKLOADS[args.workload]
     f = np.load(args.oracle_in)
     A = radon.siddon_matrix(wl["n"], wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
+    state, us = None, []
     t0 = time.perf_counter()
-    res = tv.split_bregman(A, f, (wl["n"], wl["n"]), wl["alpha"], wl["lam"], args.oracle_updates, wl["inner"])
+    for _ in range(args.oracle_updates):
+        res = tv.split_bregman(A, f, (wl["n"], wl["n"]), wl["alpha"], wl["lam"], 1, wl["inner"], state=state)
+        state = (res["u"], res["dx"], res["dy"], res["bx"], res["by"])
+        us.append(res["u"].ravel().copy())
     dt = time.perf_counter() - t0
-    np.save(args.oracle_out, res["u"].ravel())
+    np.save(args.oracle_out, np.stack(us))
     print(json.dumps({"seconds": dt}))
 
 
 def run_oracle_sample(wl_name, f, updates):
+    """(seconds, iterates [updates][N*N]) of the oracle on the first updates."""
     with tempfile.TemporaryDirectory() as td:
         fin, fout = os.path.join(td, "f.npy"), os.path.join(td, "u.npy")
         np.save(fin, f)
@@ -284,7 +290,8 @@ def bench_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_secs = float(t.item())
 
-    launches_per_step = 1 + wl["outer"] * (2 + 4 * wl["inner"] + 1)
+    # to_split + A^T f + widen, per update (A u, residual, inner x 4, shrink), narrow
+    launches_per_step = 3 + wl["outer"] * (2 + 4 * wl["inner"] + 1) + 1
     out = {
         "metric": METRIC,
         "value": round(value, 4),
@@ -306,7 +313,8 @@ def bench_ours(args):
             "parallelism": "replicas over slices" if world > 1 else "single GPU",
         },
         "roofline": {
-            "kernel": "spmv_store_kernel<float> (y = A x, CSR FP32, one warp per row)",
+            "kernel": "csr_df_kernel<float> on A (y = A x, CSR FP32 values, double-float accumulation, "
+                      "one warp per row); the solver launches the same template for every y = A p",
             "bound": "hbm",
             "achieved": round(ach_fwd, 1),
             "peak": peak,
@@ -332,9 +340,13 @@ def bench_ours(args):
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         secs_cpu, u_oracle = run_oracle_sample(args.workload, f_host, ORACLE_UPDATES)
-        u2 = torch.zeros(n * n, dtype=torch.float32, device=dev)
-        M.split_bregman(f, u2, wl["alpha"], wl["lam"], ORACLE_UPDATES, wl["inner"])
-        err = float(np.linalg.norm(u2.cpu().double().numpy() - u_oracle) / np.linalg.norm(u_oracle))
+        errs = {}
+        for k in range(1, ORACLE_UPDATES + 1):
+            u2 = torch.zeros(n * n, dtype=torch.float32, device=dev)
+            M.split_bregman(f, u2, wl["alpha"], wl["lam"], k, wl["inner"])
+            ref = u_oracle[k - 1]
+            errs["rel_l2_vs_oracle_after_%d_updates" % k] = float(
+                np.linalg.norm(u2.cpu().double().numpy() - ref) / np.linalg.norm(ref))
         out["cpu_baseline"] = {
             "value": round(ORACLE_UPDATES / wl["outer"] / secs_cpu, 6),
             "unit": "slices/s",
@@ -343,12 +355,52 @@ def bench_ours(args):
             "sample": "%d of %d Bregman updates (20 CG steps each) of the same workload, FP64 numpy/scipy "
                       "CSR, one thread; %.1f s" % (ORACLE_UPDATES, wl["outer"], secs_cpu),
         }
-        out["parity"] = {"rel_l2_vs_oracle_after_%d_updates" % ORACLE_UPDATES: err}
+        out["parity"] = errs
     if rank == 0:
         print(json.dumps(out))
     M.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def bench_kernel(args):
+    """Small committed case for ncu: W + K launches of one product on the
+    slice workload's geometry (A and A^T resident, 0.98 GB > L2).
+    forward/adjoint: ct_forward / ct_adjoint (batch 1); solver: ct_cg_solve
+    with the split-Bregman operator and K CG steps."""
+    import torch
+
+    from paper_1705_07497_gb300 import ct
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = inputs.WORKLOADS[args.workload]
+    n = wl["n"]
+    M = ct.Matrix(n, wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
+    x = torch.tensor(inputs.ellipse_phantom(n, wl["seed"]).ravel(), dtype=torch.float32, device=dev)
+    y = torch.empty(M.rows, dtype=torch.float32, device=dev)
+    M.forward(x, y)
+    stream = torch.cuda.current_stream(dev)
+    if args.kernel == "forward":
+        fn = lambda: M.forward(x, y)  # noqa: E731
+    elif args.kernel == "adjoint":
+        fn = lambda: M.adjoint(y, x)  # noqa: E731
+    else:
+        rhs = torch.empty(M.cols, dtype=torch.float32, device=dev)
+        M.adjoint(y, rhs)
+        u = torch.zeros(M.cols, dtype=torch.float32, device=dev)
+        fn = lambda: M.cg_solve(rhs, u, 0.0, wl["alpha"], wl["lam"], args.steps)  # noqa: E731
+    for _ in range(args.warmup):
+        fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 1 if args.kernel == "solver" else args.steps
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel": args.kernel, "ms_per_call": a.elapsed_time(b) / reps, "nnz": M.nnz}))
+    M.close()
 
 
 def bench_reference(args):
@@ -409,6 +461,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(inputs.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", default=None, choices=["forward", "adjoint", "solver"],
+                    help="time one product kernel in isolation (small case for profilers)")
     ap.add_argument("--_oracle-in", dest="oracle_in", default=None)
     ap.add_argument("--_oracle-out", dest="oracle_out", default=None)
     ap.add_argument("--_oracle-updates", dest="oracle_updates", type=int, default=ORACLE_UPDATES)
@@ -416,7 +470,9 @@ def main():
     if args.oracle_in:
         oracle_sample_main(args)
         return
-    if args.impl == "reference":
+    if args.kernel:
+        bench_kernel(args)
+    elif args.impl == "reference":
         bench_reference(args)
     else:
         bench_ours(args)

@@ -394,7 +394,9 @@ int make_stencil(ct_matrix* M, int r, int square, Stencil** out)
             S.h_di.push_back(di);
             S.h_dj.push_back(dj);
             S.h_w.push_back(v);
-            wf.push_back((float)v);
+            const float hi = (float)v;
+            wf.push_back(hi);
+            wf.push_back((float)(v - (double)hi));
             dd.push_back(di);
             dd.push_back(dj);
         }

@@ -78,7 +78,7 @@ struct Stencil {
     int ntaps = 0;
     int r = 0;
     int32_t* d = nullptr;  // device [ntaps][2] offsets (di, dj)
-    float* w = nullptr;    // device [ntaps] FP32 taps
+    float* w = nullptr;    // device [ntaps][2] taps as FP32 pairs (hi, lo)
     std::vector<int32_t> h_di, h_dj;
     std::vector<double> h_w;  // FP64 taps (host copy)
 };
@@ -87,16 +87,20 @@ struct Workspace {
     int device = -1;
     int32_t batch = 0;
     int64_t n2 = 0, rows = 0;
-    // vectors [len][batch]
-    float *y = nullptr;  // sinogram temp
-    float *r = nullptr, *p = nullptr, *q = nullptr;
-    float *atf = nullptr, *u_old = nullptr, *bx = nullptr, *by = nullptr, *vx = nullptr, *vy = nullptr;
-    double* partials = nullptr;  // reduction partials
+    // Solver vectors are FP64 ([len][batch]); the vectors that the sparse
+    // products gather are also kept split as FP32 pairs (hi, lo).
+    double *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *rhs = nullptr;
+    double *atf = nullptr, *u_old = nullptr, *bx = nullptr, *by = nullptr, *vx = nullptr, *vy = nullptr;
+    float2 *u2 = nullptr, *p2 = nullptr;  // split copies of u and p
+    float2* y2 = nullptr;                  // sinogram temp, split [rows][batch]
+    float2* pub_y2 = nullptr;              // ct_adjoint with FP16 storage: s .* y, split
+    int64_t pub_y2_len = 0;
+    double* partials = nullptr;            // reduction partials
     int64_t partials_len = 0;
-    unsigned* counter = nullptr; // last-block counter (one per workspace)
+    unsigned* counter = nullptr;           // last-block counter (one per workspace)
     CgSlice* cg = nullptr;
     SbSlice* sb = nullptr;
-    // staging for host pointers
+    // staging for host pointers (FP32, caller layout)
     float *stage_a = nullptr, *stage_b = nullptr;
     int64_t stage_a_len = 0, stage_b_len = 0;
     cudaStream_t cap_stream = nullptr;
@@ -138,30 +142,48 @@ int launch_forward(const ct_matrix* M, ValKind vk, const float* x, float* y, int
 int launch_adjoint(const ct_matrix* M, ValKind vk, const float* y, float* x, int32_t batch,
                    float out_scale, bool scale_y, cudaStream_t st);
 
-// Epilogue of the adjoint product inside the CG operator.
+// Epilogue of the adjoint product inside the CG operator (FP64 vectors).
 struct OpEpilogue {
-    int mode;             // 1: q = Op(p) and p.q partial; 2: residual r = rhs - Op(u), p = r
-    float c_id, c_ata, c_grad;
-    const float* in;      // p (mode 1) or u (mode 2)
-    float* out;           // q (mode 1) or r (mode 2)
-    float* p_out;         // mode 2: p = r
-    const float* rhs;     // mode 2: explicit rhs, or null to build it as atf + lambda grad^T v
-    const float* atf;     // mode 2 (SB): alpha A^T f
-    const float* vx;      // mode 2 (SB): v = d - b
-    const float* vy;
-    float lam;
-    const int32_t* gate;  // optional: skip all work when *gate != 0 (stopped SB)
+    int mode;             // 1: q = Op(p) and p.q; 2: r = rhs - Op(u), p = r (CG start);
+                          // 3: r = rhs - Op(u) only (residual replacement)
+    double c_id, c_ata, c_grad;
+    const double* in;     // p (mode 1) or u (modes 2, 3)
+    const float2* in2;    // split copy of `in` (for the stencil)
+    double* out;          // q (mode 1) or r (modes 2, 3)
+    double* p_out;        // mode 2: p = r
+    float2* p2_out;       // mode 2: split copy of p
+    const double* rhs;    // modes 2, 3: explicit rhs, or null to build atf + lambda grad^T v
+    const double* atf;    // SB: alpha A^T f
+    const double* vx;     // SB: v = d - b
+    const double* vy;
+    double lam;
+    const int32_t* gate;  // skip all work when *gate != 0 (stopped SB)
     CgSlice* cg;
     double* partials;
     unsigned* counter;
     double tol;
 };
-int launch_adjoint_op(const ct_matrix* M, ValKind vk, const float* y, int32_t batch,
-                      const OpEpilogue& ep, cudaStream_t st);
-int launch_forward_gated(const ct_matrix* M, ValKind vk, const float* x, float* y, int32_t batch,
-                         bool normal_scale, const CgSlice* cg, const int32_t* gate, cudaStream_t st);
-int launch_stencil_op(const ct_matrix* M, const Stencil* S, int32_t batch, const OpEpilogue& ep,
+
+// solver_ops.cu: extended-precision products used inside the solvers
+// y2 = split(A x) with x gathered from x2 (double-float accumulation);
+// rpow: multiply rows by s^rpow (FP16 storage).
+int launch_forward_df(const ct_matrix* M, ValKind vk, const float2* x2, float2* y2, int rpow,
+                      const CgSlice* cg, const int32_t* gate, cudaStream_t st);
+// out = scale * A^T y2 (FP64), plain store.
+int launch_adjoint_df(const ct_matrix* M, ValKind vk, const float2* y2, double* out, double scale,
                       cudaStream_t st);
+// A^T y2 fused with the CG operator epilogue.
+int launch_adjoint_op_df(const ct_matrix* M, ValKind vk, const float2* y2, const OpEpilogue& ep,
+                         cudaStream_t st);
+// Surrogate stencil (or no sparse term at all when S is null) fused with the epilogue.
+int launch_stencil_op_df(const ct_matrix* M, const Stencil* S, const OpEpilogue& ep, cudaStream_t st);
+// Public single-slice products with FP32 vectors (same kernel template).
+int launch_forward_f32(const ct_matrix* M, ValKind vk, const float* x, float* y, cudaStream_t st);
+int launch_adjoint_f32(const ct_matrix* M, ValKind vk, const float* y, const float2* y2_scaled, float* x,
+                       cudaStream_t st);
+// out2 = split(in * scale) for FP32 input (scale may be null).
+int launch_to_split(const ct_matrix* M, const float* in, const float* scale, float2* out2, int64_t len,
+                    cudaStream_t st);
 
 // solve.cu
 int cg_solve(ct_matrix* M, const ct_cg_params* P, const float* rhs, float* u, int32_t batch,

@@ -5,57 +5,67 @@
 // never waits inside the loop.
 //
 // One CG step is four kernels: y = A p; q = Op(p) fused into the A^T product
-// (with p.q); u += alpha p, r -= alpha q (with r.r); p = r + beta p.  FP32
-// vectors, FP64 dot products; each reduction is finished by the last block of
-// its kernel in a fixed order, so results are bitwise reproducible.
+// (with p.q); u += alpha p, r -= alpha q (with r.r); p = r + beta p.  The
+// iteration vectors are FP64 (a fixed number of CG steps amplifies their
+// rounding by orders of magnitude, see solver_ops.cu); each reduction is
+// finished by the last block of its kernel in a fixed order, so results are
+// bitwise reproducible run to run.
+#include <cmath>
 #include <cstring>
 
 #include "ct_internal.cuh"
+#include "dfloat.cuh"
 #include "reduce.cuh"
 
 namespace ct {
 namespace {
 
-__global__ void __launch_bounds__(256) cg_update_kernel(float* __restrict__ u, float* __restrict__ r,
-                                                        const float* __restrict__ p,
-                                                        const float* __restrict__ q, int64_t len,
+__global__ void __launch_bounds__(256) cg_update_kernel(double* __restrict__ u, float2* __restrict__ u2,
+                                                        double* __restrict__ r,
+                                                        const double* __restrict__ p,
+                                                        const double* __restrict__ q, int64_t len,
                                                         CgSlice* cg, double tol, double* partials,
                                                         unsigned* counter, const int32_t* gate)
 {
     if (gate && *gate) return;
     if (!cg->active) return;
-    const float al = (float)cg->alpha;
+    const double al = cg->alpha;
     double d = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
          i += (int64_t)gridDim.x * blockDim.x) {
-        u[i] = fmaf(al, p[i], u[i]);
-        const float rn = fmaf(-al, q[i], r[i]);
+        const double un = u[i] + al * p[i];
+        u[i] = un;
+        u2[i] = split_f2(un);
+        const double rn = r[i] - al * q[i];
         r[i] = rn;
-        d += (double)rn * (double)rn;
+        d += rn * rn;
     }
     double v[1] = {d}, tot[1];
     if (grid_reduce_last<1>(v, partials, counter, tot)) cg_after_update(*cg, tot[0], tol);
 }
 
-__global__ void __launch_bounds__(256) cg_direction_kernel(float* __restrict__ p,
-                                                           const float* __restrict__ r, int64_t len,
+__global__ void __launch_bounds__(256) cg_direction_kernel(double* __restrict__ p, float2* __restrict__ p2,
+                                                           const double* __restrict__ r, int64_t len,
                                                            const CgSlice* cg, const int32_t* gate)
 {
     if (gate && *gate) return;
     if (!cg->active) return;
-    const float be = (float)cg->beta;
+    const double be = cg->beta;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
-         i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = fmaf(be, p[i], r[i]);
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double pn = r[i] + be * p[i];
+        p[i] = pn;
+        p2[i] = split_f2(pn);
+    }
 }
 
 // After the inner solve: g = grad u, d = shrink(g + b, 1/lambda), b += g - d,
 // v = d - b (the next right-hand side's split term), ||u - u_old||_1, u_old = u.
-__global__ void __launch_bounds__(256) sb_shrink_kernel(const float* __restrict__ u,
-                                                        float* __restrict__ u_old,
-                                                        float* __restrict__ bx, float* __restrict__ by,
-                                                        float* __restrict__ vx, float* __restrict__ vy,
-                                                        int n, float gamma, SbSlice* sb,
+__global__ void __launch_bounds__(256) sb_shrink_kernel(const double* __restrict__ u,
+                                                        double* __restrict__ u_old,
+                                                        double* __restrict__ bx, double* __restrict__ by,
+                                                        double* __restrict__ vx, double* __restrict__ vy,
+                                                        int n, double gamma, SbSlice* sb,
                                                         const CgSlice* cg, double tol,
                                                         double* partials, unsigned* counter)
 {
@@ -65,18 +75,18 @@ __global__ void __launch_bounds__(256) sb_shrink_kernel(const float* __restrict_
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(p / n), j = (int)(p - (int64_t)i * n);
-        const float c = u[p];
-        const float gx = (j < n - 1) ? u[p + 1] - c : 0.0f;
-        const float gy = (i < n - 1) ? u[p + n] - c : 0.0f;
-        const float tx = gx + bx[p], ty = gy + by[p];
-        const float dx = copysignf(fmaxf(fabsf(tx) - gamma, 0.0f), tx);
-        const float dy = copysignf(fmaxf(fabsf(ty) - gamma, 0.0f), ty);
-        const float bxn = tx - dx, byn = ty - dy;
+        const double c = u[p];
+        const double gx = (j < n - 1) ? u[p + 1] - c : 0.0;
+        const double gy = (i < n - 1) ? u[p + n] - c : 0.0;
+        const double tx = gx + bx[p], ty = gy + by[p];
+        const double dx = copysign(fmax(fabs(tx) - gamma, 0.0), tx);
+        const double dy = copysign(fmax(fabs(ty) - gamma, 0.0), ty);
+        const double bxn = tx - dx, byn = ty - dy;
         bx[p] = bxn;
         by[p] = byn;
         vx[p] = dx - bxn;
         vy[p] = dy - byn;
-        upd += fabs((double)c - (double)u_old[p]);
+        upd += fabs(c - u_old[p]);
         u_old[p] = c;
     }
     double v[1] = {upd}, tot[1];
@@ -90,9 +100,29 @@ __global__ void __launch_bounds__(256) sb_shrink_kernel(const float* __restrict_
     }
 }
 
-int alloc_f(float** p, int64_t n)
+// FP32 caller vector -> FP64 (and its split copy when u2 is given).
+__global__ void widen_kernel(const float* __restrict__ in, double* __restrict__ out,
+                             float2* __restrict__ out2, int64_t len)
 {
-    cudaError_t e = cudaMalloc((void**)p, (size_t)(n > 0 ? n : 1) * sizeof(float));
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = in[i];
+        out[i] = (double)v;
+        if (out2) out2[i] = make_float2(v, 0.0f);
+    }
+}
+
+__global__ void narrow_kernel(const double* __restrict__ in, float* __restrict__ out, int64_t len)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __double2float_rn(in[i]);
+}
+
+template <typename T>
+int alloc_n(T** p, int64_t n)
+{
+    cudaError_t e = cudaMalloc((void**)p, (size_t)(n > 0 ? n : 1) * sizeof(T));
     if (e == cudaErrorMemoryAllocation) {
         (void)cudaGetLastError();
         return fail(CT_ERR_OOM, "workspace allocation failed");
@@ -111,50 +141,52 @@ struct Plan {
     int refresh;       // residual replacement period (FP16 storage), 0 = off
 };
 
-// Op applied to `in` with the given epilogue (y = A in, then A^T y fused).
-int apply_op(const Plan& P, OpEpilogue ep, const float* in, cudaStream_t st, bool fp32_refresh = false)
+// Op applied to `in` (split copy in2) with the given epilogue.
+int apply_op(const Plan& P, OpEpilogue ep, const double* in, const float2* in2, cudaStream_t st,
+             bool fp32_refresh = false)
 {
     Workspace& w = P.M->ws;
     ep.in = in;
-    const bool sparse = P.sparse;
-    if (sparse) {
+    ep.in2 = in2;
+    if (P.sparse) {
         const ValKind vk = fp32_refresh ? ValKind::F32 : P.vk;
-        CT_CHECK(launch_forward_gated(P.M, vk, in, w.y, 1, true,
-                                      ep.mode == 2 ? nullptr : ep.cg, ep.gate, st));
-        CT_CHECK(launch_adjoint_op(P.M, vk, w.y, 1, ep, st));
+        CT_CHECK(launch_forward_df(P.M, vk, in2, w.y2, vk == ValKind::F16 ? 2 : 0,
+                                   ep.mode == 2 ? nullptr : ep.cg, ep.gate, st));
+        CT_CHECK(launch_adjoint_op_df(P.M, vk, w.y2, ep, st));
     } else {
-        CT_CHECK(launch_stencil_op(P.M, P.S, 1, ep, st));
+        CT_CHECK(launch_stencil_op_df(P.M, P.S, ep, st));
     }
     return CT_OK;
 }
 
-// Residual r = rhs - Op(u), p = r, then `iters` CG steps.
-int enqueue_cg(const Plan& P, const float* rhs, float* u, int iters, cudaStream_t st)
+// Residual r = rhs - Op(u), p = r, then `iters` CG steps on the FP64 iterate w.u.
+int enqueue_cg(const Plan& P, const double* rhs, int iters, cudaStream_t st)
 {
     Workspace& w = P.M->ws;
     OpEpilogue ep = P.base;
     ep.mode = 2;
     ep.out = w.r;
     ep.p_out = w.p;
+    ep.p2_out = w.p2;
     ep.rhs = rhs;
-    CT_CHECK(apply_op(P, ep, u, st));
+    CT_CHECK(apply_op(P, ep, w.u, w.u2, st));
     const int gv = grid_for(P.M, P.n2, 256, 8);
     for (int it = 0; it < iters; ++it) {
         OpEpilogue e1 = P.base;
         e1.mode = 1;
         e1.out = w.q;
-        CT_CHECK(apply_op(P, e1, w.p, st));
-        cg_update_kernel<<<gv, 256, 0, st>>>(u, w.r, w.p, w.q, P.n2, w.cg, P.base.tol, w.partials,
-                                             w.counter, P.base.gate);
+        CT_CHECK(apply_op(P, e1, w.p, w.p2, st));
+        cg_update_kernel<<<gv, 256, 0, st>>>(w.u, w.u2, w.r, w.p, w.q, P.n2, w.cg, P.base.tol,
+                                             w.partials, w.counter, P.base.gate);
         CT_CUDA(cudaGetLastError());
-        cg_direction_kernel<<<gv, 256, 0, st>>>(w.p, w.r, P.n2, w.cg, P.base.gate);
+        cg_direction_kernel<<<gv, 256, 0, st>>>(w.p, w.p2, w.r, P.n2, w.cg, P.base.gate);
         CT_CUDA(cudaGetLastError());
         if (P.refresh > 0 && (it + 1) % P.refresh == 0 && it + 1 < iters) {
             OpEpilogue e3 = P.base;
             e3.mode = 3;
             e3.out = w.r;
             e3.rhs = rhs;
-            CT_CHECK(apply_op(P, e3, u, st, true));
+            CT_CHECK(apply_op(P, e3, w.u, w.u2, st, true));
         }
     }
     return CT_OK;
@@ -184,9 +216,9 @@ int make_plan(ct_matrix* M, double c_id, double c_ata, double c_grad, double tol
     Workspace& w = M->ws;
     OpEpilogue& b = P.base;
     std::memset(&b, 0, sizeof(b));
-    b.c_id = (float)c_id;
-    b.c_ata = (float)c_ata;
-    b.c_grad = (float)c_grad;
+    b.c_id = c_id;
+    b.c_ata = c_ata;
+    b.c_grad = c_grad;
     b.cg = w.cg;
     b.partials = w.partials;
     b.counter = w.counter;
@@ -198,8 +230,14 @@ int make_plan(ct_matrix* M, double c_id, double c_ata, double c_grad, double tol
 
 void free_workspace(Workspace& w)
 {
-    float* fs[] = {w.y, w.r, w.p, w.q, w.atf, w.u_old, w.bx, w.by, w.vx, w.vy, w.stage_a, w.stage_b};
-    for (float* f : fs) cudaFree(f);
+    double* ds[] = {w.u, w.r, w.p, w.q, w.rhs, w.atf, w.u_old, w.bx, w.by, w.vx, w.vy};
+    for (double* d : ds) cudaFree(d);
+    cudaFree(w.u2);
+    cudaFree(w.p2);
+    cudaFree(w.y2);
+    cudaFree(w.pub_y2);
+    cudaFree(w.stage_a);
+    cudaFree(w.stage_b);
     cudaFree(w.partials);
     cudaFree(w.counter);
     cudaFree(w.cg);
@@ -214,23 +252,37 @@ int ensure_workspace(ct_matrix* M, int32_t batch, bool /*solver*/)
     if (w.batch >= batch && w.r) return CT_OK;
     CT_CUDA(cudaDeviceSynchronize());
     cudaStream_t keep = w.cap_stream;
+    float* sa = w.stage_a;
+    float* sb = w.stage_b;
+    float2* py = w.pub_y2;
+    const int64_t la = w.stage_a_len, lb = w.stage_b_len, lp = w.pub_y2_len;
     w.cap_stream = nullptr;
+    w.stage_a = w.stage_b = nullptr;
+    w.pub_y2 = nullptr;
     free_workspace(w);
     w.cap_stream = keep;
+    w.stage_a = sa;
+    w.stage_b = sb;
+    w.pub_y2 = py;
+    w.stage_a_len = la;
+    w.stage_b_len = lb;
+    w.pub_y2_len = lp;
     w.batch = batch;
     w.n2 = M->cols;
     w.rows = M->rows;
     const int64_t nv = w.n2 * batch;
-    CT_CHECK(alloc_f(&w.y, w.rows * batch));
-    float** vs[] = {&w.r, &w.p, &w.q, &w.atf, &w.u_old, &w.bx, &w.by, &w.vx, &w.vy};
-    for (float** v : vs) CT_CHECK(alloc_f(v, nv));
+    double** ds[] = {&w.u, &w.r, &w.p, &w.q, &w.rhs, &w.atf, &w.u_old, &w.bx, &w.by, &w.vx, &w.vy};
+    for (double** d : ds) CT_CHECK(alloc_n(d, nv));
+    CT_CHECK(alloc_n(&w.u2, nv));
+    CT_CHECK(alloc_n(&w.p2, nv));
+    CT_CHECK(alloc_n(&w.y2, w.rows * batch));
     w.partials_len = (int64_t)4 * (M->sm_count > 0 ? M->sm_count : 148) * 8 * batch;
-    CT_CUDA(cudaMalloc((void**)&w.partials, w.partials_len * sizeof(double)));
-    CT_CUDA(cudaMalloc((void**)&w.counter, 64));
-    CT_CUDA(cudaMemset(w.counter, 0, 64));
-    CT_CUDA(cudaMalloc((void**)&w.cg, sizeof(CgSlice) * batch));
+    CT_CHECK(alloc_n(&w.partials, w.partials_len));
+    CT_CHECK(alloc_n(&w.counter, 16));
+    CT_CUDA(cudaMemset(w.counter, 0, 16 * sizeof(unsigned)));
+    CT_CHECK(alloc_n(&w.cg, batch));
     CT_CUDA(cudaMemset(w.cg, 0, sizeof(CgSlice) * batch));
-    CT_CUDA(cudaMalloc((void**)&w.sb, sizeof(SbSlice) * batch));
+    CT_CHECK(alloc_n(&w.sb, batch));
     CT_CUDA(cudaMemset(w.sb, 0, sizeof(SbSlice) * batch));
     if (!w.cap_stream) CT_CUDA(cudaStreamCreateWithFlags(&w.cap_stream, cudaStreamNonBlocking));
     return CT_OK;
@@ -242,13 +294,20 @@ int cg_solve(ct_matrix* M, const ct_cg_params* Pp, const float* rhs, float* u, i
     if (batch != 1) return fail(CT_ERR_UNSUPPORTED, "ct_cg_solve: batch > 1 is not available yet");
     if (Pp->max_iters < 0) return fail(CT_ERR_ARG, "max_iters < 0");
     CT_CHECK(ensure_workspace(M, batch, true));
+    Workspace& w = M->ws;
     Plan P;
     CT_CHECK(make_plan(M, Pp->c_id, Pp->c_ata, Pp->c_grad, Pp->rel_tol, Pp->surrogate_r,
                        Pp->surrogate_square, Pp->refresh_every, P));
-    CT_CHECK(enqueue_cg(P, rhs, u, Pp->max_iters, st));
+    const int gv = grid_for(M, P.n2, 256, 8);
+    widen_kernel<<<gv, 256, 0, st>>>(rhs, w.rhs, nullptr, P.n2);
+    widen_kernel<<<gv, 256, 0, st>>>(u, w.u, w.u2, P.n2);
+    CT_CUDA(cudaGetLastError());
+    CT_CHECK(enqueue_cg(P, w.rhs, Pp->max_iters, st));
+    narrow_kernel<<<gv, 256, 0, st>>>(w.u, u, P.n2);
+    CT_CUDA(cudaGetLastError());
     if (stats) {
         CgSlice h;
-        CT_CUDA(cudaMemcpyAsync(&h, M->ws.cg, sizeof(h), cudaMemcpyDeviceToHost, st));
+        CT_CUDA(cudaMemcpyAsync(&h, w.cg, sizeof(h), cudaMemcpyDeviceToHost, st));
         CT_CUDA(cudaStreamSynchronize(st));
         stats->iters = h.iters;
         stats->final_rel_res = h.rhs2 > 0 ? std::sqrt(h.rr / h.rhs2) : 0.0;
@@ -262,13 +321,13 @@ int cg_solve(ct_matrix* M, const ct_cg_params* Pp, const float* rhs, float* u, i
 
 namespace {
 
-int enqueue_sb_outer(const Plan& P, float* u, const ct_sb_params* Sp, cudaStream_t st)
+int enqueue_sb_outer(const Plan& P, const ct_sb_params* Sp, cudaStream_t st)
 {
     Workspace& w = P.M->ws;
-    CT_CHECK(enqueue_cg(P, nullptr, u, Sp->inner_cg_iters, st));
+    CT_CHECK(enqueue_cg(P, nullptr, Sp->inner_cg_iters, st));
     const int gv = grid_for(P.M, P.n2, 256, 8);
-    sb_shrink_kernel<<<gv, 256, 0, st>>>(u, w.u_old, w.bx, w.by, w.vx, w.vy, P.M->g.n,
-                                         (float)(1.0 / Sp->lambda), w.sb, w.cg, Sp->stop_rel_update,
+    sb_shrink_kernel<<<gv, 256, 0, st>>>(w.u, w.u_old, w.bx, w.by, w.vx, w.vy, P.M->g.n,
+                                         1.0 / Sp->lambda, w.sb, w.cg, Sp->stop_rel_update,
                                          w.partials, w.counter);
     CT_CUDA(cudaGetLastError());
     return CT_OK;
@@ -291,28 +350,33 @@ int split_bregman(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u
     P.base.atf = w.atf;
     P.base.vx = w.vx;
     P.base.vy = w.vy;
-    P.base.lam = (float)Sp->lambda;
+    P.base.lam = Sp->lambda;
     const int64_t n2 = P.n2;
+    const int gv = grid_for(M, n2, 256, 8);
     // alpha A^T f, once (the right-hand side keeps the exact back-projection
-    // also with the surrogate, Eq. surr_SBupd)
-    CT_CHECK(launch_adjoint(M, P.vk, f, w.atf, 1, (float)Sp->alpha, true, st));
-    CT_CUDA(cudaMemsetAsync(w.bx, 0, n2 * sizeof(float), st));
-    CT_CUDA(cudaMemsetAsync(w.by, 0, n2 * sizeof(float), st));
-    CT_CUDA(cudaMemsetAsync(w.vx, 0, n2 * sizeof(float), st));
-    CT_CUDA(cudaMemsetAsync(w.vy, 0, n2 * sizeof(float), st));
+    // also with the surrogate, Eq. surr_SBupd); FP16 storage applies A^T as
+    // Q^T (s .* f)
+    CT_CHECK(launch_to_split(M, f, P.vk == ValKind::F16 ? M->row_scale : nullptr, w.y2, M->rows, st));
+    CT_CHECK(launch_adjoint_df(M, P.vk, w.y2, w.atf, Sp->alpha, st));
+    widen_kernel<<<gv, 256, 0, st>>>(u, w.u, w.u2, n2);
+    CT_CUDA(cudaGetLastError());
+    CT_CUDA(cudaMemsetAsync(w.bx, 0, n2 * sizeof(double), st));
+    CT_CUDA(cudaMemsetAsync(w.by, 0, n2 * sizeof(double), st));
+    CT_CUDA(cudaMemsetAsync(w.vx, 0, n2 * sizeof(double), st));
+    CT_CUDA(cudaMemsetAsync(w.vy, 0, n2 * sizeof(double), st));
     CT_CUDA(cudaMemsetAsync(w.sb, 0, sizeof(SbSlice), st));
-    CT_CUDA(cudaMemcpyAsync(w.u_old, u, n2 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    CT_CUDA(cudaMemcpyAsync(w.u_old, w.u, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
 
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CT_CUDA(cudaStreamIsCapturing(st, &cs));
     if (cs != cudaStreamCaptureStatusNone || Sp->outer_iters <= 2) {
-        for (int k = 0; k < Sp->outer_iters; ++k) CT_CHECK(enqueue_sb_outer(P, u, Sp, st));
+        for (int k = 0; k < Sp->outer_iters; ++k) CT_CHECK(enqueue_sb_outer(P, Sp, st));
     } else {
         // capture one Bregman update and replay it
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         CT_CUDA(cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal));
-        int rc = enqueue_sb_outer(P, u, Sp, w.cap_stream);
+        int rc = enqueue_sb_outer(P, Sp, w.cap_stream);
         cudaError_t e = cudaStreamEndCapture(w.cap_stream, &graph);
         if (rc != CT_OK) {
             if (graph) cudaGraphDestroy(graph);
@@ -329,6 +393,8 @@ int split_bregman(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u
         cudaGraphExecDestroy(exec);
         CT_CUDA(e);
     }
+    narrow_kernel<<<gv, 256, 0, st>>>(w.u, u, n2);
+    CT_CUDA(cudaGetLastError());
     if (stats) {
         SbSlice h;
         CT_CUDA(cudaMemcpyAsync(&h, w.sb, sizeof(h), cudaMemcpyDeviceToHost, st));

@@ -248,17 +248,21 @@ def test_split_bregman_host_buffers(dev):
     assert rel(u, want) <= RECON_TOL
 
 
-def test_split_bregman_512_short(dev):
-    """512x512, 180 of 720 angles, 725 bins, 1% Gaussian noise, alpha = lambda = 1:
-    the first 3 Bregman updates of 20 CG steps against the oracle."""
+def test_split_bregman_512_first_update(dev):
+    """512x512, 180 of 720 angles, 725 bins, 1% Gaussian noise, alpha = lambda = 1,
+    one Bregman update of 20 CG steps against the oracle.  The first update is
+    well conditioned (FP64 perturbations of A at 1e-9 move it by 1e-5); later
+    updates of this workload amplify FP64 rounding itself to ~1e-3, see
+    test_split_bregman_512_band."""
     geom = (512, 720, 4, 725)
     ref, truth, f = _sb_case(geom, 1000, noise=0.01)
     M = gpu_A(*geom)
-    want = tv.split_bregman(ref, f, (512, 512), 1.0, 1.0, 3, 20)
+    want = tv.split_bregman(ref, f, (512, 512), 1.0, 1.0, 1, 20)
     u = torch.zeros(512 * 512, device=dev)
-    st = M.split_bregman(t32(f, dev), u, 1.0, 1.0, 3, 20)
-    assert st["outer_done"] == 3
-    assert rel(u.cpu().numpy(), want["u"].ravel()) <= RECON_TOL
+    st = M.split_bregman(t32(f, dev), u, 1.0, 1.0, 1, 20)
+    assert st["outer_done"] == 1
+    assert rel(u.cpu().numpy(), want["u"].ravel()) <= 1e-4
+    assert abs(st["first_update_l1"] - want["updates"][0]) <= 1e-4 * want["updates"][0]
 
 
 def test_split_bregman_stop_rule(dev):
@@ -286,19 +290,36 @@ def test_surrogate_stencil_matches_oracle(dev, r, square):
         assert abs(got[k] - v) <= 1e-12 * abs(want[(0, 0)])
 
 
-@pytest.mark.parametrize("r,square", [(1, False), (3, False), (2, True)])
-def test_surrogate_split_bregman_parity(dev, r, square):
+@pytest.mark.parametrize("r", [1, 3])
+def test_surrogate_split_bregman_parity(dev, r):
     """Eq. surr_SBupd: the surrogate T replaces A^T A, the rhs keeps alpha A^T f."""
     geom = (64, 90, 3, 91)
     ref, truth, f = _sb_case(geom, 0)
     M = gpu_A(*geom)
-    taps = tv.surrogate_stencil(tv.point_response(ref, 64), r, "square" if square else "disc")
+    taps = tv.surrogate_stencil(tv.point_response(ref, 64), r, "disc")
     T = tv.surrogate_matrix(taps, 64)
     want = tv.split_bregman(ref, f, (64, 64), 1.0, 1.0, 20, 10, normal=lambda x: T @ x)
     u = torch.zeros(64 * 64, device=dev)
-    st = M.split_bregman(t32(f, dev), u, 1.0, 1.0, 20, 10, surrogate_r=r, square=square)
+    st = M.split_bregman(t32(f, dev), u, 1.0, 1.0, 20, 10, surrogate_r=r)
     assert st["status"] == 0
     assert rel(u.cpu().numpy(), want["u"].ravel()) <= RECON_TOL
+
+
+def test_surrogate_indefinite_window_reports_breakdown(dev):
+    """The 5x5 square window of this geometry gives an indefinite alpha T +
+    lambda grad^T grad: the oracle's CG breaks down, and so must the library's
+    (reported as a status, not hidden)."""
+    geom = (64, 90, 3, 91)
+    ref, truth, f = _sb_case(geom, 0)
+    M = gpu_A(*geom)
+    taps = tv.surrogate_stencil(tv.point_response(ref, 64), 2, "square")
+    T = tv.surrogate_matrix(taps, 64)
+    with pytest.raises(tv.Breakdown):
+        tv.split_bregman(ref, f, (64, 64), 1.0, 1.0, 20, 10, normal=lambda x: T @ x)
+    u = torch.zeros(64 * 64, device=dev)
+    with pytest.raises(ct.CtError) as ei:
+        M.split_bregman(t32(f, dev), u, 1.0, 1.0, 20, 10, surrogate_r=2, square=True)
+    assert ei.value.code == ct.CT_ERR_BREAKDOWN
 
 
 def test_nonfinite_rhs_is_reported(dev):
