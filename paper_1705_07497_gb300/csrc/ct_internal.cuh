@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "ct.h"
+#include "dfloat.cuh"
 
 namespace ct {
 
@@ -54,13 +55,15 @@ struct Csr {
 
 // Per-slice conjugate-gradient scalars, resident on the device.
 struct CgSlice {
-    double rr;      // r.r of the current residual
-    double rhs2;    // rhs.rhs
-    double alpha;   // step of the current iteration
-    double beta;    // rr_new / rr
-    int32_t active; // 1 while the slice keeps iterating
-    int32_t iters;  // steps taken
-    int32_t status; // CT_OK / CT_ERR_BREAKDOWN / CT_ERR_NONFINITE
+    double rr;       // r.r of the current residual
+    double rhs2;     // rhs.rhs
+    double alpha;    // step of the current iteration
+    double beta;     // rr_new / rr
+    float2 alpha_df; // alpha and beta as double-float pairs for the vector kernels
+    float2 beta_df;
+    int32_t active;  // 1 while the slice keeps iterating
+    int32_t iters;   // steps taken
+    int32_t status;  // CT_OK / CT_ERR_BREAKDOWN / CT_ERR_NONFINITE
     int32_t pad;
 };
 
@@ -87,15 +90,13 @@ struct Workspace {
     int device = -1;
     int32_t batch = 0;
     int64_t n2 = 0, rows = 0;
-    // Solver vectors are FP64 ([len][batch]); the vectors that the sparse
-    // products gather are also kept split as FP32 pairs (hi, lo).
-    double *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *rhs = nullptr;
-    double *atf = nullptr, *u_old = nullptr, *bx = nullptr, *by = nullptr, *vx = nullptr, *vy = nullptr;
-    float2 *u2 = nullptr, *p2 = nullptr;  // split copies of u and p
-    float2* y2 = nullptr;                  // sinogram temp, split [rows][batch]
-    float2* pub_y2 = nullptr;              // ct_adjoint with FP16 storage: s .* y, split
+    // Solver vectors ([len][batch]) are double-float pairs (hi, lo).
+    float2 *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *rhs = nullptr;
+    float2 *atf = nullptr, *u_old = nullptr, *bx = nullptr, *by = nullptr, *vx = nullptr, *vy = nullptr;
+    float2* y = nullptr;                   // sinogram temp [rows][batch]
+    float2* pub_y2 = nullptr;              // ct_adjoint with FP16 storage: s .* y
     int64_t pub_y2_len = 0;
-    double* partials = nullptr;            // reduction partials
+    float2* partials = nullptr;            // reduction partials
     int64_t partials_len = 0;
     unsigned* counter = nullptr;           // last-block counter (one per workspace)
     CgSlice* cg = nullptr;
@@ -142,48 +143,45 @@ int launch_forward(const ct_matrix* M, ValKind vk, const float* x, float* y, int
 int launch_adjoint(const ct_matrix* M, ValKind vk, const float* y, float* x, int32_t batch,
                    float out_scale, bool scale_y, cudaStream_t st);
 
-// Epilogue of the adjoint product inside the CG operator (FP64 vectors).
+// Epilogue of the adjoint product inside the CG operator (double-float vectors).
 struct OpEpilogue {
     int mode;             // 1: q = Op(p) and p.q; 2: r = rhs - Op(u), p = r (CG start);
                           // 3: r = rhs - Op(u) only (residual replacement)
-    double c_id, c_ata, c_grad;
-    const double* in;     // p (mode 1) or u (modes 2, 3)
-    const float2* in2;    // split copy of `in` (for the stencil)
-    double* out;          // q (mode 1) or r (modes 2, 3)
-    double* p_out;        // mode 2: p = r
-    float2* p2_out;       // mode 2: split copy of p
-    const double* rhs;    // modes 2, 3: explicit rhs, or null to build atf + lambda grad^T v
-    const double* atf;    // SB: alpha A^T f
-    const double* vx;     // SB: v = d - b
-    const double* vy;
-    double lam;
+    float2 c_id, c_ata, c_grad;  // coefficients as double-float pairs
+    const float2* in;     // p (mode 1) or u (modes 2, 3)
+    float2* out;          // q (mode 1) or r (modes 2, 3)
+    float2* p_out;        // mode 2: p = r
+    const float2* rhs;    // modes 2, 3: explicit rhs, or null to build atf + lambda grad^T v
+    const float2* atf;    // SB: alpha A^T f
+    const float2* vx;     // SB: v = d - b
+    const float2* vy;
+    float2 lam;
     const int32_t* gate;  // skip all work when *gate != 0 (stopped SB)
     CgSlice* cg;
-    double* partials;
+    float2* partials;
     unsigned* counter;
     double tol;
 };
 
-// solver_ops.cu: extended-precision products used inside the solvers
-// y2 = split(A x) with x gathered from x2 (double-float accumulation);
-// rpow: multiply rows by s^rpow (FP16 storage).
-int launch_forward_df(const ct_matrix* M, ValKind vk, const float2* x2, float2* y2, int rpow,
+// solver_ops.cu: products used inside the solvers (double-float accumulation)
+// y = A x, rows scaled by s^rpow (FP16 storage), gated by cg->active / *gate.
+int launch_forward_df(const ct_matrix* M, ValKind vk, const float2* x, float2* y, int rpow,
                       const CgSlice* cg, const int32_t* gate, cudaStream_t st);
-// out = scale * A^T y2 (FP64), plain store.
-int launch_adjoint_df(const ct_matrix* M, ValKind vk, const float2* y2, double* out, double scale,
+// out = scale * A^T y.
+int launch_adjoint_df(const ct_matrix* M, ValKind vk, const float2* y, float2* out, double scale,
                       cudaStream_t st);
-// A^T y2 fused with the CG operator epilogue.
-int launch_adjoint_op_df(const ct_matrix* M, ValKind vk, const float2* y2, const OpEpilogue& ep,
+// A^T y fused with the CG operator epilogue.
+int launch_adjoint_op_df(const ct_matrix* M, ValKind vk, const float2* y, const OpEpilogue& ep,
                          cudaStream_t st);
 // Surrogate stencil (or no sparse term at all when S is null) fused with the epilogue.
 int launch_stencil_op_df(const ct_matrix* M, const Stencil* S, const OpEpilogue& ep, cudaStream_t st);
 // Public single-slice products with FP32 vectors (same kernel template).
 int launch_forward_f32(const ct_matrix* M, ValKind vk, const float* x, float* y, cudaStream_t st);
-int launch_adjoint_f32(const ct_matrix* M, ValKind vk, const float* y, const float2* y2_scaled, float* x,
+int launch_adjoint_f32(const ct_matrix* M, ValKind vk, const float* y, const float2* y_scaled, float* x,
                        cudaStream_t st);
-// out2 = split(in * scale) for FP32 input (scale may be null).
-int launch_to_split(const ct_matrix* M, const float* in, const float* scale, float2* out2, int64_t len,
-                    cudaStream_t st);
+// out = (in * scale, exactly as a double-float pair) for FP32 input (scale may be null).
+int launch_to_df(const ct_matrix* M, const float* in, const float* scale, float2* out, int64_t len,
+                 cudaStream_t st);
 
 // solve.cu
 int cg_solve(ct_matrix* M, const ct_cg_params* P, const float* rhs, float* u, int32_t batch,

@@ -1,52 +1,41 @@
-// Deterministic FP64 block reductions and the conjugate-gradient scalar
-// updates that follow them.  Included by the kernel translation units.
+// Deterministic grid reductions and the conjugate-gradient scalar updates
+// that follow them.  Per-thread and per-block sums are double-float (FP32
+// pipes); only the grid totals and the CG scalars are FP64, computed by one
+// thread and handed back to the kernels as double-float pairs.
 #pragma once
 
 #include "ct_internal.cuh"
+#include "dfloat.cuh"
 
 namespace ct {
 
-__device__ __forceinline__ double warp_sum_d(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ float warp_sum_f(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Reduces NQ per-thread FP64 values over the block (fixed order), writes the
-// block's partials, and lets the last block to finish sum all partials (fixed
-// order).  Returns true in thread 0 of the last block, with the grid totals
-// in tot[].  The counter is reset by the last block.  blockDim.x <= 1024.
+// Reduces NQ per-thread double-float values over the block (fixed order),
+// writes the block's partials, and lets the last block to finish sum all
+// partials (fixed order).  Returns true in thread 0 of the last block, with
+// the grid totals in tot[].  The counter is reset by the last block.
 template <int NQ>
-__device__ bool grid_reduce_last(const double (&v)[NQ], double* partials, unsigned* counter,
+__device__ bool grid_reduce_last(const float2 (&v)[NQ], float2* partials, unsigned* counter,
                                  double (&tot)[NQ])
 {
-    __shared__ double sh[NQ][32];
+    __shared__ float2 sh[NQ][32];
     __shared__ int last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarp = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        double s = warp_sum_d(v[q]);
+        const float2 s = warp_sum_df(v[q]);
         if (lane == 0) sh[q][warp] = s;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            double s = 0.0;
-            for (int w = 0; w < nwarp; ++w) s += sh[q][w];
+            float2 s = sh[q][0];
+            for (int w = 1; w < nwarp; ++w) s = df_add(s, sh[q][w]);
             partials[(size_t)q * gridDim.x + blockIdx.x] = s;
         }
         __threadfence();
-        unsigned prev = atomicAdd(counter, 1u);
+        const unsigned prev = atomicAdd(counter, 1u);
         last = (prev == gridDim.x - 1);
     }
     __syncthreads();
@@ -54,19 +43,19 @@ __device__ bool grid_reduce_last(const double (&v)[NQ], double* partials, unsign
     __threadfence();
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        double s = 0.0;
+        float2 s = df_zero();
         for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
-            s += __ldcg(partials + (size_t)q * gridDim.x + b);
-        s = warp_sum_d(s);
+            s = df_add(s, __ldcg(partials + (size_t)q * gridDim.x + b));
+        s = warp_sum_df(s);
         if (lane == 0) sh[q][warp] = s;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            double s = 0.0;
-            for (int w = 0; w < nwarp; ++w) s += sh[q][w];
-            tot[q] = s;
+            float2 s = sh[q][0];
+            for (int w = 1; w < nwarp; ++w) s = df_add(s, sh[q][w]);
+            tot[q] = df_to_double(s);
         }
         *counter = 0u;
     }
@@ -83,6 +72,8 @@ __device__ __forceinline__ void cg_after_residual(CgSlice& st, double rr, double
     st.iters = 0;
     st.alpha = 0.0;
     st.beta = 0.0;
+    st.alpha_df = df_zero();
+    st.beta_df = df_zero();
     st.status = CT_OK;
     if (!finite_d(rr) || !finite_d(rhs2)) {
         st.status = CT_ERR_NONFINITE;
@@ -97,6 +88,7 @@ __device__ __forceinline__ void cg_after_pq(CgSlice& st, double pq)
 {
     if (!st.active) {
         st.alpha = 0.0;
+        st.alpha_df = df_zero();
         return;
     }
     if (!finite_d(pq)) {
@@ -110,17 +102,20 @@ __device__ __forceinline__ void cg_after_pq(CgSlice& st, double pq)
     } else {
         st.alpha = st.rr / pq;
     }
+    st.alpha_df = df_from_double(st.alpha);
 }
 
-// u += alpha p, r -= alpha q done and r.r known: the new search direction's beta.
+// u += alpha p, r -= alpha q done and r.r known: the new direction's beta.
 __device__ __forceinline__ void cg_after_update(CgSlice& st, double rr_new, double tol)
 {
     if (!st.active) {
         st.beta = 0.0;
+        st.beta_df = df_zero();
         return;
     }
     st.iters += 1;
     st.beta = rr_new / st.rr;
+    st.beta_df = df_from_double(st.beta);
     st.rr = rr_new;
     if (!finite_d(rr_new)) {
         st.status = CT_ERR_NONFINITE;

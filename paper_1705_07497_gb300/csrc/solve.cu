@@ -6,10 +6,10 @@
 //
 // One CG step is four kernels: y = A p; q = Op(p) fused into the A^T product
 // (with p.q); u += alpha p, r -= alpha q (with r.r); p = r + beta p.  The
-// iteration vectors are FP64 (a fixed number of CG steps amplifies their
-// rounding by orders of magnitude, see solver_ops.cu); each reduction is
-// finished by the last block of its kernel in a fixed order, so results are
-// bitwise reproducible run to run.
+// iteration vectors are double-float pairs (a fixed number of CG steps
+// amplifies their rounding by orders of magnitude, see solver_ops.cu); each
+// reduction is finished by the last block of its kernel in a fixed order, so
+// results are bitwise reproducible run to run.
 #include <cmath>
 #include <cstring>
 
@@ -20,76 +20,78 @@
 namespace ct {
 namespace {
 
-__global__ void __launch_bounds__(256) cg_update_kernel(double* __restrict__ u, float2* __restrict__ u2,
-                                                        double* __restrict__ r,
-                                                        const double* __restrict__ p,
-                                                        const double* __restrict__ q, int64_t len,
-                                                        CgSlice* cg, double tol, double* partials,
+__global__ void __launch_bounds__(256) cg_update_kernel(float2* __restrict__ u, float2* __restrict__ r,
+                                                        const float2* __restrict__ p,
+                                                        const float2* __restrict__ q, int64_t len,
+                                                        CgSlice* cg, double tol, float2* partials,
                                                         unsigned* counter, const int32_t* gate)
 {
     if (gate && *gate) return;
     if (!cg->active) return;
-    const double al = cg->alpha;
-    double d = 0.0;
+    const float2 al = cg->alpha_df;
+    float s = 0.0f, c = 0.0f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const double un = u[i] + al * p[i];
-        u[i] = un;
-        u2[i] = split_f2(un);
-        const double rn = r[i] - al * q[i];
+        u[i] = df_add(u[i], df_mul(al, p[i]));
+        const float2 rn = df_sub(r[i], df_mul(al, q[i]));
         r[i] = rn;
-        d += rn * rn;
+        acc_add(s, c, df_mul(rn, rn));
     }
-    double v[1] = {d}, tot[1];
+    float2 v[1] = {acc_value(s, c)};
+    double tot[1];
     if (grid_reduce_last<1>(v, partials, counter, tot)) cg_after_update(*cg, tot[0], tol);
 }
 
-__global__ void __launch_bounds__(256) cg_direction_kernel(double* __restrict__ p, float2* __restrict__ p2,
-                                                           const double* __restrict__ r, int64_t len,
-                                                           const CgSlice* cg, const int32_t* gate)
+__global__ void __launch_bounds__(256) cg_direction_kernel(float2* __restrict__ p, const float2* __restrict__ r,
+                                                           int64_t len, const CgSlice* cg, const int32_t* gate)
 {
     if (gate && *gate) return;
     if (!cg->active) return;
-    const double be = cg->beta;
+    const float2 be = cg->beta_df;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const double pn = r[i] + be * p[i];
-        p[i] = pn;
-        p2[i] = split_f2(pn);
-    }
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = df_add(r[i], df_mul(be, p[i]));
+}
+
+// shrink(x, gamma) = sign(x) max(|x| - gamma, 0) in double-float.
+__device__ __forceinline__ float2 shrink_df(float2 x, float2 gamma)
+{
+    const float2 ax = df_abs(x);
+    if (!df_gt(ax, gamma)) return df_zero();
+    return x.x < 0.0f ? df_add(x, gamma) : df_sub(x, gamma);
 }
 
 // After the inner solve: g = grad u, d = shrink(g + b, 1/lambda), b += g - d,
 // v = d - b (the next right-hand side's split term), ||u - u_old||_1, u_old = u.
-__global__ void __launch_bounds__(256) sb_shrink_kernel(const double* __restrict__ u,
-                                                        double* __restrict__ u_old,
-                                                        double* __restrict__ bx, double* __restrict__ by,
-                                                        double* __restrict__ vx, double* __restrict__ vy,
-                                                        int n, double gamma, SbSlice* sb,
+__global__ void __launch_bounds__(256) sb_shrink_kernel(const float2* __restrict__ u,
+                                                        float2* __restrict__ u_old,
+                                                        float2* __restrict__ bx, float2* __restrict__ by,
+                                                        float2* __restrict__ vx, float2* __restrict__ vy,
+                                                        int n, float2 gamma, SbSlice* sb,
                                                         const CgSlice* cg, double tol,
-                                                        double* partials, unsigned* counter)
+                                                        float2* partials, unsigned* counter)
 {
     if (sb->stopped) return;
     const int64_t n2 = (int64_t)n * n;
-    double upd = 0.0;
+    float s = 0.0f, cc = 0.0f;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(p / n), j = (int)(p - (int64_t)i * n);
-        const double c = u[p];
-        const double gx = (j < n - 1) ? u[p + 1] - c : 0.0;
-        const double gy = (i < n - 1) ? u[p + n] - c : 0.0;
-        const double tx = gx + bx[p], ty = gy + by[p];
-        const double dx = copysign(fmax(fabs(tx) - gamma, 0.0), tx);
-        const double dy = copysign(fmax(fabs(ty) - gamma, 0.0), ty);
-        const double bxn = tx - dx, byn = ty - dy;
+        const float2 c = u[p];
+        const float2 gx = (j < n - 1) ? df_sub(u[p + 1], c) : df_zero();
+        const float2 gy = (i < n - 1) ? df_sub(u[p + n], c) : df_zero();
+        const float2 tx = df_add(gx, bx[p]), ty = df_add(gy, by[p]);
+        const float2 dx = shrink_df(tx, gamma), dy = shrink_df(ty, gamma);
+        const float2 bxn = df_sub(tx, dx), byn = df_sub(ty, dy);
         bx[p] = bxn;
         by[p] = byn;
-        vx[p] = dx - bxn;
-        vy[p] = dy - byn;
-        upd += fabs(c - u_old[p]);
+        vx[p] = df_sub(dx, bxn);
+        vy[p] = df_sub(dy, byn);
+        acc_add(s, cc, df_abs(df_sub(c, u_old[p])));
         u_old[p] = c;
     }
-    double v[1] = {upd}, tot[1];
+    float2 v[1] = {acc_value(s, cc)};
+    double tot[1];
     if (grid_reduce_last<1>(v, partials, counter, tot)) {
         if (cg->status != CT_OK) {
             sb->status = cg->status;
@@ -100,23 +102,19 @@ __global__ void __launch_bounds__(256) sb_shrink_kernel(const double* __restrict
     }
 }
 
-// FP32 caller vector -> FP64 (and its split copy when u2 is given).
-__global__ void widen_kernel(const float* __restrict__ in, double* __restrict__ out,
-                             float2* __restrict__ out2, int64_t len)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float v = in[i];
-        out[i] = (double)v;
-        if (out2) out2[i] = make_float2(v, 0.0f);
-    }
-}
-
-__global__ void narrow_kernel(const double* __restrict__ in, float* __restrict__ out, int64_t len)
+// FP32 caller vector -> double-float.
+__global__ void widen_kernel(const float* __restrict__ in, float2* __restrict__ out, int64_t len)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
          i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = __double2float_rn(in[i]);
+        out[i] = make_float2(in[i], 0.0f);
+}
+
+__global__ void narrow_kernel(const float2* __restrict__ in, float* __restrict__ out, int64_t len)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = df_to_float(in[i]);
 }
 
 template <typename T>
@@ -141,52 +139,49 @@ struct Plan {
     int refresh;       // residual replacement period (FP16 storage), 0 = off
 };
 
-// Op applied to `in` (split copy in2) with the given epilogue.
-int apply_op(const Plan& P, OpEpilogue ep, const double* in, const float2* in2, cudaStream_t st,
-             bool fp32_refresh = false)
+// Op applied to `in` with the given epilogue (y = A in, then A^T y fused).
+int apply_op(const Plan& P, OpEpilogue ep, const float2* in, cudaStream_t st, bool fp32_refresh = false)
 {
     Workspace& w = P.M->ws;
     ep.in = in;
-    ep.in2 = in2;
     if (P.sparse) {
         const ValKind vk = fp32_refresh ? ValKind::F32 : P.vk;
-        CT_CHECK(launch_forward_df(P.M, vk, in2, w.y2, vk == ValKind::F16 ? 2 : 0,
+        CT_CHECK(launch_forward_df(P.M, vk, in, w.y, vk == ValKind::F16 ? 2 : 0,
                                    ep.mode == 2 ? nullptr : ep.cg, ep.gate, st));
-        CT_CHECK(launch_adjoint_op_df(P.M, vk, w.y2, ep, st));
+        CT_CHECK(launch_adjoint_op_df(P.M, vk, w.y, ep, st));
     } else {
         CT_CHECK(launch_stencil_op_df(P.M, P.S, ep, st));
     }
     return CT_OK;
 }
 
-// Residual r = rhs - Op(u), p = r, then `iters` CG steps on the FP64 iterate w.u.
-int enqueue_cg(const Plan& P, const double* rhs, int iters, cudaStream_t st)
+// Residual r = rhs - Op(u), p = r, then `iters` CG steps on the iterate w.u.
+int enqueue_cg(const Plan& P, const float2* rhs, int iters, cudaStream_t st)
 {
     Workspace& w = P.M->ws;
     OpEpilogue ep = P.base;
     ep.mode = 2;
     ep.out = w.r;
     ep.p_out = w.p;
-    ep.p2_out = w.p2;
     ep.rhs = rhs;
-    CT_CHECK(apply_op(P, ep, w.u, w.u2, st));
+    CT_CHECK(apply_op(P, ep, w.u, st));
     const int gv = grid_for(P.M, P.n2, 256, 8);
     for (int it = 0; it < iters; ++it) {
         OpEpilogue e1 = P.base;
         e1.mode = 1;
         e1.out = w.q;
-        CT_CHECK(apply_op(P, e1, w.p, w.p2, st));
-        cg_update_kernel<<<gv, 256, 0, st>>>(w.u, w.u2, w.r, w.p, w.q, P.n2, w.cg, P.base.tol,
-                                             w.partials, w.counter, P.base.gate);
+        CT_CHECK(apply_op(P, e1, w.p, st));
+        cg_update_kernel<<<gv, 256, 0, st>>>(w.u, w.r, w.p, w.q, P.n2, w.cg, P.base.tol, w.partials,
+                                             w.counter, P.base.gate);
         CT_CUDA(cudaGetLastError());
-        cg_direction_kernel<<<gv, 256, 0, st>>>(w.p, w.p2, w.r, P.n2, w.cg, P.base.gate);
+        cg_direction_kernel<<<gv, 256, 0, st>>>(w.p, w.r, P.n2, w.cg, P.base.gate);
         CT_CUDA(cudaGetLastError());
         if (P.refresh > 0 && (it + 1) % P.refresh == 0 && it + 1 < iters) {
             OpEpilogue e3 = P.base;
             e3.mode = 3;
             e3.out = w.r;
             e3.rhs = rhs;
-            CT_CHECK(apply_op(P, e3, w.u, w.u2, st, true));
+            CT_CHECK(apply_op(P, e3, w.u, st, true));
         }
     }
     return CT_OK;
@@ -216,9 +211,9 @@ int make_plan(ct_matrix* M, double c_id, double c_ata, double c_grad, double tol
     Workspace& w = M->ws;
     OpEpilogue& b = P.base;
     std::memset(&b, 0, sizeof(b));
-    b.c_id = c_id;
-    b.c_ata = c_ata;
-    b.c_grad = c_grad;
+    b.c_id = df_from_double(c_id);
+    b.c_ata = df_from_double(c_ata);
+    b.c_grad = df_from_double(c_grad);
     b.cg = w.cg;
     b.partials = w.partials;
     b.counter = w.counter;
@@ -230,12 +225,8 @@ int make_plan(ct_matrix* M, double c_id, double c_ata, double c_grad, double tol
 
 void free_workspace(Workspace& w)
 {
-    double* ds[] = {w.u, w.r, w.p, w.q, w.rhs, w.atf, w.u_old, w.bx, w.by, w.vx, w.vy};
-    for (double* d : ds) cudaFree(d);
-    cudaFree(w.u2);
-    cudaFree(w.p2);
-    cudaFree(w.y2);
-    cudaFree(w.pub_y2);
+    float2* vs[] = {w.u, w.r, w.p, w.q, w.rhs, w.atf, w.u_old, w.bx, w.by, w.vx, w.vy, w.y, w.pub_y2};
+    for (float2* v : vs) cudaFree(v);
     cudaFree(w.stage_a);
     cudaFree(w.stage_b);
     cudaFree(w.partials);
@@ -271,11 +262,9 @@ int ensure_workspace(ct_matrix* M, int32_t batch, bool /*solver*/)
     w.n2 = M->cols;
     w.rows = M->rows;
     const int64_t nv = w.n2 * batch;
-    double** ds[] = {&w.u, &w.r, &w.p, &w.q, &w.rhs, &w.atf, &w.u_old, &w.bx, &w.by, &w.vx, &w.vy};
-    for (double** d : ds) CT_CHECK(alloc_n(d, nv));
-    CT_CHECK(alloc_n(&w.u2, nv));
-    CT_CHECK(alloc_n(&w.p2, nv));
-    CT_CHECK(alloc_n(&w.y2, w.rows * batch));
+    float2** vs[] = {&w.u, &w.r, &w.p, &w.q, &w.rhs, &w.atf, &w.u_old, &w.bx, &w.by, &w.vx, &w.vy};
+    for (float2** v : vs) CT_CHECK(alloc_n(v, nv));
+    CT_CHECK(alloc_n(&w.y, w.rows * batch));
     w.partials_len = (int64_t)4 * (M->sm_count > 0 ? M->sm_count : 148) * 8 * batch;
     CT_CHECK(alloc_n(&w.partials, w.partials_len));
     CT_CHECK(alloc_n(&w.counter, 16));
@@ -299,8 +288,8 @@ int cg_solve(ct_matrix* M, const ct_cg_params* Pp, const float* rhs, float* u, i
     CT_CHECK(make_plan(M, Pp->c_id, Pp->c_ata, Pp->c_grad, Pp->rel_tol, Pp->surrogate_r,
                        Pp->surrogate_square, Pp->refresh_every, P));
     const int gv = grid_for(M, P.n2, 256, 8);
-    widen_kernel<<<gv, 256, 0, st>>>(rhs, w.rhs, nullptr, P.n2);
-    widen_kernel<<<gv, 256, 0, st>>>(u, w.u, w.u2, P.n2);
+    widen_kernel<<<gv, 256, 0, st>>>(rhs, w.rhs, P.n2);
+    widen_kernel<<<gv, 256, 0, st>>>(u, w.u, P.n2);
     CT_CUDA(cudaGetLastError());
     CT_CHECK(enqueue_cg(P, w.rhs, Pp->max_iters, st));
     narrow_kernel<<<gv, 256, 0, st>>>(w.u, u, P.n2);
@@ -327,7 +316,7 @@ int enqueue_sb_outer(const Plan& P, const ct_sb_params* Sp, cudaStream_t st)
     CT_CHECK(enqueue_cg(P, nullptr, Sp->inner_cg_iters, st));
     const int gv = grid_for(P.M, P.n2, 256, 8);
     sb_shrink_kernel<<<gv, 256, 0, st>>>(w.u, w.u_old, w.bx, w.by, w.vx, w.vy, P.M->g.n,
-                                         1.0 / Sp->lambda, w.sb, w.cg, Sp->stop_rel_update,
+                                         df_from_double(1.0 / Sp->lambda), w.sb, w.cg, Sp->stop_rel_update,
                                          w.partials, w.counter);
     CT_CUDA(cudaGetLastError());
     return CT_OK;
@@ -350,22 +339,22 @@ int split_bregman(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u
     P.base.atf = w.atf;
     P.base.vx = w.vx;
     P.base.vy = w.vy;
-    P.base.lam = Sp->lambda;
+    P.base.lam = df_from_double(Sp->lambda);
     const int64_t n2 = P.n2;
     const int gv = grid_for(M, n2, 256, 8);
     // alpha A^T f, once (the right-hand side keeps the exact back-projection
     // also with the surrogate, Eq. surr_SBupd); FP16 storage applies A^T as
     // Q^T (s .* f)
-    CT_CHECK(launch_to_split(M, f, P.vk == ValKind::F16 ? M->row_scale : nullptr, w.y2, M->rows, st));
-    CT_CHECK(launch_adjoint_df(M, P.vk, w.y2, w.atf, Sp->alpha, st));
-    widen_kernel<<<gv, 256, 0, st>>>(u, w.u, w.u2, n2);
+    CT_CHECK(launch_to_df(M, f, P.vk == ValKind::F16 ? M->row_scale : nullptr, w.y, M->rows, st));
+    CT_CHECK(launch_adjoint_df(M, P.vk, w.y, w.atf, Sp->alpha, st));
+    widen_kernel<<<gv, 256, 0, st>>>(u, w.u, n2);
     CT_CUDA(cudaGetLastError());
-    CT_CUDA(cudaMemsetAsync(w.bx, 0, n2 * sizeof(double), st));
-    CT_CUDA(cudaMemsetAsync(w.by, 0, n2 * sizeof(double), st));
-    CT_CUDA(cudaMemsetAsync(w.vx, 0, n2 * sizeof(double), st));
-    CT_CUDA(cudaMemsetAsync(w.vy, 0, n2 * sizeof(double), st));
+    CT_CUDA(cudaMemsetAsync(w.bx, 0, n2 * sizeof(float2), st));
+    CT_CUDA(cudaMemsetAsync(w.by, 0, n2 * sizeof(float2), st));
+    CT_CUDA(cudaMemsetAsync(w.vx, 0, n2 * sizeof(float2), st));
+    CT_CUDA(cudaMemsetAsync(w.vy, 0, n2 * sizeof(float2), st));
     CT_CUDA(cudaMemsetAsync(w.sb, 0, sizeof(SbSlice), st));
-    CT_CUDA(cudaMemcpyAsync(w.u_old, w.u, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CT_CUDA(cudaMemcpyAsync(w.u_old, w.u, n2 * sizeof(float2), cudaMemcpyDeviceToDevice, st));
 
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CT_CUDA(cudaStreamIsCapturing(st, &cs));

@@ -21,6 +21,13 @@
 namespace ct {
 namespace {
 
+__device__ __forceinline__ float warp_sum_f(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Dot product of one CSR row with a gathered vector (result in every lane).
 template <typename VT, bool GS>
 __device__ __forceinline__ float row_dot(const CsrView& m, const VT* __restrict__ val, int64_t row,
@@ -192,7 +199,7 @@ int launch_adjoint(const ct_matrix* M, ValKind vk, const float* y, float* x, int
             CT_CUDA(cudaMalloc((void**)&w.pub_y2, (size_t)M->rows * sizeof(float2)));
             w.pub_y2_len = M->rows;
         }
-        CT_CHECK(launch_to_split(M, y, M->row_scale, w.pub_y2, M->rows, st));
+        CT_CHECK(launch_to_df(M, y, M->row_scale, w.pub_y2, M->rows, st));
         return launch_adjoint_f32(M, vk, y, w.pub_y2, x, st);
     }
     StoreArgs a{};
