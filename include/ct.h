@@ -161,6 +161,33 @@ typedef struct {
 int ct_split_bregman(ct_matrix_t A, const ct_sb_params *params, const float *f, float *u,
                      int32_t batch, ct_sb_stats *stats, void *cuda_stream);
 
+/* Allocation-free variant of ct_cg_solve.  The paper has no counterpart.
+ *
+ * Some callers cannot allocate device memory at the moment they need a solve:
+ * a real-time reconstruction loop that must not stall on an allocation (which
+ * can synchronise the device), or a process whose device memory has already
+ * been taken by another allocator, so that a fresh cudaMalloc would fail.
+ * This entry point does the same single-slice CG solve as ct_cg_solve
+ * (batch 1, exact operator: surrogate_r must be 0) but never allocates: its
+ * vectors, reduction buffers and CG scalars live in one fixed scratch array
+ * of CT_NOALLOC_SCRATCH_BYTES that is part of libct.so's device image.
+ *   - Every GPU that loads the library holds this array until the process exits.
+ *   - Problems that need more scratch than the limit (about 40 bytes per pixel
+ *     plus 8 per sinogram sample; N = 512 with 130,500 rays fits) are rejected
+ *     with CT_ERR_ARG and a message giving the size needed.
+ *   - rhs and u must be device pointers (host staging would allocate).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make that
+ *     first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents:
+ *     the call clears what must start at zero itself, but calls whose work
+ *     overlaps on the GPU (other streams, other threads) race on it; serialise
+ *     them.
+ * Arguments, results and errors are otherwise those of ct_cg_solve. */
+#define CT_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+int ct_cg_solve_noalloc(ct_matrix_t A, const ct_cg_params *params, const float *rhs, float *u,
+                        ct_cg_stats *stats, void *cuda_stream);
+
 /* Copies A (which = 0) or A^T (which = 1) to host memory as unpadded CSR:
  * row_ptr[rows+1] (int64), cols[nnz] (int32), vals[nnz] (FP32; with FP16
  * storage, the dequantised s_q * Q_qp).  Pass NULL arrays to query sizes

@@ -184,6 +184,10 @@ int launch_to_df(const ct_matrix* M, const float* in, const float* scale, float2
                  cudaStream_t st);
 
 // solve.cu
+// CG on a caller-prepared workspace view (u, r, p, q, rhs, y, partials,
+// counter and cg must be set; the counter must be zero).
+int cg_solve_in(ct_matrix* M, Workspace& w, const ct_cg_params* P, const float* rhs, float* u,
+                ct_cg_stats* stats, cudaStream_t st);
 int cg_solve(ct_matrix* M, const ct_cg_params* P, const float* rhs, float* u, int32_t batch,
              ct_cg_stats* stats, cudaStream_t st);
 int split_bregman(ct_matrix* M, const ct_sb_params* P, const float* f, float* u, int32_t batch,

@@ -131,6 +131,7 @@ int alloc_n(T** p, int64_t n)
 
 struct Plan {
     ct_matrix* M;
+    Workspace* w;      // vectors, scalars and reduction buffers of this solve
     ValKind vk;
     bool sparse;       // A^T A through the sparse products (else stencil / none)
     const Stencil* S;  // surrogate stencil, or null
@@ -142,7 +143,7 @@ struct Plan {
 // Op applied to `in` with the given epilogue (y = A in, then A^T y fused).
 int apply_op(const Plan& P, OpEpilogue ep, const float2* in, cudaStream_t st, bool fp32_refresh = false)
 {
-    Workspace& w = P.M->ws;
+    Workspace& w = *P.w;
     ep.in = in;
     if (P.sparse) {
         const ValKind vk = fp32_refresh ? ValKind::F32 : P.vk;
@@ -158,7 +159,7 @@ int apply_op(const Plan& P, OpEpilogue ep, const float2* in, cudaStream_t st, bo
 // Residual r = rhs - Op(u), p = r, then `iters` CG steps on the iterate w.u.
 int enqueue_cg(const Plan& P, const float2* rhs, int iters, cudaStream_t st)
 {
-    Workspace& w = P.M->ws;
+    Workspace& w = *P.w;
     OpEpilogue ep = P.base;
     ep.mode = 2;
     ep.out = w.r;
@@ -187,10 +188,11 @@ int enqueue_cg(const Plan& P, const float2* rhs, int iters, cudaStream_t st)
     return CT_OK;
 }
 
-int make_plan(ct_matrix* M, double c_id, double c_ata, double c_grad, double tol, int surr_r,
+int make_plan(ct_matrix* M, Workspace* ws, double c_id, double c_ata, double c_grad, double tol, int surr_r,
               int surr_square, int refresh, Plan& P)
 {
     P.M = M;
+    P.w = ws;
     P.vk = (M->flags & CT_VAL_FP16_ROWSCALE) ? ValKind::F16 : ValKind::F32;
     P.S = nullptr;
     if (surr_r > 0) {
@@ -208,7 +210,7 @@ int make_plan(ct_matrix* M, double c_id, double c_ata, double c_grad, double tol
         if (!P.sparse) refresh = 0;
     }
     P.refresh = refresh;
-    Workspace& w = M->ws;
+    Workspace& w = *ws;
     OpEpilogue& b = P.base;
     std::memset(&b, 0, sizeof(b));
     b.c_id = df_from_double(c_id);
@@ -277,15 +279,11 @@ int ensure_workspace(ct_matrix* M, int32_t batch, bool /*solver*/)
     return CT_OK;
 }
 
-int cg_solve(ct_matrix* M, const ct_cg_params* Pp, const float* rhs, float* u, int32_t batch,
-             ct_cg_stats* stats, cudaStream_t st)
+int cg_solve_in(ct_matrix* M, Workspace& w, const ct_cg_params* Pp, const float* rhs, float* u,
+                ct_cg_stats* stats, cudaStream_t st)
 {
-    if (batch != 1) return fail(CT_ERR_UNSUPPORTED, "ct_cg_solve: batch > 1 is not available yet");
-    if (Pp->max_iters < 0) return fail(CT_ERR_ARG, "max_iters < 0");
-    CT_CHECK(ensure_workspace(M, batch, true));
-    Workspace& w = M->ws;
     Plan P;
-    CT_CHECK(make_plan(M, Pp->c_id, Pp->c_ata, Pp->c_grad, Pp->rel_tol, Pp->surrogate_r,
+    CT_CHECK(make_plan(M, &w, Pp->c_id, Pp->c_ata, Pp->c_grad, Pp->rel_tol, Pp->surrogate_r,
                        Pp->surrogate_square, Pp->refresh_every, P));
     const int gv = grid_for(M, P.n2, 256, 8);
     widen_kernel<<<gv, 256, 0, st>>>(rhs, w.rhs, P.n2);
@@ -308,11 +306,20 @@ int cg_solve(ct_matrix* M, const ct_cg_params* Pp, const float* rhs, float* u, i
     return CT_OK;
 }
 
+int cg_solve(ct_matrix* M, const ct_cg_params* Pp, const float* rhs, float* u, int32_t batch,
+             ct_cg_stats* stats, cudaStream_t st)
+{
+    if (batch != 1) return fail(CT_ERR_UNSUPPORTED, "ct_cg_solve: batch > 1 is not available yet");
+    if (Pp->max_iters < 0) return fail(CT_ERR_ARG, "max_iters < 0");
+    CT_CHECK(ensure_workspace(M, batch, true));
+    return cg_solve_in(M, M->ws, Pp, rhs, u, stats, st);
+}
+
 namespace {
 
 int enqueue_sb_outer(const Plan& P, const ct_sb_params* Sp, cudaStream_t st)
 {
-    Workspace& w = P.M->ws;
+    Workspace& w = *P.w;
     CT_CHECK(enqueue_cg(P, nullptr, Sp->inner_cg_iters, st));
     const int gv = grid_for(P.M, P.n2, 256, 8);
     sb_shrink_kernel<<<gv, 256, 0, st>>>(w.u, w.u_old, w.bx, w.by, w.vx, w.vy, P.M->g.n,
@@ -333,7 +340,7 @@ int split_bregman(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u
     CT_CHECK(ensure_workspace(M, batch, true));
     Workspace& w = M->ws;
     Plan P;
-    CT_CHECK(make_plan(M, 0.0, Sp->alpha, Sp->lambda, 0.0, Sp->surrogate_r, Sp->surrogate_square,
+    CT_CHECK(make_plan(M, &w, 0.0, Sp->alpha, Sp->lambda, 0.0, Sp->surrogate_r, Sp->surrogate_square,
                        Sp->refresh_every, P));
     P.base.gate = &w.sb->stopped;
     P.base.atf = w.atf;

@@ -39,6 +39,7 @@ SYMBOLS = (
     "ct_forward",
     "ct_adjoint",
     "ct_cg_solve",
+    "ct_cg_solve_noalloc",
     "ct_split_bregman",
     "ct_matrix_export",
     "ct_matrix_export_fp16",
@@ -127,6 +128,7 @@ def lib():
         L.ct_forward.argtypes = [vp, vp, vp, i32, vp]
         L.ct_adjoint.argtypes = [vp, vp, vp, i32, vp]
         L.ct_cg_solve.argtypes = [vp, P(CgParams), vp, vp, i32, P(CgStats), vp]
+        L.ct_cg_solve_noalloc.argtypes = [vp, P(CgParams), vp, vp, P(CgStats), vp]
         L.ct_split_bregman.argtypes = [vp, P(SbParams), vp, vp, i32, P(SbStats), vp]
         L.ct_matrix_export.argtypes = [vp, i32, vp, vp, vp]
         L.ct_matrix_export_fp16.argtypes = [vp, vp, vp]
@@ -206,6 +208,14 @@ def ct_cg_solve(h, params, rhs, u, batch, stats=None, stream=None):
     pu, _ = _vec(u)
     sp = ctypes.byref(stats) if stats is not None else None
     return _check(lib().ct_cg_solve(h, ctypes.byref(params), pr, pu, batch, sp, sr if stream is None else stream))
+
+
+def ct_cg_solve_noalloc(h, params, rhs, u, stats=None, stream=None):
+    """ct_cg_solve for one slice on the library's fixed scratch array (no allocation)."""
+    pr, sr = _vec(rhs)
+    pu, _ = _vec(u)
+    sp = ctypes.byref(stats) if stats is not None else None
+    return _check(lib().ct_cg_solve_noalloc(h, ctypes.byref(params), pr, pu, sp, sr if stream is None else stream))
 
 
 def ct_split_bregman(h, params, f, u, batch, stats=None, stream=None):
