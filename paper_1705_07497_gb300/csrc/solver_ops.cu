@@ -12,9 +12,9 @@
 // FP64 pipe is far too narrow for that.
 //
 // Layout of the work: a warp owns a group of 16 consecutive CSR rows and
-// computes their dot products one after the other (each lane streams 8
-// consecutive entries per step: two 16-byte column loads and one or two
-// 16-byte value loads, evict-first; a shuffle reduction per row).  Lane r
+// computes their dot products one after the other (the lanes stream the row
+// interleaved, 8 independent entries per lane in flight, evict-first; a
+// shuffle reduction per row).  Lane r
 // keeps row r's total, and the 16 epilogues then run side by side with
 // coalesced vector accesses.  Grid-wide dot products finish in the last block
 // (reduce.cuh).
@@ -39,20 +39,29 @@ __device__ __forceinline__ void store_y(float* y, int64_t i, float2 v) { y[i] = 
 __device__ __forceinline__ void store_y(float2* y, int64_t i, float2 v) { y[i] = v; }
 
 // Dot product of one CSR row with a gathered vector; every lane gets it.
+// Lane l takes entries s + l, s + l + 32, ...: at each step the warp reads 32
+// consecutive entries (coalesced) and gathers 32 consecutive columns, which
+// along a ray or across neighbouring bins are mostly adjacent in memory.
 template <typename VT, typename XT>
 __device__ __forceinline__ float2 row_dot(const CsrView& m, const VT* __restrict__ val, int64_t row,
                                           const XT* __restrict__ x, int lane)
 {
     const int64_t s = m.rp[row], e = m.rp[row + 1];
     float hs = 0.0f, hc = 0.0f;
-    for (int64_t k = s + lane * 8; k < e; k += 256) {
-        const int4 c0 = __ldcs(reinterpret_cast<const int4*>(m.col + k));
-        const int4 c1 = __ldcs(reinterpret_cast<const int4*>(m.col + k + 4));
+    for (int64_t k0 = s + lane; k0 < e; k0 += 8 * 32) {
+        int c[8];
         float v[8];
-        Vals<VT>::load8(val, k, v);
-        const int c[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
 #pragma unroll
-        for (int t = 0; t < 8; ++t) acc_fma(hs, hc, v[t], gather_x(x, c[t]));
+        for (int t = 0; t < 8; ++t) {
+            const int64_t k = k0 + 32 * t;
+            c[t] = k < e ? __ldcs(m.col + k) : -1;
+            v[t] = k < e ? Vals<VT>::one(val, k) : 0.0f;
+        }
+        float2 xv[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) xv[t] = c[t] >= 0 ? gather_x(x, c[t]) : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc_fma(hs, hc, v[t], xv[t]);
     }
     return warp_sum_df(acc_value(hs, hc));
 }

@@ -41,7 +41,7 @@ struct Vals<__half> {
     }
     static __device__ __forceinline__ float one(const __half* v, int64_t k)
     {
-        return __half2float(v[k]);
+        return __half2float(__ldcs(v + k));
     }
 };
 
