@@ -104,6 +104,14 @@ int ct_forward(ct_matrix_t A, const float *x, float *y, int32_t batch, void *cud
  * With FP16 storage: x = Q^T (s .* y). */
 int ct_adjoint(ct_matrix_t A, const float *y, float *x, int32_t batch, void *cuda_stream);
 
+/* FP64-vector forms of ct_forward / ct_adjoint for callers that keep their
+ * vectors in FP64 (the differentiable reconstruction of the Python layer).
+ * Same layout and batching; device pointers only (CT_ERR_ARG otherwise).  The
+ * matrix values are those of the storage form; products accumulate in
+ * double-float (about 48 significant bits) and are returned as FP64. */
+int ct_forward_f64(ct_matrix_t A, const double *x, double *y, int32_t batch, void *cuda_stream);
+int ct_adjoint_f64(ct_matrix_t A, const double *y, double *x, int32_t batch, void *cuda_stream);
+
 typedef struct {
     double c_id, c_ata, c_grad; /* Op = c_id I + c_ata A^T A (or T) + c_grad grad^T grad.
                                    SB (Eq. SB_solve): (0, alpha, lambda);

@@ -155,13 +155,13 @@ int ct_forward(ct_matrix_t A, const float* x, float* y, int32_t batch, void* cud
     CT_CHECK(classify(x, y, &host));
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const ValKind vk = storage_kind(A);
-    if (!host) return launch_forward(A, vk, x, y, batch, 1.0f, false, st);
+    if (!host) return launch_forward(A, vk, x, y, batch, st);
     Workspace& w = A->ws;
     const int64_t nx = A->cols * batch, ny = A->rows * batch;
     CT_CHECK(ensure_stage(&w.stage_a, &w.stage_a_len, nx));
     CT_CHECK(ensure_stage(&w.stage_b, &w.stage_b_len, ny));
     CT_CUDA(cudaMemcpyAsync(w.stage_a, x, nx * sizeof(float), cudaMemcpyHostToDevice, st));
-    CT_CHECK(launch_forward(A, vk, w.stage_a, w.stage_b, batch, 1.0f, false, st));
+    CT_CHECK(launch_forward(A, vk, w.stage_a, w.stage_b, batch, st));
     CT_CUDA(cudaMemcpyAsync(y, w.stage_b, ny * sizeof(float), cudaMemcpyDeviceToHost, st));
     CT_CUDA(cudaStreamSynchronize(st));
     return CT_OK;
@@ -175,16 +175,36 @@ int ct_adjoint(ct_matrix_t A, const float* y, float* x, int32_t batch, void* cud
     CT_CHECK(classify(y, x, &host));
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const ValKind vk = storage_kind(A);
-    if (!host) return launch_adjoint(A, vk, y, x, batch, 1.0f, true, st);
+    if (!host) return launch_adjoint(A, vk, y, x, batch, st);
     Workspace& w = A->ws;
     const int64_t nx = A->cols * batch, ny = A->rows * batch;
     CT_CHECK(ensure_stage(&w.stage_a, &w.stage_a_len, nx));
     CT_CHECK(ensure_stage(&w.stage_b, &w.stage_b_len, ny));
     CT_CUDA(cudaMemcpyAsync(w.stage_b, y, ny * sizeof(float), cudaMemcpyHostToDevice, st));
-    CT_CHECK(launch_adjoint(A, vk, w.stage_b, w.stage_a, batch, 1.0f, true, st));
+    CT_CHECK(launch_adjoint(A, vk, w.stage_b, w.stage_a, batch, st));
     CT_CUDA(cudaMemcpyAsync(x, w.stage_a, nx * sizeof(float), cudaMemcpyDeviceToHost, st));
     CT_CUDA(cudaStreamSynchronize(st));
     return CT_OK;
+}
+
+int ct_forward_f64(ct_matrix_t A, const double* x, double* y, int32_t batch, void* cuda_stream)
+{
+    CT_CHECK(check_handle(A));
+    if (batch < 1) return fail(CT_ERR_ARG, "batch must be >= 1");
+    int host = 0;
+    CT_CHECK(classify(x, y, &host));
+    if (host) return fail(CT_ERR_ARG, "ct_forward_f64 needs device pointers");
+    return launch_forward_f64(A, storage_kind(A), x, y, batch, (cudaStream_t)cuda_stream);
+}
+
+int ct_adjoint_f64(ct_matrix_t A, const double* y, double* x, int32_t batch, void* cuda_stream)
+{
+    CT_CHECK(check_handle(A));
+    if (batch < 1) return fail(CT_ERR_ARG, "batch must be >= 1");
+    int host = 0;
+    CT_CHECK(classify(y, x, &host));
+    if (host) return fail(CT_ERR_ARG, "ct_adjoint_f64 needs device pointers");
+    return launch_adjoint_f64(A, storage_kind(A), y, x, batch, (cudaStream_t)cuda_stream);
 }
 
 int ct_cg_solve(ct_matrix_t A, const ct_cg_params* params, const float* rhs, float* u,

@@ -94,8 +94,10 @@ struct Workspace {
     float2 *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *rhs = nullptr;
     float2 *atf = nullptr, *u_old = nullptr, *bx = nullptr, *by = nullptr, *vx = nullptr, *vy = nullptr;
     float2* y = nullptr;                   // sinogram temp [rows][batch]
-    float2* pub_y2 = nullptr;              // ct_adjoint with FP16 storage: s .* y
+    float2* pub_y2 = nullptr;              // public products: sinogram-side double-float buffer
     int64_t pub_y2_len = 0;
+    float2* pub_x2 = nullptr;              // public FP64 products: image-side buffer
+    int64_t pub_x2_len = 0;
     float2* partials = nullptr;            // reduction partials
     int64_t partials_len = 0;
     unsigned* counter = nullptr;           // last-block counter (one per workspace)
@@ -138,10 +140,10 @@ void free_workspace(Workspace& w);
 
 // spmv.cu
 enum class ValKind { F32 = 0, F16 = 1 };
-int launch_forward(const ct_matrix* M, ValKind vk, const float* x, float* y, int32_t batch,
-                   float out_scale, bool scale_sq, cudaStream_t st);
-int launch_adjoint(const ct_matrix* M, ValKind vk, const float* y, float* x, int32_t batch,
-                   float out_scale, bool scale_y, cudaStream_t st);
+int launch_forward(const ct_matrix* M, ValKind vk, const float* x, float* y, int32_t batch, cudaStream_t st);
+int launch_adjoint(const ct_matrix* M, ValKind vk, const float* y, float* x, int32_t batch, cudaStream_t st);
+int launch_forward_f64(const ct_matrix* M, ValKind vk, const double* x, double* y, int32_t batch, cudaStream_t st);
+int launch_adjoint_f64(const ct_matrix* M, ValKind vk, const double* y, double* x, int32_t batch, cudaStream_t st);
 
 // Epilogue of the adjoint product inside the CG operator (double-float vectors).
 struct OpEpilogue {
@@ -194,5 +196,17 @@ int split_bregman(ct_matrix* M, const ct_sb_params* P, const float* f, float* u,
                   ct_sb_stats* stats, cudaStream_t st);
 
 int grid_for(const ct_matrix* M, int64_t work_items, int items_per_block, int max_per_sm);
+
+// batch.cu: many slices sharing one geometry (vectors [len][B])
+// which = 0: y = A x; which = 1: x = A^T y (FP32 vectors, double-float accumulation).
+int batched_forward_adjoint(const ct_matrix* M, int which, const float* in, float* out, int32_t B,
+                            cudaStream_t st);
+// Double-float in and out (which = 0: A, which = 1: A^T; FP16 storage: A^T
+// expects its input already multiplied by the row scale).
+int batched_product_df(const ct_matrix* M, int which, const float2* in, float2* out, int32_t B, cudaStream_t st);
+int cg_solve_batched(ct_matrix* M, const ct_cg_params* P, const float* rhs, float* u, int32_t B,
+                     ct_cg_stats* stats, cudaStream_t st);
+int split_bregman_batched(ct_matrix* M, const ct_sb_params* P, const float* f, float* u, int32_t B,
+                          ct_sb_stats* stats, cudaStream_t st);
 
 }  // namespace ct

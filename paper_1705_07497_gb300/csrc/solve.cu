@@ -227,7 +227,7 @@ int make_plan(ct_matrix* M, Workspace* ws, double c_id, double c_ata, double c_g
 
 void free_workspace(Workspace& w)
 {
-    float2* vs[] = {w.u, w.r, w.p, w.q, w.rhs, w.atf, w.u_old, w.bx, w.by, w.vx, w.vy, w.y, w.pub_y2};
+    float2* vs[] = {w.u, w.r, w.p, w.q, w.rhs, w.atf, w.u_old, w.bx, w.by, w.vx, w.vy, w.y, w.pub_y2, w.pub_x2};
     for (float2* v : vs) cudaFree(v);
     cudaFree(w.stage_a);
     cudaFree(w.stage_b);
@@ -248,10 +248,12 @@ int ensure_workspace(ct_matrix* M, int32_t batch, bool /*solver*/)
     float* sa = w.stage_a;
     float* sb = w.stage_b;
     float2* py = w.pub_y2;
-    const int64_t la = w.stage_a_len, lb = w.stage_b_len, lp = w.pub_y2_len;
+    float2* px = w.pub_x2;
+    const int64_t la = w.stage_a_len, lb = w.stage_b_len, lp = w.pub_y2_len, lx = w.pub_x2_len;
     w.cap_stream = nullptr;
     w.stage_a = w.stage_b = nullptr;
     w.pub_y2 = nullptr;
+    w.pub_x2 = nullptr;
     free_workspace(w);
     w.cap_stream = keep;
     w.stage_a = sa;
@@ -260,6 +262,8 @@ int ensure_workspace(ct_matrix* M, int32_t batch, bool /*solver*/)
     w.stage_a_len = la;
     w.stage_b_len = lb;
     w.pub_y2_len = lp;
+    w.pub_x2 = px;
+    w.pub_x2_len = lx;
     w.batch = batch;
     w.n2 = M->cols;
     w.rows = M->rows;
@@ -309,8 +313,8 @@ int cg_solve_in(ct_matrix* M, Workspace& w, const ct_cg_params* Pp, const float*
 int cg_solve(ct_matrix* M, const ct_cg_params* Pp, const float* rhs, float* u, int32_t batch,
              ct_cg_stats* stats, cudaStream_t st)
 {
-    if (batch != 1) return fail(CT_ERR_UNSUPPORTED, "ct_cg_solve: batch > 1 is not available yet");
     if (Pp->max_iters < 0) return fail(CT_ERR_ARG, "max_iters < 0");
+    if (batch != 1) return cg_solve_batched(M, Pp, rhs, u, batch, stats, st);
     CT_CHECK(ensure_workspace(M, batch, true));
     return cg_solve_in(M, M->ws, Pp, rhs, u, stats, st);
 }
@@ -334,9 +338,9 @@ int enqueue_sb_outer(const Plan& P, const ct_sb_params* Sp, cudaStream_t st)
 int split_bregman(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u, int32_t batch,
                   ct_sb_stats* stats, cudaStream_t st)
 {
-    if (batch != 1) return fail(CT_ERR_UNSUPPORTED, "ct_split_bregman: batch > 1 is not available yet");
     if (!(Sp->lambda > 0.0) || Sp->outer_iters < 0 || Sp->inner_cg_iters < 0)
         return fail(CT_ERR_ARG, "split Bregman needs lambda > 0 and non-negative iteration counts");
+    if (batch != 1) return split_bregman_batched(M, Sp, f, u, batch, stats, st);
     CT_CHECK(ensure_workspace(M, batch, true));
     Workspace& w = M->ws;
     Plan P;

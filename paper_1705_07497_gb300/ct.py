@@ -38,6 +38,8 @@ SYMBOLS = (
     "ct_destroy_matrix",
     "ct_forward",
     "ct_adjoint",
+    "ct_forward_f64",
+    "ct_adjoint_f64",
     "ct_cg_solve",
     "ct_cg_solve_noalloc",
     "ct_split_bregman",
@@ -127,6 +129,8 @@ def lib():
         L.ct_destroy_matrix.restype = None
         L.ct_forward.argtypes = [vp, vp, vp, i32, vp]
         L.ct_adjoint.argtypes = [vp, vp, vp, i32, vp]
+        L.ct_forward_f64.argtypes = [vp, vp, vp, i32, vp]
+        L.ct_adjoint_f64.argtypes = [vp, vp, vp, i32, vp]
         L.ct_cg_solve.argtypes = [vp, P(CgParams), vp, vp, i32, P(CgStats), vp]
         L.ct_cg_solve_noalloc.argtypes = [vp, P(CgParams), vp, vp, P(CgStats), vp]
         L.ct_split_bregman.argtypes = [vp, P(SbParams), vp, vp, i32, P(SbStats), vp]
@@ -154,20 +158,22 @@ def _check(code):
     return code
 
 
-def _vec(x):
-    """(pointer, stream handle) of a float32 contiguous tensor or array."""
+def _vec(x, f64=False):
+    """(pointer, stream handle) of a contiguous float32 (or float64) tensor or array."""
     try:
         import torch
     except ImportError:  # pragma: no cover
         torch = None
     if torch is not None and isinstance(x, torch.Tensor):
-        if x.dtype != torch.float32 or not x.is_contiguous():
-            raise TypeError("expected a contiguous float32 tensor")
+        want = torch.float64 if f64 else torch.float32
+        if x.dtype != want or not x.is_contiguous():
+            raise TypeError("expected a contiguous %s tensor" % want)
         stream = torch.cuda.current_stream(x.device).cuda_stream if x.is_cuda else 0
         return x.data_ptr(), stream
     if isinstance(x, np.ndarray):
-        if x.dtype != np.float32 or not x.flags["C_CONTIGUOUS"]:
-            raise TypeError("expected a C-contiguous float32 array")
+        want = np.float64 if f64 else np.float32
+        if x.dtype != want or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError("expected a C-contiguous %s array" % np.dtype(want).name)
         return x.ctypes.data, 0
     raise TypeError("expected a torch tensor or numpy array, got %r" % type(x))
 
@@ -201,6 +207,18 @@ def ct_adjoint(h, y, x, batch, stream=None):
     py, sy = _vec(y)
     px, _ = _vec(x)
     return _check(lib().ct_adjoint(h, py, px, batch, sy if stream is None else stream))
+
+
+def ct_forward_f64(h, x, y, batch, stream=None):
+    px, sx = _vec(x, f64=True)
+    py, _ = _vec(y, f64=True)
+    return _check(lib().ct_forward_f64(h, px, py, batch, sx if stream is None else stream))
+
+
+def ct_adjoint_f64(h, y, x, batch, stream=None):
+    py, sy = _vec(y, f64=True)
+    px, _ = _vec(x, f64=True)
+    return _check(lib().ct_adjoint_f64(h, py, px, batch, sy if stream is None else stream))
 
 
 def ct_cg_solve(h, params, rhs, u, batch, stats=None, stream=None):
@@ -257,6 +275,11 @@ def ct_surrogate_stencil(h, r, square=False):
     return {(int(a), int(b)): float(v) for a, b, v in zip(di, dj, w)}
 
 
+def _is_f64(x):
+    dt = getattr(x, "dtype", None)
+    return str(dt) in ("torch.float64", "float64")
+
+
 # ---------------------------------------------------------------------------
 # convenience wrapper
 # ---------------------------------------------------------------------------
@@ -288,11 +311,15 @@ class Matrix:
         return total // length
 
     def forward(self, x, y):
-        ct_forward(self.handle, x, y, self._batch(x, self.cols))
+        """y = A x; float64 tensors use the FP64-vector entry point."""
+        fn = ct_forward_f64 if _is_f64(x) else ct_forward
+        fn(self.handle, x, y, self._batch(x, self.cols))
         return y
 
     def adjoint(self, y, x):
-        ct_adjoint(self.handle, y, x, self._batch(y, self.rows))
+        """x = A^T y; float64 tensors use the FP64-vector entry point."""
+        fn = ct_adjoint_f64 if _is_f64(y) else ct_adjoint
+        fn(self.handle, y, x, self._batch(y, self.rows))
         return x
 
     def cg_solve(self, rhs, u, c_id, c_ata, c_grad, max_iters, rel_tol=0.0, surrogate_r=0,

@@ -1,0 +1,225 @@
+"""Batched solvers and the FP16 storage form against the FP64 oracle.
+
+Batches put the slice index innermost ([N*N][B], [rows][B]); each slice is an
+independent problem and is compared with its own oracle run.  The FP16 form
+(A = diag(s) Q, Q in binary16) is compared bit for bit with the oracle's
+quantisation, its products with the oracle's dequantised matrix, and its
+reconstructions both with the dequantised oracle (kernel error) and with the
+unquantised FP64 oracle (the storage error, stated and bounded by 1e-3).
+"""
+
+import functools
+
+import numpy as np
+import pytest
+
+from oracle import radon, tv
+from paper_1705_07497_gb300 import ct, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GEOM64 = (64, 90, 3, 91)
+FP16 = ct.CT_VAL_FP16_ROWSCALE
+FP16_COPY = ct.CT_VAL_FP16_ROWSCALE | ct.CT_KEEP_FP32_COPY
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    d = torch.device("cuda:0")
+    torch.cuda.set_device(d)
+    return d
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_A(*geom):
+    return radon.siddon_matrix(*geom)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_A16(*geom):
+    s, Q = radon.quantize_rowscale(oracle_A(*geom))
+    return radon.dequantize(s, Q).tocsr(), s, Q
+
+
+@functools.lru_cache(maxsize=None)
+def gpu_A(geom, flags=0):
+    return ct.Matrix(*geom, flags)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def t32(x, dev):
+    return torch.tensor(np.asarray(x), dtype=torch.float32, device=dev)
+
+
+def _data(geom, seeds, A):
+    n = geom[0]
+    truths = [inputs.ellipse_phantom(n, s) for s in seeds]
+    return truths, np.stack([A @ t.ravel() for t in truths], axis=1)
+
+
+@pytest.mark.parametrize("B", [3, 40])
+def test_batched_cg_matches_per_slice_oracle(dev, B):
+    ref = oracle_A(*GEOM64)
+    M = gpu_A(GEOM64)
+    n2 = M.cols
+    rhs = inputs.random_vector(n2 * B, 60).reshape(n2, B)
+    u0 = 0.1 * inputs.random_vector(n2 * B, 61).reshape(n2, B)
+    op = tv.make_operator(ref, (64, 64), 0.0, 1.0, 0.1)
+    u = t32(u0, dev)
+    st = M.cg_solve(t32(rhs, dev), u, 0.0, 1.0, 0.1, 10)
+    assert st["status"] == 0 and st["iters"] == 10
+    got = u.cpu().numpy()
+    for b in range(B):
+        want, _ = tv.cg(op, rhs[:, b], u0[:, b], 10)
+        assert rel(got[:, b], want) <= 1e-4, b
+
+
+def test_batched_cg_slices_stop_independently(dev):
+    """rel_tol: slices converge after different numbers of steps; each stops on its own."""
+    ref = oracle_A(*GEOM64)
+    M = gpu_A(GEOM64)
+    n2 = M.cols
+    B = 3
+    rhs = inputs.random_vector(n2 * B, 62).reshape(n2, B)
+    coef = (1.0, 0.02, 0.0)
+    op = tv.make_operator(ref, (64, 64), *coef)
+    u = torch.zeros((n2, B), device=dev)
+    tols = 1e-4
+    M.cg_solve(t32(rhs, dev), u, *coef, 300, rel_tol=tols)
+    got = u.cpu().numpy()
+    for b in range(B):
+        want, st = tv.cg(op, rhs[:, b], np.zeros(n2), 300, rel_tol=tols)
+        assert st["iters"] < 300
+        assert rel(got[:, b], want) <= 1e-3
+
+
+def test_batched_split_bregman_matches_per_slice_oracle(dev):
+    ref = oracle_A(*GEOM64)
+    M = gpu_A(GEOM64)
+    seeds = [0, 1, 2, 3]
+    truths, F = _data(GEOM64, seeds, ref)
+    u = torch.zeros((M.cols, len(seeds)), device=dev)
+    st = M.split_bregman(t32(F, dev), u, 1.0, 0.1, 20, 10)
+    assert st["status"] == 0 and st["outer_done"] == 20
+    got = u.cpu().numpy()
+    for b in range(len(seeds)):
+        want = tv.split_bregman(ref, F[:, b], (64, 64), 1.0, 0.1, 20, 10)["u"].ravel()
+        assert rel(got[:, b], want) <= 1e-3, b
+
+
+def test_batched_surrogate_split_bregman(dev):
+    ref = oracle_A(*GEOM64)
+    M = gpu_A(GEOM64)
+    truths, F = _data(GEOM64, [5, 6], ref)
+    T = tv.surrogate_matrix(tv.surrogate_stencil(tv.point_response(ref, 64), 3), 64)
+    u = torch.zeros((M.cols, 2), device=dev)
+    st = M.split_bregman(t32(F, dev), u, 1.0, 1.0, 15, 10, surrogate_r=3)
+    assert st["status"] == 0
+    got = u.cpu().numpy()
+    for b in range(2):
+        want = tv.split_bregman(ref, F[:, b], (64, 64), 1.0, 1.0, 15, 10, normal=lambda x: T @ x)["u"].ravel()
+        assert rel(got[:, b], want) <= 1e-3
+
+
+def test_batched_stop_rule_per_slice(dev):
+    ref = oracle_A(*GEOM64)
+    M = gpu_A(GEOM64)
+    truths, F = _data(GEOM64, [0, 9], ref)
+    u = torch.zeros((M.cols, 2), device=dev)
+    st = M.split_bregman(t32(F, dev), u, 1.0, 0.1, 300, 10, stop_rel_update=0.05)
+    dones = [tv.split_bregman(ref, F[:, b], (64, 64), 1.0, 0.1, 300, 10, stop_rel_update=0.05)["outer_done"]
+             for b in range(2)]
+    assert max(dones) < 300
+    assert abs(st["outer_done"] - min(dones)) <= 1
+
+
+# ---------------------------------------------------------------------------
+# FP16 storage with a per-row FP32 scale
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("geom", [GEOM64, (33, 37, 2, 47)])
+def test_fp16_codes_match_oracle_quantisation(dev, geom):
+    A16, s_ref, Q_ref = oracle_A16(*geom)
+    M = gpu_A(geom, FP16)
+    q, s = M.export_fp16()
+    np.testing.assert_array_equal(s, s_ref)
+    np.testing.assert_array_equal(q, Q_ref.data.view(np.uint16))
+
+
+@pytest.mark.parametrize("batch", [1, 5])
+def test_fp16_products_match_dequantised_oracle(dev, batch):
+    A16, _, _ = oracle_A16(*GEOM64)
+    M = gpu_A(GEOM64, FP16)
+    x = inputs.random_vector(M.cols * batch, 63).reshape(M.cols, batch)
+    y = inputs.random_vector(M.rows * batch, 64).reshape(M.rows, batch)
+    yg = torch.empty((M.rows, batch), device=dev)
+    xg = torch.empty((M.cols, batch), device=dev)
+    M.forward(t32(x, dev), yg)
+    M.adjoint(t32(y, dev), xg)
+    assert rel(yg.cpu().numpy(), A16 @ x) <= 1e-5
+    assert rel(xg.cpu().numpy(), A16.T @ y) <= 1e-5
+
+
+@pytest.mark.parametrize("batch", [1, 3])
+def test_fp16_split_bregman(dev, batch):
+    """Kernel error against the dequantised oracle, storage error against FP64."""
+    ref = oracle_A(*GEOM64)
+    A16, _, _ = oracle_A16(*GEOM64)
+    M = gpu_A(GEOM64, FP16)
+    truths, F = _data(GEOM64, list(range(batch)), ref)
+    u = torch.zeros((M.cols, batch), device=dev)
+    M.split_bregman(t32(F, dev), u, 1.0, 0.1, 20, 10)
+    got = u.cpu().numpy()
+    for b in range(batch):
+        want16 = tv.split_bregman(A16, F[:, b], (64, 64), 1.0, 0.1, 20, 10)["u"].ravel()
+        want = tv.split_bregman(ref, F[:, b], (64, 64), 1.0, 0.1, 20, 10)["u"].ravel()
+        assert rel(got[:, b], want16) <= 1e-5
+        assert rel(got[:, b], want) <= 1e-3
+
+
+def test_fp16_refresh_split_bregman_batched(dev):
+    """FP16 products with an FP32-matrix residual replacement every 5 CG steps."""
+    ref = oracle_A(*GEOM64)
+    M = gpu_A(GEOM64, FP16_COPY)
+    truths, F = _data(GEOM64, [3, 4], ref)
+    u = torch.zeros((M.cols, 2), device=dev)
+    st = M.split_bregman(t32(F, dev), u, 1.0, 0.1, 20, 10, refresh_every=5)
+    assert st["status"] == 0
+    got = u.cpu().numpy()
+    for b in range(2):
+        want = tv.split_bregman(ref, F[:, b], (64, 64), 1.0, 0.1, 20, 10)["u"].ravel()
+        assert rel(got[:, b], want) <= 1e-3
+
+
+def test_fp16_refresh_needs_fp32_copy(dev):
+    M = gpu_A(GEOM64, FP16)
+    u = torch.zeros(M.cols, device=dev)
+    with pytest.raises(ct.CtError) as ei:
+        M.cg_solve(torch.ones(M.cols, device=dev), u, 0.0, 1.0, 1.0, 10, refresh_every=5)
+    assert ei.value.code == ct.CT_ERR_UNSUPPORTED
+
+
+def test_batched_512_fp16_first_update(dev):
+    """8 slices of the 512x512 geometry, FP16 storage with FP32 refresh every 5
+    steps, Poisson noise at 1e4 counts: the first Bregman update of slices 0 and 7
+    against the FP64 oracle (later updates of this workload are chaotic in FP64
+    itself)."""
+    geom = (512, 720, 4, 725)
+    ref = oracle_A(*geom)
+    M = ct.Matrix(*geom, FP16_COPY)
+    B = 8
+    F = np.stack([inputs.poisson_noisy(ref @ inputs.ellipse_phantom(512, 2000 + b).ravel(), 1e4, 2500 + b)
+                  for b in range(B)], axis=1)
+    u = torch.zeros((M.cols, B), device=dev)
+    st = M.split_bregman(t32(F, dev), u, 1.0, 1.0, 1, 20, refresh_every=5)
+    assert st["status"] == 0 and st["outer_done"] == 1
+    got = u.cpu().numpy()
+    for b in (0, B - 1):
+        want = tv.split_bregman(ref, F[:, b], (512, 512), 1.0, 1.0, 1, 20)["u"].ravel()
+        assert rel(got[:, b], want) <= 1e-3, b
+    M.close()
