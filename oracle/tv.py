@@ -61,8 +61,14 @@ def grad_adj(wx, wy):
 
 
 def shrink(x, gamma):
-    """Soft thresholding sign(x) max(|x| - gamma, 0)."""
-    return np.sign(x) * np.maximum(np.abs(x) - gamma, 0.0)
+    """Soft thresholding sign(x) max(|x| - gamma, 0).
+
+    Written as x - gamma sign(x) where |x| > gamma, else 0, with the branch
+    decided on the real part: the same values for real x, and the analytic
+    continuation of the active branch for complex x (complex-step
+    differentiation evaluates the oracle at f + i h d)."""
+    xr = np.real(x)
+    return np.where(np.abs(xr) > gamma, x - gamma * np.sign(xr), 0.0 * x)
 
 
 # --------------------------------------------------------------------------
@@ -105,29 +111,32 @@ def cg(op, rhs, u0, iters, rel_tol=0.0):
     is used.  Runs ``iters`` steps, or fewer if the residual is exactly zero
     or ||r|| <= rel_tol ||rhs||.  Returns (u, stats).
     """
-    u = np.array(u0, dtype=np.float64, copy=True)
+    # Complex inputs (complex-step differentiation) keep their dtype; the
+    # dot products are plain sums of products and every decision below is
+    # taken on real parts, so real inputs follow exactly the real algorithm.
+    u = np.array(u0, dtype=np.result_type(u0, rhs, np.float64), copy=True)
     r = rhs - op(u)
     p = r.copy()
-    rr = float(r @ r)
-    rhs_norm = float(np.sqrt(rhs @ rhs))
+    rr = r @ r
+    rhs_norm = float(np.sqrt(np.real(rhs @ rhs)))
     done = 0
     for _ in range(iters):
-        if rr == 0.0:
+        if np.real(rr) == 0.0:
             break
-        if rel_tol > 0.0 and np.sqrt(rr) <= rel_tol * rhs_norm:
+        if rel_tol > 0.0 and np.sqrt(np.real(rr)) <= rel_tol * rhs_norm:
             break
         q = op(p)
-        pq = float(p @ q)
-        if not pq > 0.0:
+        pq = p @ q
+        if not np.real(pq) > 0.0:
             raise Breakdown("p^T Op p = %r" % pq)
         a = rr / pq
-        u += a * p
-        r -= a * q
-        rr_new = float(r @ r)
+        u = u + a * p
+        r = r - a * q
+        rr_new = r @ r
         p = r + (rr_new / rr) * p
         rr = rr_new
         done += 1
-    rel = np.sqrt(rr) / rhs_norm if rhs_norm > 0 else 0.0
+    rel = float(np.sqrt(np.real(rr))) / rhs_norm if rhs_norm > 0 else 0.0
     return u, {"iters": done, "rel_res": rel}
 
 
@@ -152,7 +161,7 @@ def split_bregman(A, f, shape, alpha, lam, outer, inner, u0=None, normal=None,
     """
     ny, nx = shape
     if state is not None:
-        u, dx, dy, bx, by = (np.array(a, dtype=np.float64, copy=True) for a in state)
+        u, dx, dy, bx, by = (np.array(a, dtype=np.result_type(a, np.float64), copy=True) for a in state)
         u = u.ravel()
     else:
         u = np.zeros(ny * nx) if u0 is None else np.array(u0, dtype=np.float64).ravel().copy()
