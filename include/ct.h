@@ -107,8 +107,9 @@ int ct_adjoint(ct_matrix_t A, const float *y, float *x, int32_t batch, void *cud
 /* FP64-vector forms of ct_forward / ct_adjoint for callers that keep their
  * vectors in FP64 (the differentiable reconstruction of the Python layer).
  * Same layout and batching; device pointers only (CT_ERR_ARG otherwise).  The
- * matrix values are those of the storage form; products accumulate in
- * double-float (about 48 significant bits) and are returned as FP64. */
+ * matrix values are those of the storage form; products gather and
+ * accumulate in FP64 (one FP64 FMA per entry: slower than ct_forward, but
+ * derivatives of the unrolled reconstruction need the accuracy). */
 int ct_forward_f64(ct_matrix_t A, const double *x, double *y, int32_t batch, void *cuda_stream);
 int ct_adjoint_f64(ct_matrix_t A, const double *y, double *x, int32_t batch, void *cuda_stream);
 

@@ -94,10 +94,8 @@ struct Workspace {
     float2 *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *rhs = nullptr;
     float2 *atf = nullptr, *u_old = nullptr, *bx = nullptr, *by = nullptr, *vx = nullptr, *vy = nullptr;
     float2* y = nullptr;                   // sinogram temp [rows][batch]
-    float2* pub_y2 = nullptr;              // public products: sinogram-side double-float buffer
+    float2* pub_y2 = nullptr;              // ct_adjoint with FP16 storage: s .* y
     int64_t pub_y2_len = 0;
-    float2* pub_x2 = nullptr;              // public FP64 products: image-side buffer
-    int64_t pub_x2_len = 0;
     float2* partials = nullptr;            // reduction partials
     int64_t partials_len = 0;
     unsigned* counter = nullptr;           // last-block counter (one per workspace)

@@ -227,7 +227,7 @@ int make_plan(ct_matrix* M, Workspace* ws, double c_id, double c_ata, double c_g
 
 void free_workspace(Workspace& w)
 {
-    float2* vs[] = {w.u, w.r, w.p, w.q, w.rhs, w.atf, w.u_old, w.bx, w.by, w.vx, w.vy, w.y, w.pub_y2, w.pub_x2};
+    float2* vs[] = {w.u, w.r, w.p, w.q, w.rhs, w.atf, w.u_old, w.bx, w.by, w.vx, w.vy, w.y, w.pub_y2};
     for (float2* v : vs) cudaFree(v);
     cudaFree(w.stage_a);
     cudaFree(w.stage_b);
@@ -248,12 +248,10 @@ int ensure_workspace(ct_matrix* M, int32_t batch, bool /*solver*/)
     float* sa = w.stage_a;
     float* sb = w.stage_b;
     float2* py = w.pub_y2;
-    float2* px = w.pub_x2;
-    const int64_t la = w.stage_a_len, lb = w.stage_b_len, lp = w.pub_y2_len, lx = w.pub_x2_len;
+    const int64_t la = w.stage_a_len, lb = w.stage_b_len, lp = w.pub_y2_len;
     w.cap_stream = nullptr;
     w.stage_a = w.stage_b = nullptr;
     w.pub_y2 = nullptr;
-    w.pub_x2 = nullptr;
     free_workspace(w);
     w.cap_stream = keep;
     w.stage_a = sa;
@@ -262,8 +260,6 @@ int ensure_workspace(ct_matrix* M, int32_t batch, bool /*solver*/)
     w.stage_a_len = la;
     w.stage_b_len = lb;
     w.pub_y2_len = lp;
-    w.pub_x2 = px;
-    w.pub_x2_len = lx;
     w.batch = batch;
     w.n2 = M->cols;
     w.rows = M->rows;

@@ -6,62 +6,101 @@
 // per row and 32-slice chunk for a batch (batch.cu).
 #include "ct_internal.cuh"
 #include "dfloat.cuh"
+#include "sparse_common.cuh"
 
 namespace ct {
 namespace {
 
-// FP64 -> double-float, optionally times a per-row FP32 scale (index i / B).
-__global__ void d2df_kernel(const double* __restrict__ in, const float* __restrict__ scale, float2* __restrict__ out,
-                            int64_t len, int B)
+// FP64-vector products for the differentiable path: FP64 gathers and FP64
+// accumulation (one FMA per entry on the FP64 pipe).  The derivative of the
+// unrolled reconstruction amplifies rounding far more than the reconstruction
+// itself, so this path trades speed for FP64 accuracy; the solvers use the
+// double-float kernels.
+template <typename VT>
+__device__ __forceinline__ double val64(const VT* v, int64_t k);
+template <>
+__device__ __forceinline__ double val64<float>(const float* v, int64_t k) { return (double)__ldg(v + k); }
+template <>
+__device__ __forceinline__ double val64<__half>(const __half* v, int64_t k)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
-        double v = in[i];
-        if (scale) v *= (double)scale[i / B];
-        out[i] = df_from_double(v);
+    return (double)__half2float(v[k]);
+}
+
+// B == 1: one warp per row, lanes interleaved over the entries.
+template <typename VT>
+__global__ void __launch_bounds__(256) csr_f64_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                      const VT* __restrict__ val, int64_t rows,
+                                                      const double* __restrict__ x, double* __restrict__ y,
+                                                      const float* __restrict__ row_scale,
+                                                      const float* __restrict__ in_scale)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row = warp; row < rows; row += nw) {
+        double acc = 0.0;
+        for (int64_t k = rp[row] + lane; k < rp[row + 1]; k += 32) {
+            const int c = __ldg(col + k);
+            double xv = __ldg(x + c);
+            if (in_scale) xv *= (double)__ldg(in_scale + c);
+            acc = fma(val64<VT>(val, k), xv, acc);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) y[row] = row_scale ? acc * (double)row_scale[row] : acc;
     }
 }
 
-__global__ void df2d_kernel(const float2* __restrict__ in, double* __restrict__ out, int64_t len)
+// B > 1: one warp per (row, 32-slice chunk), lane = slice.
+template <typename VT>
+__global__ void __launch_bounds__(256) spmm_f64_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                       const VT* __restrict__ val, int64_t rows,
+                                                       const double* __restrict__ x, double* __restrict__ y, int B,
+                                                       const float* __restrict__ row_scale,
+                                                       const float* __restrict__ in_scale)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = df_to_double(in[i]);
+    const int lane = threadIdx.x & 31;
+    const int chunks = (B + 31) / 32;
+    const int64_t task0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t ntask = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t task = task0; task < rows * chunks; task += ntask) {
+        const int64_t row = task / chunks;
+        const int b = (int)(task % chunks) * 32 + lane;
+        if (b >= B) continue;
+        double acc = 0.0;
+        for (int64_t k = rp[row]; k < rp[row + 1]; ++k) {
+            const int c = __ldg(col + k);
+            double xv = __ldg(x + (int64_t)c * B + b);
+            if (in_scale) xv *= (double)__ldg(in_scale + c);
+            acc = fma(val64<VT>(val, k), xv, acc);
+        }
+        y[row * B + b] = row_scale ? acc * (double)row_scale[row] : acc;
+    }
 }
 
-int ensure_buf(float2** buf, int64_t* len, int64_t need)
-{
-    if (*len >= need) return CT_OK;
-    cudaFree(*buf);
-    *buf = nullptr;
-    *len = 0;
-    CT_CUDA(cudaMalloc((void**)buf, (size_t)need * sizeof(float2)));
-    *len = need;
-    return CT_OK;
-}
-
-// in (FP64, len_in) -> product -> out (FP64, len_out), through double-float buffers.
 int product_f64(const ct_matrix* M, int which, const double* in, double* out, int32_t B, cudaStream_t st)
 {
-    ct_matrix* Mm = const_cast<ct_matrix*>(M);
-    Workspace& w = Mm->ws;
-    const int64_t nx = M->cols * B, ny = M->rows * B;
-    CT_CHECK(ensure_buf(&w.pub_x2, &w.pub_x2_len, nx));
-    CT_CHECK(ensure_buf(&w.pub_y2, &w.pub_y2_len, ny));
-    float2* src = which == 0 ? w.pub_x2 : w.pub_y2;
-    float2* dst = which == 0 ? w.pub_y2 : w.pub_x2;
-    const int64_t lin = which == 0 ? nx : ny, lout = which == 0 ? ny : nx;
+    const Csr& C = which == 0 ? M->A : M->At;
     const bool f16 = (M->flags & CT_VAL_FP16_ROWSCALE) != 0;
-    d2df_kernel<<<grid_for(M, lin, 256, 8), 256, 0, st>>>(in, (which == 1 && f16) ? M->row_scale : nullptr, src,
-                                                          lin, B);
-    CT_CUDA(cudaGetLastError());
+    // FP16 storage: A = diag(s) Q, A^T y = Q^T (s .* y)
+    const float* row_scale = (f16 && which == 0) ? M->row_scale : nullptr;
+    const float* in_scale = (f16 && which == 1) ? M->row_scale : nullptr;
     if (B == 1) {
-        if (which == 0)
-            CT_CHECK(launch_forward_df(M, f16 ? ValKind::F16 : ValKind::F32, src, dst, 1, nullptr, nullptr, st));
+        const int grid = grid_for(M, C.rows, 8, 8);
+        if (f16)
+            csr_f64_kernel<__half><<<grid, 256, 0, st>>>(C.row_ptr, C.col, C.qval, C.rows, in, out, row_scale, in_scale);
         else
-            CT_CHECK(launch_adjoint_df(M, f16 ? ValKind::F16 : ValKind::F32, src, dst, 1.0, st));
+            csr_f64_kernel<float><<<grid, 256, 0, st>>>(C.row_ptr, C.col, C.val, C.rows, in, out, row_scale, in_scale);
     } else {
-        CT_CHECK(batched_product_df(M, which, src, dst, B, st));
+        const int64_t tasks = C.rows * ((B + 31) / 32);
+        const int grid = grid_for(M, tasks, 8, 8);
+        if (f16)
+            spmm_f64_kernel<__half><<<grid, 256, 0, st>>>(C.row_ptr, C.col, C.qval, C.rows, in, out, B, row_scale,
+                                                          in_scale);
+        else
+            spmm_f64_kernel<float><<<grid, 256, 0, st>>>(C.row_ptr, C.col, C.val, C.rows, in, out, B, row_scale,
+                                                         in_scale);
     }
-    df2d_kernel<<<grid_for(M, lout, 256, 8), 256, 0, st>>>(dst, out, lout);
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
