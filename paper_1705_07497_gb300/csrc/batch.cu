@@ -83,11 +83,35 @@ struct BProd {
     const SbSlice* sb;
 };
 
+// Column of an entry: A stores internal pixel indices; A^T stores band-local
+// indices k * W + w that map to sinogram row k * n_bins + band_lo(tile, k) + w.
+struct ColMap {
+    const int32_t* col;       // A
+    const uint16_t* col16;    // A^T (band-local)
+    const int32_t* band_lo;
+    int nb, nk;
+};
+
+__device__ __forceinline__ int map_col(const ColMap& cm, int64_t row, int64_t k)
+{
+    if (cm.col) return __ldcs(cm.col + k);
+    const int c = (int)__ldcs(cm.col16 + k);
+    const int a = c / kBandW;
+    return a * cm.nb + cm.band_lo[(row >> 8) * cm.nk + a] + (c - a * kBandW);
+}
+
+// Output position of (row, slice): internal layout, or for USER_OUT the
+// caller's row-major image (rows are internal pixel indices; padding skipped).
+struct OutMap {
+    int user;  // 1: rows are pixels written in the caller's layout
+    int n, tn;
+};
+
 // Y[row][b] = scale * sum_k val_k X[col_k][b].
 template <typename VT, typename XT, typename YT>
-__global__ void __launch_bounds__(256) spmm_df_kernel(CsrView m, const VT* __restrict__ val,
+__global__ void __launch_bounds__(256) spmm_df_kernel(CsrView m, ColMap cm, const VT* __restrict__ val,
                                                       const XT* __restrict__ x, YT* __restrict__ y, int B,
-                                                      BProd a)
+                                                      BProd a, OutMap om)
 {
     __shared__ int2 stage[kWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -103,7 +127,7 @@ __global__ void __launch_bounds__(256) spmm_df_kernel(CsrView m, const VT* __res
         for (int64_t k0 = rs; k0 < re; k0 += 32) {
             const int64_t k = k0 + lane;
             int2 e = make_int2(0, 0);
-            if (k < re) e = make_int2(__ldcs(m.col + k), __float_as_int(Vals<VT>::one(val, k)));
+            if (k < re) e = make_int2(map_col(cm, row, k), __float_as_int(Vals<VT>::one(val, k)));
             stage[w][lane] = e;
             __syncwarp();
             const int cnt = (re - k0) < 32 ? (int)(re - k0) : 32;
@@ -133,7 +157,14 @@ __global__ void __launch_bounds__(256) spmm_df_kernel(CsrView m, const VT* __res
                 v = df_mul_f(v, s);
                 if (a.rpow == 2) v = df_mul_f(v, s);
             }
-            st_y(y, row * B + b, df_mul(a.scale, v));
+            int64_t pos = row;
+            if (om.user) {
+                int i, j;
+                tiled_coords(row, om.tn, i, j);
+                if (i >= om.n || j >= om.n) continue;
+                pos = (int64_t)i * om.n + j;
+            }
+            st_y(y, pos * B + b, df_mul(a.scale, v));
         }
     }
 }
@@ -151,47 +182,47 @@ struct BOp {
     const CgSlice* cg;
     const SbSlice* sb;
     float2* partials;
-    int n;
+    int n, tn;
 };
 
-__device__ __forceinline__ float2 lap_b(const float2* __restrict__ u, int64_t p, int n, int B, int b)
+__device__ __forceinline__ float2 lap_b(const float2* __restrict__ u, int64_t t, int i, int j, int n, int tn, int B,
+                                       int b)
 {
-    const int i = (int)(p / n), j = (int)(p - (int64_t)i * n);
-    const float2 c = u[p * B + b];
+    const float2 c = u[t * B + b];
     float2 acc = df_zero();
-    if (j > 0) acc = df_add(acc, df_sub(c, u[(p - 1) * B + b]));
-    if (j < n - 1) acc = df_add(acc, df_sub(c, u[(p + 1) * B + b]));
-    if (i > 0) acc = df_add(acc, df_sub(c, u[(p - n) * B + b]));
-    if (i < n - 1) acc = df_add(acc, df_sub(c, u[(p + n) * B + b]));
+    if (j > 0) acc = df_add(acc, df_sub(c, u[tiled_index(i, j - 1, tn) * B + b]));
+    if (j < n - 1) acc = df_add(acc, df_sub(c, u[tiled_index(i, j + 1, tn) * B + b]));
+    if (i > 0) acc = df_add(acc, df_sub(c, u[tiled_index(i - 1, j, tn) * B + b]));
+    if (i < n - 1) acc = df_add(acc, df_sub(c, u[tiled_index(i + 1, j, tn) * B + b]));
     return acc;
 }
 
 __device__ __forceinline__ float2 grad_adj_b(const float2* __restrict__ vx, const float2* __restrict__ vy,
-                                             int64_t p, int n, int B, int b)
+                                             int64_t t, int i, int j, int n, int tn, int B, int b)
 {
-    const int i = (int)(p / n), j = (int)(p - (int64_t)i * n);
     float2 acc = df_zero();
-    if (j >= 1) acc = df_add(acc, vx[(p - 1) * B + b]);
-    if (j <= n - 2) acc = df_sub(acc, vx[p * B + b]);
-    if (i >= 1) acc = df_add(acc, vy[(p - n) * B + b]);
-    if (i <= n - 2) acc = df_sub(acc, vy[p * B + b]);
+    if (j >= 1) acc = df_add(acc, vx[tiled_index(i, j - 1, tn) * B + b]);
+    if (j <= n - 2) acc = df_sub(acc, vx[t * B + b]);
+    if (i >= 1) acc = df_add(acc, vy[tiled_index(i - 1, j, tn) * B + b]);
+    if (i <= n - 2) acc = df_sub(acc, vy[t * B + b]);
     return acc;
 }
 
 template <int MODE>
-__device__ __forceinline__ void bop_epilogue(const BOp& a, int64_t p, int B, int b, float2 nacc, float& s0,
-                                             float& c0, float& s1, float& c1)
+__device__ __forceinline__ void bop_epilogue(const BOp& a, int64_t t, int i, int j, int B, int b, float2 nacc,
+                                             float& s0, float& c0, float& s1, float& c1)
 {
-    const int64_t e = p * B + b;
+    const int64_t e = t * B + b;
     const float2 in = a.in[e];
     float2 op = df_mul(a.c_ata, nacc);
-    op = df_add(op, df_mul(a.c_grad, lap_b(a.in, p, a.n, B, b)));
+    op = df_add(op, df_mul(a.c_grad, lap_b(a.in, t, i, j, a.n, a.tn, B, b)));
     op = df_add(op, df_mul(a.c_id, in));
     if (MODE == 1) {
         a.out[e] = op;
         acc_add(s0, c0, df_mul(in, op));
     } else {
-        const float2 rhs = a.rhs ? a.rhs[e] : df_add(a.atf[e], df_mul(a.lam, grad_adj_b(a.vx, a.vy, p, a.n, B, b)));
+        const float2 rhs =
+            a.rhs ? a.rhs[e] : df_add(a.atf[e], df_mul(a.lam, grad_adj_b(a.vx, a.vy, t, i, j, a.n, a.tn, B, b)));
         const float2 r = df_sub(rhs, op);
         a.out[e] = r;
         if (MODE == 2) a.p_out[e] = r;
@@ -202,7 +233,7 @@ __device__ __forceinline__ void bop_epilogue(const BOp& a, int64_t p, int B, int
 
 // A^T y for every slice fused with the operator epilogue (rows = pixels).
 template <typename VT, int MODE>
-__global__ void __launch_bounds__(256) spmm_op_kernel(CsrView m, const VT* __restrict__ val,
+__global__ void __launch_bounds__(256) spmm_op_kernel(CsrView m, ColMap cm, const VT* __restrict__ val,
                                                       const float2* __restrict__ y, int B, BOp a)
 {
     __shared__ int2 stage[kWarps][32];
@@ -220,7 +251,7 @@ __global__ void __launch_bounds__(256) spmm_op_kernel(CsrView m, const VT* __res
         for (int64_t k0 = rs; k0 < re; k0 += 32) {
             const int64_t k = k0 + lane;
             int2 e = make_int2(0, 0);
-            if (k < re) e = make_int2(__ldcs(m.col + k), __float_as_int(Vals<VT>::one(val, k)));
+            if (k < re) e = make_int2(map_col(cm, row, k), __float_as_int(Vals<VT>::one(val, k)));
             stage[w][lane] = e;
             __syncwarp();
             const int cnt = (re - k0) < 32 ? (int)(re - k0) : 32;
@@ -243,7 +274,16 @@ __global__ void __launch_bounds__(256) spmm_op_kernel(CsrView m, const VT* __res
             }
             __syncwarp();
         }
-        if (live) bop_epilogue<MODE>(a, row, B, b, acc_value(hs, hc), s0, c0, s1, c1);
+        if (live) {
+            int i, j;
+            tiled_coords(row, a.tn, i, j);
+            if (i < a.n && j < a.n) {
+                bop_epilogue<MODE>(a, row, i, j, B, b, acc_value(hs, hc), s0, c0, s1, c1);
+            } else {
+                a.out[row * B + b] = df_zero();  // padding stays zero
+                if (MODE == 2) a.p_out[row * B + b] = df_zero();
+            }
+        }
     }
     float2 v[2] = {acc_value(s0, c0), acc_value(s1, c1)};
     block_partials<2>(v, a.partials, B, G, rb, chunk);
@@ -270,18 +310,24 @@ __global__ void __launch_bounds__(256) stencil_b_kernel(int B, BOp a, const int3
     const int b = chunk * 32 + lane;
     const bool live = slice_live(b, B, MODE == 2 ? nullptr : a.cg, a.sb);
     const int n = a.n;
-    const int64_t n2 = (int64_t)n * n;
+    const int64_t npad = padded_pixels(n);
     float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
     if (live) {
-        for (int64_t p = (int64_t)rb * kWarps + w; p < n2; p += (int64_t)G * kWarps) {
-            const int i = (int)(p / n), j = (int)(p - (int64_t)i * n);
+        for (int64_t p = (int64_t)rb * kWarps + w; p < npad; p += (int64_t)G * kWarps) {
+            int i, j;
+            tiled_coords(p, a.tn, i, j);
+            if (i >= n || j >= n) {
+                a.out[p * B + b] = df_zero();  // padding stays zero
+                if (MODE == 2) a.p_out[p * B + b] = df_zero();
+                continue;
+            }
             float hs = 0.0f, hc = 0.0f;
             for (int t = 0; t < ntaps; ++t) {
                 const int ii = i + sd[t].x, jj = j + sd[t].y;
                 if (ii >= 0 && ii < n && jj >= 0 && jj < n)
-                    acc_add(hs, hc, df_mul(sw[t], a.in[((int64_t)ii * n + jj) * B + b]));
+                    acc_add(hs, hc, df_mul(sw[t], a.in[tiled_index(ii, jj, a.tn) * B + b]));
             }
-            bop_epilogue<MODE>(a, p, B, b, acc_value(hs, hc), s0, c0, s1, c1);
+            bop_epilogue<MODE>(a, p, i, j, B, b, acc_value(hs, hc), s0, c0, s1, c1);
         }
     }
     float2 v[2] = {acc_value(s0, c0), acc_value(s1, c1)};
@@ -343,7 +389,7 @@ __device__ __forceinline__ float2 shrink_b(float2 x, float2 gamma)
 __global__ void __launch_bounds__(256) bsb_shrink_kernel(const float2* __restrict__ u, float2* __restrict__ u_old,
                                                          float2* __restrict__ bx, float2* __restrict__ by,
                                                          float2* __restrict__ vx, float2* __restrict__ vy, int n,
-                                                         int B, float2 gamma, const SbSlice* sb,
+                                                         int tn, int B, float2 gamma, const SbSlice* sb,
                                                          float2* partials)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -352,15 +398,17 @@ __global__ void __launch_bounds__(256) bsb_shrink_kernel(const float2* __restric
     block_coords(chunks, rb, chunk);
     const int G = (int)gridDim.x / chunks;
     const int b = chunk * 32 + lane;
-    const int64_t n2 = (int64_t)n * n;
+    const int64_t npad = padded_pixels(n);
     float s = 0.0f, cc = 0.0f;
     if (slice_live(b, B, nullptr, sb)) {
-        for (int64_t p = (int64_t)rb * kWarps + w; p < n2; p += (int64_t)G * kWarps) {
-            const int i = (int)(p / n), j = (int)(p - (int64_t)i * n);
+        for (int64_t p = (int64_t)rb * kWarps + w; p < npad; p += (int64_t)G * kWarps) {
+            int i, j;
+            tiled_coords(p, tn, i, j);
+            if (i >= n || j >= n) continue;
             const int64_t e = p * B + b;
             const float2 c = u[e];
-            const float2 gx = (j < n - 1) ? df_sub(u[e + B], c) : df_zero();
-            const float2 gy = (i < n - 1) ? df_sub(u[e + (int64_t)n * B], c) : df_zero();
+            const float2 gx = (j < n - 1) ? df_sub(u[tiled_index(i, j + 1, tn) * B + b], c) : df_zero();
+            const float2 gy = (i < n - 1) ? df_sub(u[tiled_index(i + 1, j, tn) * B + b], c) : df_zero();
             const float2 tx = df_add(gx, bx[e]), ty = df_add(gy, by[e]);
             const float2 dx = shrink_b(tx, gamma), dy = shrink_b(ty, gamma);
             const float2 bxn = df_sub(tx, dx), byn = df_sub(ty, dy);
@@ -422,16 +470,42 @@ __global__ void __launch_bounds__(256) finalize_kernel(const float2* __restrict_
     if (KIND == FIN_REFRESH && cg[b].active) cg[b].rr = tot[0];
 }
 
-__global__ void bwiden_kernel(const float* __restrict__ in, float2* __restrict__ out, int64_t len)
+// Caller's row-major [n*n][B] (FP32) -> internal tiled [npad][B] double-float.
+__global__ void bwiden_kernel(const float* __restrict__ in, float2* __restrict__ out, int n, int tn, int B)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = make_float2(in[i], 0.0f);
+    const int64_t len = padded_pixels(n) * B;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = e / B;
+        const int b = (int)(e - t * B);
+        int i, j;
+        tiled_coords(t, tn, i, j);
+        out[e] = (i < n && j < n) ? make_float2(in[((int64_t)i * n + j) * B + b], 0.0f) : make_float2(0.0f, 0.0f);
+    }
 }
 
-__global__ void bnarrow_kernel(const float2* __restrict__ in, float* __restrict__ out, int64_t len)
+__global__ void bnarrow_kernel(const float2* __restrict__ in, float* __restrict__ out, int n, int tn, int B)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = df_to_float(in[i]);
+    const int64_t len = padded_pixels(n) * B;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = e / B;
+        const int b = (int)(e - t * B);
+        int i, j;
+        tiled_coords(t, tn, i, j);
+        if (i < n && j < n) out[((int64_t)i * n + j) * B + b] = df_to_float(in[e]);
+    }
+}
+
+// Caller's row-major [n*n][B] (FP32) -> internal tiled [npad][B] FP32.
+__global__ void bpermute_in_kernel(const float* __restrict__ in, float* __restrict__ out, int n, int tn, int B)
+{
+    const int64_t len = padded_pixels(n) * B;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = e / B;
+        const int b = (int)(e - t * B);
+        int i, j;
+        tiled_coords(t, tn, i, j);
+        out[e] = (i < n && j < n) ? in[((int64_t)i * n + j) * B + b] : 0.0f;
+    }
 }
 
 // f (FP32, [rows][B]) -> double-float, times the row scale s (FP16 storage).
@@ -490,16 +564,27 @@ int launch_fin(const BPlan& P, int kind, const Grid2& g, cudaStream_t st)
     return CT_OK;
 }
 
-template <typename XT, typename YT>
-int launch_spmm(const ct_matrix* M, const Csr& C, ValKind vk, const XT* x, YT* y, int B, BProd a, cudaStream_t st)
+ColMap colmap_of(const ct_matrix* M, int which)
 {
-    CsrView m{C.row_ptr, C.col, C.rows};
+    if (which == 0) return ColMap{M->A.col, nullptr, nullptr, M->g.n_bins, M->n_kept};
+    return ColMap{nullptr, M->At.col16, M->band_lo, M->g.n_bins, M->n_kept};
+}
+
+// which = 0: rows of A (rays); which = 1: rows of A^T (internal pixels).
+template <typename XT, typename YT>
+int launch_spmm(const ct_matrix* M, int which, ValKind vk, const XT* x, YT* y, int B, BProd a, cudaStream_t st,
+                bool user_out = false)
+{
+    const Csr& C = which == 0 ? M->A : M->At;
+    CsrView m{C.row_ptr, nullptr, C.rows};
+    const ColMap cm = colmap_of(M, which);
+    const OutMap om{user_out ? 1 : 0, M->g.n, M->tn};
     const Grid2 g = make_grid(M, C.rows, B);
     const int blocks = g.rb * g.chunks;
     if (vk == ValKind::F16)
-        spmm_df_kernel<__half, XT, YT><<<blocks, 256, 0, st>>>(m, C.qval, x, y, B, a);
+        spmm_df_kernel<__half, XT, YT><<<blocks, 256, 0, st>>>(m, cm, C.qval, x, y, B, a, om);
     else
-        spmm_df_kernel<float, XT, YT><<<blocks, 256, 0, st>>>(m, C.val, x, y, B, a);
+        spmm_df_kernel<float, XT, YT><<<blocks, 256, 0, st>>>(m, cm, C.val, x, y, B, a, om);
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -513,16 +598,17 @@ int bapply(const BPlan& P, BOp ep, const float2* in, cudaStream_t st, Grid2& g_u
         const ValKind vk = fp32_refresh ? ValKind::F32 : P.vk;
         BProd a{vk == ValKind::F16 ? P.M->row_scale : nullptr, vk == ValKind::F16 ? 2 : 0,
                 make_float2(1.0f, 0.0f), ep.mode == 2 ? nullptr : w.cg, P.sb};
-        CT_CHECK(launch_spmm(P.M, P.M->A, vk, in, w.y, P.B, a, st));
+        CT_CHECK(launch_spmm(P.M, 0, vk, in, w.y, P.B, a, st));
         const Csr& C = P.M->At;
-        CsrView m{C.row_ptr, C.col, C.rows};
+        CsrView m{C.row_ptr, nullptr, C.rows};
+        const ColMap cm = colmap_of(P.M, 1);
         g_used = P.g_rows_t;
         const int blocks = g_used.rb * g_used.chunks;
 #define CT_BOP(VT, VAL)                                                                              \
     switch (ep.mode) {                                                                               \
-    case 1: spmm_op_kernel<VT, 1><<<blocks, 256, 0, st>>>(m, VAL, w.y, P.B, ep); break;             \
-    case 2: spmm_op_kernel<VT, 2><<<blocks, 256, 0, st>>>(m, VAL, w.y, P.B, ep); break;             \
-    default: spmm_op_kernel<VT, 3><<<blocks, 256, 0, st>>>(m, VAL, w.y, P.B, ep); break;            \
+    case 1: spmm_op_kernel<VT, 1><<<blocks, 256, 0, st>>>(m, cm, VAL, w.y, P.B, ep); break;         \
+    case 2: spmm_op_kernel<VT, 2><<<blocks, 256, 0, st>>>(m, cm, VAL, w.y, P.B, ep); break;         \
+    default: spmm_op_kernel<VT, 3><<<blocks, 256, 0, st>>>(m, cm, VAL, w.y, P.B, ep); break;        \
     }
         if (vk == ValKind::F16) {
             CT_BOP(__half, C.qval)
@@ -597,7 +683,7 @@ int bmake_plan(ct_matrix* M, int B, double c_id, double c_ata, double c_grad, do
     }
     P.sparse = (c_ata != 0.0) && P.S == nullptr;
     if (c_ata == 0.0) P.S = nullptr;
-    P.n2 = (int64_t)M->g.n * M->g.n;
+    P.n2 = M->npad;
     if (refresh > 0) {
         if (P.vk != ValKind::F16 || !M->A.val)
             return fail(CT_ERR_UNSUPPORTED, "refresh_every needs FP16 storage built with CT_KEEP_FP32_COPY");
@@ -607,7 +693,7 @@ int bmake_plan(ct_matrix* M, int B, double c_id, double c_ata, double c_grad, do
     P.tol = tol;
     P.sb = nullptr;
     P.g_rows_a = make_grid(M, M->rows, B);
-    P.g_rows_t = make_grid(M, M->cols, B);
+    P.g_rows_t = make_grid(M, M->At.rows, B);
     P.g_pix = make_grid(M, P.n2, B);
     BOp& b = P.base;
     std::memset(&b, 0, sizeof(b));
@@ -617,6 +703,7 @@ int bmake_plan(ct_matrix* M, int B, double c_id, double c_ata, double c_grad, do
     b.cg = M->ws.cg;
     b.partials = M->ws.partials;
     b.n = M->g.n;
+    b.tn = M->tn;
     return CT_OK;
 }
 
@@ -632,33 +719,27 @@ int batched_forward_adjoint(const ct_matrix* M, int which, const float* in, floa
 {
     BProd a{nullptr, 0, make_float2(1.0f, 0.0f), nullptr, nullptr};
     const ValKind vk = (M->flags & CT_VAL_FP16_ROWSCALE) ? ValKind::F16 : ValKind::F32;
+    ct_matrix* Mm = const_cast<ct_matrix*>(M);
+    CT_CHECK(ensure_workspace(Mm, B, true));
+    Workspace& w = Mm->ws;
     if (which == 0) {
         if (vk == ValKind::F16) {
             a.row_scale = M->row_scale;
             a.rpow = 1;
         }
-        return launch_spmm(M, M->A, vk, in, out, B, a, st);
+        // the caller's image goes to the internal tile order first (FP32 copy in w.u)
+        float* xt = reinterpret_cast<float*>(w.u);
+        bpermute_in_kernel<<<grid_blocks(M, M->npad * B), 256, 0, st>>>(in, xt, M->g.n, M->tn, B);
+        CT_CUDA(cudaGetLastError());
+        return launch_spmm(M, 0, vk, (const float*)xt, out, B, a, st);
     }
     if (vk == ValKind::F16) {
         // A^T y = Q^T (s .* y): the scaled copy goes through the workspace sinogram buffer
-        ct_matrix* Mm = const_cast<ct_matrix*>(M);
-        CT_CHECK(ensure_workspace(Mm, B, true));
-        bto_df_kernel<<<grid_blocks(M, M->rows * B), 256, 0, st>>>(in, M->row_scale, Mm->ws.y, M->rows, B);
+        bto_df_kernel<<<grid_blocks(M, M->rows * B), 256, 0, st>>>(in, M->row_scale, w.y, M->rows, B);
         CT_CUDA(cudaGetLastError());
-        return launch_spmm(M, M->At, vk, (const float2*)Mm->ws.y, out, B, a, st);
+        return launch_spmm(M, 1, vk, (const float2*)w.y, out, B, a, st, true);
     }
-    return launch_spmm(M, M->At, vk, in, out, B, a, st);
-}
-
-int batched_product_df(const ct_matrix* M, int which, const float2* in, float2* out, int32_t B, cudaStream_t st)
-{
-    const ValKind vk = (M->flags & CT_VAL_FP16_ROWSCALE) ? ValKind::F16 : ValKind::F32;
-    BProd a{nullptr, 0, make_float2(1.0f, 0.0f), nullptr, nullptr};
-    if (which == 0 && vk == ValKind::F16) {
-        a.row_scale = M->row_scale;
-        a.rpow = 1;
-    }
-    return launch_spmm(M, which == 0 ? M->A : M->At, vk, in, out, B, a, st);
+    return launch_spmm(M, 1, vk, in, out, B, a, st, true);
 }
 
 int cg_solve_batched(ct_matrix* M, const ct_cg_params* Pp, const float* rhs, float* u, int32_t B,
@@ -671,11 +752,11 @@ int cg_solve_batched(ct_matrix* M, const ct_cg_params* Pp, const float* rhs, flo
     CT_CHECK(bmake_plan(M, B, Pp->c_id, Pp->c_ata, Pp->c_grad, Pp->rel_tol, Pp->surrogate_r,
                         Pp->surrogate_square, Pp->refresh_every, P));
     const int64_t len = P.n2 * B;
-    bwiden_kernel<<<grid_blocks(M, len), 256, 0, st>>>(rhs, w.rhs, len);
-    bwiden_kernel<<<grid_blocks(M, len), 256, 0, st>>>(u, w.u, len);
+    bwiden_kernel<<<grid_blocks(M, len), 256, 0, st>>>(rhs, w.rhs, M->g.n, M->tn, B);
+    bwiden_kernel<<<grid_blocks(M, len), 256, 0, st>>>(u, w.u, M->g.n, M->tn, B);
     CT_CUDA(cudaGetLastError());
     CT_CHECK(benqueue_cg(P, w.rhs, Pp->max_iters, st));
-    bnarrow_kernel<<<grid_blocks(M, len), 256, 0, st>>>(w.u, u, len);
+    bnarrow_kernel<<<grid_blocks(M, len), 256, 0, st>>>(w.u, u, M->g.n, M->tn, B);
     CT_CUDA(cudaGetLastError());
     if (stats) {
         std::vector<CgSlice> h(B);
@@ -718,9 +799,9 @@ int split_bregman_batched(ct_matrix* M, const ct_sb_params* Sp, const float* f, 
     CT_CUDA(cudaGetLastError());
     {
         BProd a{nullptr, 0, df_from_double(Sp->alpha), nullptr, nullptr};
-        CT_CHECK(launch_spmm(M, M->At, P.vk, (const float2*)w.y, w.atf, B, a, st));
+        CT_CHECK(launch_spmm(M, 1, P.vk, (const float2*)w.y, w.atf, B, a, st));
     }
-    bwiden_kernel<<<grid_blocks(M, len), 256, 0, st>>>(u, w.u, len);
+    bwiden_kernel<<<grid_blocks(M, len), 256, 0, st>>>(u, w.u, M->g.n, M->tn, B);
     CT_CUDA(cudaGetLastError());
     CT_CUDA(cudaMemsetAsync(w.bx, 0, len * sizeof(float2), st));
     CT_CUDA(cudaMemsetAsync(w.by, 0, len * sizeof(float2), st));
@@ -732,7 +813,7 @@ int split_bregman_batched(ct_matrix* M, const ct_sb_params* Sp, const float* f, 
     const float2 gamma = df_from_double(1.0 / Sp->lambda);
     auto outer = [&](cudaStream_t s) -> int {
         CT_CHECK(benqueue_cg(P, nullptr, Sp->inner_cg_iters, s));
-        bsb_shrink_kernel<<<pblocks, 256, 0, s>>>(w.u, w.u_old, w.bx, w.by, w.vx, w.vy, M->g.n, B, gamma, w.sb,
+        bsb_shrink_kernel<<<pblocks, 256, 0, s>>>(w.u, w.u_old, w.bx, w.by, w.vx, w.vy, M->g.n, M->tn, B, gamma, w.sb,
                                                   w.partials);
         CT_CUDA(cudaGetLastError());
         finalize_kernel<FIN_SB, 1><<<B, 256, 0, s>>>(w.partials, P.g_pix.rb, B, w.cg, w.sb, Sp->stop_rel_update);
@@ -764,7 +845,7 @@ int split_bregman_batched(ct_matrix* M, const ct_sb_params* Sp, const float* f, 
         cudaGraphExecDestroy(exec);
         CT_CUDA(e);
     }
-    bnarrow_kernel<<<grid_blocks(M, len), 256, 0, st>>>(w.u, u, len);
+    bnarrow_kernel<<<grid_blocks(M, len), 256, 0, st>>>(w.u, u, M->g.n, M->tn, B);
     CT_CUDA(cudaGetLastError());
     if (stats) {
         std::vector<SbSlice> h(B);

@@ -84,7 +84,7 @@ __device__ __forceinline__ __half f16_from_bits(uint16_t b)
 // One thread per ray q = k*n_bins + b: sweep the image rows, evaluate the
 // pixels of each row the line can reach, keep lengths >= kMinLen.
 template <bool FILL>
-__global__ void a_rows_kernel(int n, int nb, int n_kept, const AngleRow* __restrict__ ang,
+__global__ void a_rows_kernel(int n, int tn, int nb, int n_kept, const AngleRow* __restrict__ ang,
                               int32_t* __restrict__ row_len, float* __restrict__ row_max,
                               const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col,
                               float* __restrict__ val, __half* __restrict__ qval,
@@ -125,7 +125,7 @@ __global__ void a_rows_kernel(int n, int nb, int n_kept, const AngleRow* __restr
             const double xc = j - half + 0.5;
             const double len = chord(ray_offset(xc, yc, g.c, g.s, sb), g);
             if (len < kMinLen) continue;
-            last = i * n + j;
+            last = (int32_t)tiled_index(i, j, tn);
             if (FILL) {
                 col[base + cnt] = last;
                 if (val) val[base + cnt] = (float)len;
@@ -149,23 +149,33 @@ __global__ void a_rows_kernel(int n, int nb, int n_kept, const AngleRow* __restr
     }
 }
 
-// One thread per pixel p = i*N + j: for every kept angle, evaluate the bins
-// whose rays can cross the pixel; columns come out as ascending ray indices.
+// One thread per internal pixel index t (tile order): for every kept angle,
+// evaluate the bins whose rays can cross the pixel; entries come out by angle,
+// then bin, with the column written as the band-local index
+// k * W + (b - band_lo(tile, k)).  Padding pixels get empty rows.
 template <bool FILL>
-__global__ void at_rows_kernel(int n, int nb, int n_kept, const AngleRow* __restrict__ ang,
+__global__ void at_rows_kernel(int n, int tn, int nb, int n_kept, const AngleRow* __restrict__ ang,
+                               const int32_t* __restrict__ band_lo, int64_t npad,
                                int32_t* __restrict__ row_len, const int64_t* __restrict__ row_ptr,
-                               int32_t* __restrict__ col, float* __restrict__ val,
-                               __half* __restrict__ qval, const float* __restrict__ scale)
+                               uint16_t* __restrict__ col16, float* __restrict__ val,
+                               __half* __restrict__ qval, const float* __restrict__ scale,
+                               int32_t* __restrict__ bad)
 {
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= (int64_t)n * n) return;
-    const int i = (int)(p / n), j = (int)(p % n);
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= npad) return;
+    int i, j;
+    tiled_coords(t, tn, i, j);
+    if (i >= n || j >= n) {
+        if (!FILL) row_len[t] = 0;
+        return;
+    }
+    const int32_t* blo = band_lo + (t >> 8) * (int64_t)n_kept;
     const double half = 0.5 * n;
     const double xc = j - half + 0.5, yc = i - half + 0.5;
     const double mid = 0.5 * (nb - 1);
     int cnt = 0;
-    int64_t base = FILL ? row_ptr[p] : 0;
-    int32_t last = 0;
+    int64_t base = FILL ? row_ptr[t] : 0;
+    uint16_t last = 0;
     for (int k = 0; k < n_kept; ++k) {
         const AngleRow g = ang[k];
         const double tc = xc * g.c + yc * g.s + mid;
@@ -175,21 +185,26 @@ __global__ void at_rows_kernel(int n, int nb, int n_kept, const AngleRow* __rest
             const double sb = b - mid;
             const double len = chord(ray_offset(xc, yc, g.c, g.s, sb), g);
             if (len < kMinLen) continue;
-            last = k * nb + b;
+            const int w = b - blo[k];
+            if (w < 0 || w >= kBandW) {
+                atomicExch(bad, 1);
+                continue;
+            }
+            last = (uint16_t)(k * kBandW + w);
             if (FILL) {
-                col[base + cnt] = last;
+                col16[base + cnt] = last;
                 if (val) val[base + cnt] = (float)len;
-                if (qval) qval[base + cnt] = f16_from_bits(f64_to_f16_bits(len / (double)scale[last]));
+                if (qval) qval[base + cnt] = f16_from_bits(f64_to_f16_bits(len / (double)scale[(int64_t)k * nb + b]));
             }
             ++cnt;
         }
     }
     if (!FILL) {
-        row_len[p] = cnt;
+        row_len[t] = cnt;
     } else {
-        const int64_t end = row_ptr[p + 1];
+        const int64_t end = row_ptr[t + 1];
         for (int64_t e = base + cnt; e < end; ++e) {
-            col[e] = last;
+            col16[e] = last;
             if (val) val[e] = 0.0f;
             if (qval) qval[e] = __float2half(0.0f);
         }
@@ -265,6 +280,33 @@ int finish_layout(Csr& m, const std::vector<int32_t>& len)
     return CT_OK;
 }
 
+// First bin of every (tile, angle) band: the bins whose rays can cross any
+// point of the tile's square lie within [floor(t_min + mid), ceil(t_max + mid)]
+// where t runs over the projections of the square's corners; one more bin of
+// margin below, and the band has kBandW bins (a 16-pixel square projects to
+// at most 16 sqrt(2) < 22.7 detector units).
+std::vector<int32_t> band_table(const ct_geometry& g, const std::vector<double>& hc,
+                                const std::vector<double>& hs, int tn)
+{
+    const int nk = (int)hc.size();
+    const double half = 0.5 * g.n, mid = 0.5 * (g.n_bins - 1);
+    std::vector<int32_t> lo((size_t)tn * tn * nk);
+    for (int ti = 0; ti < tn; ++ti) {
+        for (int tj = 0; tj < tn; ++tj) {
+            const double x0 = tj * kTile - half, y0 = ti * kTile - half;
+            for (int k = 0; k < nk; ++k) {
+                double tmin = 1e300;
+                for (int cx = 0; cx < 2; ++cx)
+                    for (int cy = 0; cy < 2; ++cy)
+                        tmin = std::fmin(tmin, (x0 + cx * kTile) * hc[k] + (y0 + cy * kTile) * hs[k]);
+                const double b = std::floor(tmin + mid) - 1.0;
+                lo[((size_t)ti * tn + tj) * nk + k] = (int32_t)std::fmax(b, 0.0);
+            }
+        }
+    }
+    return lo;
+}
+
 std::vector<AngleRow> angle_table(const ct_geometry& g, std::vector<double>& hc, std::vector<double>& hs)
 {
     const int n_kept = (g.n_angles_total + g.keep_every - 1) / g.keep_every;
@@ -301,6 +343,7 @@ void free_csr(Csr& c)
     cudaFree(c.row_ptr);
     cudaFree(c.row_len);
     cudaFree(c.col);
+    cudaFree(c.col16);
     cudaFree(c.val);
     cudaFree(c.qval);
     c = Csr{};
@@ -322,12 +365,25 @@ int build_matrices(ct_matrix* M)
     CT_CUDA(cudaMemcpy(d_ang, tab.data(), tab.size() * sizeof(AngleRow), cudaMemcpyHostToDevice));
     M->dirs = (double*)d_ang;
 
+    M->tn = tiles_per_side(n);
+    M->npad = padded_pixels(n);
+    const int tn = M->tn;
+    if ((int64_t)nk * kBandW > 65536)
+        return fail(CT_ERR_UNSUPPORTED, "more than 2340 kept angles do not fit 16-bit band indices");
+    M->h_band_lo = band_table(g, M->h_cos, M->h_sin, tn);
+    CT_CHECK(alloc_dev((void**)&M->band_lo, M->h_band_lo.size() * sizeof(int32_t)));
+    CT_CUDA(cudaMemcpy(M->band_lo, M->h_band_lo.data(), M->h_band_lo.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice));
+    int32_t* d_bad = nullptr;
+    CT_CHECK(alloc_dev((void**)&d_bad, sizeof(int32_t)));
+    CT_CUDA(cudaMemset(d_bad, 0, sizeof(int32_t)));
+
     Csr& A = M->A;
     Csr& T = M->At;
     A.rows = M->rows;
-    A.cols = M->cols;
-    T.rows = M->cols;
-    T.cols = M->rows;
+    A.cols = M->npad;
+    T.rows = M->npad;
+    T.cols = (int64_t)nk * kBandW;
     CT_CHECK(alloc_dev((void**)&A.row_len, A.rows * sizeof(int32_t)));
     CT_CHECK(alloc_dev((void**)&T.row_len, T.rows * sizeof(int32_t)));
     if (f16) CT_CHECK(alloc_dev((void**)&M->row_scale, A.rows * sizeof(float)));
@@ -335,11 +391,11 @@ int build_matrices(ct_matrix* M)
     const int tpb = 128;
     // pass 1: counts (and row maxima for the FP16 scale)
     a_rows_kernel<false><<<(unsigned)((A.rows + tpb - 1) / tpb), tpb>>>(
-        n, nb, nk, d_ang, A.row_len, f16 ? M->row_scale : nullptr, nullptr, nullptr, nullptr,
+        n, tn, nb, nk, d_ang, A.row_len, f16 ? M->row_scale : nullptr, nullptr, nullptr, nullptr,
         nullptr, nullptr);
     CT_CUDA(cudaGetLastError());
     at_rows_kernel<false><<<(unsigned)((T.rows + tpb - 1) / tpb), tpb>>>(
-        n, nb, nk, d_ang, T.row_len, nullptr, nullptr, nullptr, nullptr, nullptr);
+        n, tn, nb, nk, d_ang, M->band_lo, M->npad, T.row_len, nullptr, nullptr, nullptr, nullptr, nullptr, d_bad);
     CT_CUDA(cudaGetLastError());
     std::vector<int32_t> la(A.rows), lt(T.rows);
     CT_CUDA(cudaMemcpy(la.data(), A.row_len, A.rows * sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -349,19 +405,23 @@ int build_matrices(ct_matrix* M)
     if (A.nnz != T.nnz)
         return fail(CT_ERR_CUDA, "internal: A and A^T entry counts differ (" + std::to_string(A.nnz) +
                                      " vs " + std::to_string(T.nnz) + ")");
+    CT_CHECK(alloc_dev((void**)&A.col, A.nnz_pad * sizeof(int32_t)));
+    CT_CHECK(alloc_dev((void**)&T.col16, T.nnz_pad * sizeof(uint16_t)));
     for (Csr* m : {&A, &T}) {
-        CT_CHECK(alloc_dev((void**)&m->col, m->nnz_pad * sizeof(int32_t)));
         if (f32) CT_CHECK(alloc_dev((void**)&m->val, m->nnz_pad * sizeof(float)));
         if (f16) CT_CHECK(alloc_dev((void**)&m->qval, m->nnz_pad * sizeof(__half)));
     }
     // pass 2: fill
     a_rows_kernel<true><<<(unsigned)((A.rows + tpb - 1) / tpb), tpb>>>(
-        n, nb, nk, d_ang, nullptr, nullptr, A.row_ptr, A.col, A.val, A.qval, M->row_scale);
+        n, tn, nb, nk, d_ang, nullptr, nullptr, A.row_ptr, A.col, A.val, A.qval, M->row_scale);
     CT_CUDA(cudaGetLastError());
     at_rows_kernel<true><<<(unsigned)((T.rows + tpb - 1) / tpb), tpb>>>(
-        n, nb, nk, d_ang, nullptr, T.row_ptr, T.col, T.val, T.qval, M->row_scale);
+        n, tn, nb, nk, d_ang, M->band_lo, M->npad, nullptr, T.row_ptr, T.col16, T.val, T.qval, M->row_scale, d_bad);
     CT_CUDA(cudaGetLastError());
-    CT_CUDA(cudaDeviceSynchronize());
+    int32_t bad = 0;
+    CT_CUDA(cudaMemcpy(&bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    cudaFree(d_bad);
+    if (bad) return fail(CT_ERR_CUDA, "internal: an A^T entry fell outside its tile band");
     return CT_OK;
 }
 

@@ -143,6 +143,7 @@ void ct_destroy_matrix(ct_matrix_t A)
     free_csr(A->At);
     cudaFree(A->row_scale);
     cudaFree(A->dirs);
+    cudaFree(A->band_lo);
     if (prev >= 0 && prev != A->device) cudaSetDevice(prev);
     delete A;
 }
@@ -259,14 +260,22 @@ int ct_matrix_export(ct_matrix_t A, int32_t which, int64_t* row_ptr, int32_t* co
     if (which != 0 && which != 1) return fail(CT_ERR_ARG, "which must be 0 (A) or 1 (A^T)");
     if (!row_ptr || !cols || !vals) return fail(CT_ERR_ARG, "NULL output array");
     const Csr& C = which == 0 ? A->A : A->At;
+    const int n = A->g.n, tn = A->tn, nb = A->g.n_bins, nk = A->n_kept;
     std::vector<int64_t> rp(C.rows + 1);
-    std::vector<int32_t> len(C.rows), col(C.nnz_pad);
+    std::vector<int32_t> len(C.rows), col;
+    std::vector<uint16_t> col16;
     std::vector<float> val(C.nnz_pad);
     std::vector<uint16_t> q;
     std::vector<float> s;
     CT_CUDA(cudaMemcpy(rp.data(), C.row_ptr, rp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
     CT_CUDA(cudaMemcpy(len.data(), C.row_len, len.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    CT_CUDA(cudaMemcpy(col.data(), C.col, col.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (which == 0) {
+        col.resize(C.nnz_pad);
+        CT_CUDA(cudaMemcpy(col.data(), C.col, col.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    } else {
+        col16.resize(C.nnz_pad);
+        CT_CUDA(cudaMemcpy(col16.data(), C.col16, col16.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+    }
     const bool f16 = (A->flags & CT_VAL_FP16_ROWSCALE) != 0;
     if (f16) {
         q.resize(C.nnz_pad);
@@ -276,21 +285,44 @@ int ct_matrix_export(ct_matrix_t A, int32_t which, int64_t* row_ptr, int32_t* co
     } else {
         CT_CUDA(cudaMemcpy(val.data(), C.val, val.size() * sizeof(float), cudaMemcpyDeviceToHost));
     }
+    auto value = [&](int64_t k, int64_t ray) -> float {
+        if (!f16) return val[k];
+        __half_raw hr;
+        hr.x = q[k];
+        return __half2float(__half(hr)) * s[ray];
+    };
     int64_t o = 0;
     row_ptr[0] = 0;
-    for (int64_t r = 0; r < C.rows; ++r) {
-        for (int64_t k = rp[r]; k < rp[r] + len[r]; ++k, ++o) {
-            cols[o] = col[k];
-            if (f16) {
-                __half_raw hr;
-                hr.x = q[k];
-                const float qf = __half2float(__half(hr));
-                vals[o] = qf * s[which == 0 ? r : col[k]];
-            } else {
-                vals[o] = val[k];
+    if (which == 0) {
+        // entries are stored in row-major pixel order; columns are tile-order indices
+        for (int64_t r = 0; r < C.rows; ++r) {
+            for (int64_t k = rp[r]; k < rp[r] + len[r]; ++k, ++o) {
+                int i, j;
+                tiled_coords(col[k], tn, i, j);
+                cols[o] = i * n + j;
+                vals[o] = value(k, r);
             }
+            row_ptr[r + 1] = o;
         }
-        row_ptr[r + 1] = o;
+        return CT_OK;
+    }
+    // A^T: rows in tile order, columns band-local; emit by row-major pixel
+    std::vector<int64_t> row_of((size_t)n * n, -1);
+    for (int64_t t = 0; t < C.rows; ++t) {
+        int i, j;
+        tiled_coords(t, tn, i, j);
+        if (i < n && j < n) row_of[(size_t)i * n + j] = t;
+    }
+    for (int64_t p = 0; p < (int64_t)n * n; ++p) {
+        const int64_t t = row_of[p];
+        for (int64_t k = rp[t]; k < rp[t] + len[t]; ++k, ++o) {
+            const int c = col16[k];
+            const int a = c / kBandW;
+            const int64_t ray = (int64_t)a * nb + A->h_band_lo[(size_t)(t >> 8) * nk + a] + (c - a * kBandW);
+            cols[o] = (int32_t)ray;
+            vals[o] = value(k, ray);
+        }
+        row_ptr[p + 1] = o;
     }
     return CT_OK;
 }

@@ -12,6 +12,7 @@
 
 #include "ct.h"
 #include "dfloat.cuh"
+#include "layout.cuh"
 
 namespace ct {
 
@@ -48,7 +49,8 @@ struct Csr {
     int64_t nnz_pad = 0;   // entries including row padding
     int64_t* row_ptr = nullptr;  // [rows+1] padded offsets
     int32_t* row_len = nullptr;  // [rows] unpadded lengths
-    int32_t* col = nullptr;      // [nnz_pad]
+    int32_t* col = nullptr;      // [nnz_pad] column indices (A: internal pixel index)
+    uint16_t* col16 = nullptr;   // [nnz_pad] A^T: local band index k*W + (b - band_lo)
     float* val = nullptr;        // [nnz_pad] FP32 values (may be null)
     __half* qval = nullptr;      // [nnz_pad] FP16 Q values (may be null)
 };
@@ -96,6 +98,8 @@ struct Workspace {
     float2* y = nullptr;                   // sinogram temp [rows][batch]
     float2* pub_y2 = nullptr;              // ct_adjoint with FP16 storage: s .* y
     int64_t pub_y2_len = 0;
+    float* pub_x = nullptr;                // ct_forward: the caller's image in tile order
+    int64_t pub_x_len = 0;
     float2* partials = nullptr;            // reduction partials
     int64_t partials_len = 0;
     unsigned* counter = nullptr;           // last-block counter (one per workspace)
@@ -116,6 +120,10 @@ struct ct_matrix {
     int sm_count = 0;
     int n_kept = 0;
     int64_t rows = 0, cols = 0;
+    int tn = 0;              // image tiles per side
+    int64_t npad = 0;        // padded internal image length (tn * 16)^2
+    int32_t* band_lo = nullptr;  // device [tn*tn][n_kept]: first bin of each (tile, angle) band
+    std::vector<int32_t> h_band_lo;
     double* dirs = nullptr;  // device [n_kept][2]: cos, sin
     std::vector<double> h_cos, h_sin;
     ct::Csr A, At;
@@ -199,9 +207,6 @@ int grid_for(const ct_matrix* M, int64_t work_items, int items_per_block, int ma
 // which = 0: y = A x; which = 1: x = A^T y (FP32 vectors, double-float accumulation).
 int batched_forward_adjoint(const ct_matrix* M, int which, const float* in, float* out, int32_t B,
                             cudaStream_t st);
-// Double-float in and out (which = 0: A, which = 1: A^T; FP16 storage: A^T
-// expects its input already multiplied by the row scale).
-int batched_product_df(const ct_matrix* M, int which, const float2* in, float2* out, int32_t B, cudaStream_t st);
 int cg_solve_batched(ct_matrix* M, const ct_cg_params* P, const float* rhs, float* u, int32_t B,
                      ct_cg_stats* stats, cudaStream_t st);
 int split_bregman_batched(ct_matrix* M, const ct_sb_params* P, const float* f, float* u, int32_t B,

@@ -47,7 +47,7 @@ struct Layout {
 Layout layout_for(const ct_matrix* M)
 {
     Layout L;
-    const size_t n2 = (size_t)M->cols, rows = (size_t)M->rows;
+    const size_t n2 = (size_t)M->npad, rows = (size_t)M->rows;
     const size_t nparts = (size_t)4 * (M->sm_count > 0 ? M->sm_count : 148) * 8;
     L.vec = round256(n2 * sizeof(float2));
     L.y = round256(rows * sizeof(float2));
@@ -94,7 +94,7 @@ extern "C" int ct_cg_solve_noalloc(ct_matrix_t A, const ct_cg_params* params, co
     CT_CHECK(scratch_address(dev, &base));
     Workspace w;
     w.batch = 1;
-    w.n2 = A->cols;
+    w.n2 = A->npad;
     w.rows = A->rows;
     unsigned char* at = base;
     float2** vecs[] = {&w.u, &w.r, &w.p, &w.q, &w.rhs};

@@ -67,19 +67,21 @@ __global__ void __launch_bounds__(256) sb_shrink_kernel(const float2* __restrict
                                                         float2* __restrict__ u_old,
                                                         float2* __restrict__ bx, float2* __restrict__ by,
                                                         float2* __restrict__ vx, float2* __restrict__ vy,
-                                                        int n, float2 gamma, SbSlice* sb,
+                                                        int n, int tn, float2 gamma, SbSlice* sb,
                                                         const CgSlice* cg, double tol,
                                                         float2* partials, unsigned* counter)
 {
     if (sb->stopped) return;
-    const int64_t n2 = (int64_t)n * n;
+    const int64_t npad = padded_pixels(n);
     float s = 0.0f, cc = 0.0f;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npad;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(p / n), j = (int)(p - (int64_t)i * n);
+        int i, j;
+        tiled_coords(p, tn, i, j);
+        if (i >= n || j >= n) continue;
         const float2 c = u[p];
-        const float2 gx = (j < n - 1) ? df_sub(u[p + 1], c) : df_zero();
-        const float2 gy = (i < n - 1) ? df_sub(u[p + n], c) : df_zero();
+        const float2 gx = (j < n - 1) ? df_sub(u[tiled_index(i, j + 1, tn)], c) : df_zero();
+        const float2 gy = (i < n - 1) ? df_sub(u[tiled_index(i + 1, j, tn)], c) : df_zero();
         const float2 tx = df_add(gx, bx[p]), ty = df_add(gy, by[p]);
         const float2 dx = shrink_df(tx, gamma), dy = shrink_df(ty, gamma);
         const float2 bxn = df_sub(tx, dx), byn = df_sub(ty, dy);
@@ -102,19 +104,27 @@ __global__ void __launch_bounds__(256) sb_shrink_kernel(const float2* __restrict
     }
 }
 
-// FP32 caller vector -> double-float.
-__global__ void widen_kernel(const float* __restrict__ in, float2* __restrict__ out, int64_t len)
+// Caller's row-major FP32 image -> internal tiled double-float (padding zero).
+__global__ void widen_kernel(const float* __restrict__ in, float2* __restrict__ out, int n, int tn)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
-         i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = make_float2(in[i], 0.0f);
+    const int64_t npad = padded_pixels(n);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npad;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int i, j;
+        tiled_coords(t, tn, i, j);
+        out[t] = (i < n && j < n) ? make_float2(in[(int64_t)i * n + j], 0.0f) : make_float2(0.0f, 0.0f);
+    }
 }
 
-__global__ void narrow_kernel(const float2* __restrict__ in, float* __restrict__ out, int64_t len)
+__global__ void narrow_kernel(const float2* __restrict__ in, float* __restrict__ out, int n, int tn)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
-         i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = df_to_float(in[i]);
+    const int64_t npad = padded_pixels(n);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npad;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int i, j;
+        tiled_coords(t, tn, i, j);
+        if (i < n && j < n) out[(int64_t)i * n + j] = df_to_float(in[t]);
+    }
 }
 
 template <typename T>
@@ -202,7 +212,7 @@ int make_plan(ct_matrix* M, Workspace* ws, double c_id, double c_ata, double c_g
     }
     P.sparse = (c_ata != 0.0) && P.S == nullptr;
     if (c_ata == 0.0) P.S = nullptr;
-    P.n2 = (int64_t)M->g.n * M->g.n;
+    P.n2 = M->npad;
     if (refresh > 0) {
         if (P.vk != ValKind::F16 || !M->A.val)
             return fail(CT_ERR_UNSUPPORTED,
@@ -231,6 +241,7 @@ void free_workspace(Workspace& w)
     for (float2* v : vs) cudaFree(v);
     cudaFree(w.stage_a);
     cudaFree(w.stage_b);
+    cudaFree(w.pub_x);
     cudaFree(w.partials);
     cudaFree(w.counter);
     cudaFree(w.cg);
@@ -248,10 +259,12 @@ int ensure_workspace(ct_matrix* M, int32_t batch, bool /*solver*/)
     float* sa = w.stage_a;
     float* sb = w.stage_b;
     float2* py = w.pub_y2;
-    const int64_t la = w.stage_a_len, lb = w.stage_b_len, lp = w.pub_y2_len;
+    float* pxx = w.pub_x;
+    const int64_t la = w.stage_a_len, lb = w.stage_b_len, lp = w.pub_y2_len, lxx = w.pub_x_len;
     w.cap_stream = nullptr;
     w.stage_a = w.stage_b = nullptr;
     w.pub_y2 = nullptr;
+    w.pub_x = nullptr;
     free_workspace(w);
     w.cap_stream = keep;
     w.stage_a = sa;
@@ -260,8 +273,10 @@ int ensure_workspace(ct_matrix* M, int32_t batch, bool /*solver*/)
     w.stage_a_len = la;
     w.stage_b_len = lb;
     w.pub_y2_len = lp;
+    w.pub_x = pxx;
+    w.pub_x_len = lxx;
     w.batch = batch;
-    w.n2 = M->cols;
+    w.n2 = M->npad;
     w.rows = M->rows;
     const int64_t nv = w.n2 * batch;
     float2** vs[] = {&w.u, &w.r, &w.p, &w.q, &w.rhs, &w.atf, &w.u_old, &w.bx, &w.by, &w.vx, &w.vy};
@@ -286,11 +301,11 @@ int cg_solve_in(ct_matrix* M, Workspace& w, const ct_cg_params* Pp, const float*
     CT_CHECK(make_plan(M, &w, Pp->c_id, Pp->c_ata, Pp->c_grad, Pp->rel_tol, Pp->surrogate_r,
                        Pp->surrogate_square, Pp->refresh_every, P));
     const int gv = grid_for(M, P.n2, 256, 8);
-    widen_kernel<<<gv, 256, 0, st>>>(rhs, w.rhs, P.n2);
-    widen_kernel<<<gv, 256, 0, st>>>(u, w.u, P.n2);
+    widen_kernel<<<gv, 256, 0, st>>>(rhs, w.rhs, M->g.n, M->tn);
+    widen_kernel<<<gv, 256, 0, st>>>(u, w.u, M->g.n, M->tn);
     CT_CUDA(cudaGetLastError());
     CT_CHECK(enqueue_cg(P, w.rhs, Pp->max_iters, st));
-    narrow_kernel<<<gv, 256, 0, st>>>(w.u, u, P.n2);
+    narrow_kernel<<<gv, 256, 0, st>>>(w.u, u, M->g.n, M->tn);
     CT_CUDA(cudaGetLastError());
     if (stats) {
         CgSlice h;
@@ -322,7 +337,7 @@ int enqueue_sb_outer(const Plan& P, const ct_sb_params* Sp, cudaStream_t st)
     Workspace& w = *P.w;
     CT_CHECK(enqueue_cg(P, nullptr, Sp->inner_cg_iters, st));
     const int gv = grid_for(P.M, P.n2, 256, 8);
-    sb_shrink_kernel<<<gv, 256, 0, st>>>(w.u, w.u_old, w.bx, w.by, w.vx, w.vy, P.M->g.n,
+    sb_shrink_kernel<<<gv, 256, 0, st>>>(w.u, w.u_old, w.bx, w.by, w.vx, w.vy, P.M->g.n, P.M->tn,
                                          df_from_double(1.0 / Sp->lambda), w.sb, w.cg, Sp->stop_rel_update,
                                          w.partials, w.counter);
     CT_CUDA(cudaGetLastError());
@@ -354,7 +369,7 @@ int split_bregman(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u
     // Q^T (s .* f)
     CT_CHECK(launch_to_df(M, f, P.vk == ValKind::F16 ? M->row_scale : nullptr, w.y, M->rows, st));
     CT_CHECK(launch_adjoint_df(M, P.vk, w.y, w.atf, Sp->alpha, st));
-    widen_kernel<<<gv, 256, 0, st>>>(u, w.u, n2);
+    widen_kernel<<<gv, 256, 0, st>>>(u, w.u, M->g.n, M->tn);
     CT_CUDA(cudaGetLastError());
     CT_CUDA(cudaMemsetAsync(w.bx, 0, n2 * sizeof(float2), st));
     CT_CUDA(cudaMemsetAsync(w.by, 0, n2 * sizeof(float2), st));
@@ -389,7 +404,7 @@ int split_bregman(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u
         cudaGraphExecDestroy(exec);
         CT_CUDA(e);
     }
-    narrow_kernel<<<gv, 256, 0, st>>>(w.u, u, n2);
+    narrow_kernel<<<gv, 256, 0, st>>>(w.u, u, M->g.n, M->tn);
     CT_CUDA(cudaGetLastError());
     if (stats) {
         SbSlice h;

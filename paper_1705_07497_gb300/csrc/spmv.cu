@@ -1,15 +1,28 @@
-// Stand-alone products y = A x and x = A^T y with FP32 vectors (ct_forward and
-// ct_adjoint).  Sec. 2: the normal operator R* M* M R is the bottleneck of
-// every iterative solver; Sec. 3 replaces it by precomputed sparse matrix
-// products.  Both forms accumulate in double-float with the same kernels the
-// solvers use: one warp per row for a single slice (solver_ops.cu), one warp
-// per row and 32-slice chunk for a batch (batch.cu).
+// Stand-alone products y = A x and x = A^T y (ct_forward, ct_adjoint and their
+// FP64-vector forms).  Sec. 2: the normal operator R* M* M R is the
+// bottleneck of every iterative solver; Sec. 3 replaces it by precomputed
+// sparse matrix products.  The FP32 forms accumulate in double-float with the
+// kernels the solvers use (solver_ops.cu for one slice, batch.cu for a
+// batch); the caller's row-major image is moved to and from the internal tile
+// order on the way.
 #include "ct_internal.cuh"
 #include "dfloat.cuh"
+#include "layout.cuh"
 #include "sparse_common.cuh"
 
 namespace ct {
 namespace {
+
+// Caller's row-major image -> internal tile order (FP32, padding zero).
+__global__ void to_tiles_kernel(const float* __restrict__ in, float* __restrict__ out, int n, int tn)
+{
+    const int64_t npad = padded_pixels(n);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npad; t += (int64_t)gridDim.x * blockDim.x) {
+        int i, j;
+        tiled_coords(t, tn, i, j);
+        out[t] = (i < n && j < n) ? in[(int64_t)i * n + j] : 0.0f;
+    }
+}
 
 // FP64-vector products for the differentiable path: FP64 gathers and FP64
 // accumulation (one FMA per entry on the FP64 pipe).  The derivative of the
@@ -26,55 +39,76 @@ __device__ __forceinline__ double val64<__half>(const __half* v, int64_t k)
     return (double)__half2float(v[k]);
 }
 
-// B == 1: one warp per row, lanes interleaved over the entries.
+struct F64Map {
+    int which;  // 0: A (rows = rays, columns = internal pixels); 1: A^T (rows = internal pixels)
+    const int32_t* col;
+    const uint16_t* col16;
+    const int32_t* band_lo;
+    int n, tn, nb, nk;
+};
+
+// Index into the caller's vector for an entry (pixel: row-major; ray: q).
+__device__ __forceinline__ int64_t f64_col(const F64Map& fm, int64_t row, int64_t k)
+{
+    if (fm.which == 0) {
+        int i, j;
+        tiled_coords(__ldg(fm.col + k), fm.tn, i, j);
+        return (int64_t)i * fm.n + j;
+    }
+    const int c = (int)__ldg(fm.col16 + k);
+    const int a = c / kBandW;
+    return (int64_t)a * fm.nb + fm.band_lo[(row >> 8) * fm.nk + a] + (c - a * kBandW);
+}
+
+// Output position of a row in the caller's vector (-1: padding pixel).
+__device__ __forceinline__ int64_t f64_row(const F64Map& fm, int64_t row)
+{
+    if (fm.which == 0) return row;
+    int i, j;
+    tiled_coords(row, fm.tn, i, j);
+    return (i < fm.n && j < fm.n) ? (int64_t)i * fm.n + j : -1;
+}
+
+// One warp per (row, 32-slice chunk), lane = slice (B = 1 uses lanes over entries).
 template <typename VT>
-__global__ void __launch_bounds__(256) csr_f64_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                                      const VT* __restrict__ val, int64_t rows,
-                                                      const double* __restrict__ x, double* __restrict__ y,
-                                                      const float* __restrict__ row_scale,
-                                                      const float* __restrict__ in_scale)
+__global__ void __launch_bounds__(256) f64_kernel(const int64_t* __restrict__ rp, F64Map fm, const VT* __restrict__ val,
+                                                  int64_t rows, const double* __restrict__ x, double* __restrict__ y,
+                                                  int B, const float* __restrict__ row_scale,
+                                                  const float* __restrict__ in_scale)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t row = warp; row < rows; row += nw) {
-        double acc = 0.0;
-        for (int64_t k = rp[row] + lane; k < rp[row + 1]; k += 32) {
-            const int c = __ldg(col + k);
-            double xv = __ldg(x + c);
-            if (in_scale) xv *= (double)__ldg(in_scale + c);
-            acc = fma(val64<VT>(val, k), xv, acc);
-        }
+    if (B == 1) {
+        for (int64_t row = warp; row < rows; row += nw) {
+            double acc = 0.0;
+            for (int64_t k = rp[row] + lane; k < rp[row + 1]; k += 32) {
+                const int64_t c = f64_col(fm, row, k);
+                double xv = __ldg(x + c);
+                if (in_scale) xv *= (double)__ldg(in_scale + c);
+                acc = fma(val64<VT>(val, k), xv, acc);
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) y[row] = row_scale ? acc * (double)row_scale[row] : acc;
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            const int64_t pos = f64_row(fm, row);
+            if (lane == 0 && pos >= 0) y[pos] = row_scale ? acc * (double)row_scale[row] : acc;
+        }
+        return;
     }
-}
-
-// B > 1: one warp per (row, 32-slice chunk), lane = slice.
-template <typename VT>
-__global__ void __launch_bounds__(256) spmm_f64_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                                       const VT* __restrict__ val, int64_t rows,
-                                                       const double* __restrict__ x, double* __restrict__ y, int B,
-                                                       const float* __restrict__ row_scale,
-                                                       const float* __restrict__ in_scale)
-{
-    const int lane = threadIdx.x & 31;
     const int chunks = (B + 31) / 32;
-    const int64_t task0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t ntask = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t task = task0; task < rows * chunks; task += ntask) {
+    for (int64_t task = warp; task < rows * chunks; task += nw) {
         const int64_t row = task / chunks;
         const int b = (int)(task % chunks) * 32 + lane;
-        if (b >= B) continue;
+        const int64_t pos = f64_row(fm, row);
+        if (b >= B || pos < 0) continue;
         double acc = 0.0;
         for (int64_t k = rp[row]; k < rp[row + 1]; ++k) {
-            const int c = __ldg(col + k);
-            double xv = __ldg(x + (int64_t)c * B + b);
+            const int64_t c = f64_col(fm, row, k);
+            double xv = __ldg(x + c * B + b);
             if (in_scale) xv *= (double)__ldg(in_scale + c);
             acc = fma(val64<VT>(val, k), xv, acc);
         }
-        y[row * B + b] = row_scale ? acc * (double)row_scale[row] : acc;
+        y[pos * B + b] = row_scale ? acc * (double)row_scale[row] : acc;
     }
 }
 
@@ -85,37 +119,18 @@ int product_f64(const ct_matrix* M, int which, const double* in, double* out, in
     // FP16 storage: A = diag(s) Q, A^T y = Q^T (s .* y)
     const float* row_scale = (f16 && which == 0) ? M->row_scale : nullptr;
     const float* in_scale = (f16 && which == 1) ? M->row_scale : nullptr;
-    if (B == 1) {
-        const int grid = grid_for(M, C.rows, 8, 8);
-        if (f16)
-            csr_f64_kernel<__half><<<grid, 256, 0, st>>>(C.row_ptr, C.col, C.qval, C.rows, in, out, row_scale, in_scale);
-        else
-            csr_f64_kernel<float><<<grid, 256, 0, st>>>(C.row_ptr, C.col, C.val, C.rows, in, out, row_scale, in_scale);
-    } else {
-        const int64_t tasks = C.rows * ((B + 31) / 32);
-        const int grid = grid_for(M, tasks, 8, 8);
-        if (f16)
-            spmm_f64_kernel<__half><<<grid, 256, 0, st>>>(C.row_ptr, C.col, C.qval, C.rows, in, out, B, row_scale,
-                                                          in_scale);
-        else
-            spmm_f64_kernel<float><<<grid, 256, 0, st>>>(C.row_ptr, C.col, C.val, C.rows, in, out, B, row_scale,
-                                                         in_scale);
-    }
+    const F64Map fm{which, M->A.col, M->At.col16, M->band_lo, M->g.n, M->tn, M->g.n_bins, M->n_kept};
+    const int64_t tasks = C.rows * (B == 1 ? 1 : (B + 31) / 32);
+    const int grid = grid_for(M, tasks, 8, 8);
+    if (f16)
+        f64_kernel<__half><<<grid, 256, 0, st>>>(C.row_ptr, fm, C.qval, C.rows, in, out, B, row_scale, in_scale);
+    else
+        f64_kernel<float><<<grid, 256, 0, st>>>(C.row_ptr, fm, C.val, C.rows, in, out, B, row_scale, in_scale);
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
 
 }  // namespace
-
-int launch_forward_f64(const ct_matrix* M, ValKind, const double* x, double* y, int32_t batch, cudaStream_t st)
-{
-    return product_f64(M, 0, x, y, batch, st);
-}
-
-int launch_adjoint_f64(const ct_matrix* M, ValKind, const double* y, double* x, int32_t batch, cudaStream_t st)
-{
-    return product_f64(M, 1, y, x, batch, st);
-}
 
 int grid_for(const ct_matrix* M, int64_t work_items, int items_per_block, int max_per_sm)
 {
@@ -128,8 +143,19 @@ int grid_for(const ct_matrix* M, int64_t work_items, int items_per_block, int ma
 
 int launch_forward(const ct_matrix* M, ValKind vk, const float* x, float* y, int32_t batch, cudaStream_t st)
 {
-    if (batch == 1) return launch_forward_f32(M, vk, x, y, st);
-    return batched_forward_adjoint(M, 0, x, y, batch, st);
+    if (batch != 1) return batched_forward_adjoint(M, 0, x, y, batch, st);
+    ct_matrix* Mm = const_cast<ct_matrix*>(M);
+    Workspace& w = Mm->ws;
+    if (w.pub_x_len < M->npad) {
+        cudaFree(w.pub_x);
+        w.pub_x = nullptr;
+        w.pub_x_len = 0;
+        CT_CUDA(cudaMalloc((void**)&w.pub_x, (size_t)M->npad * sizeof(float)));
+        w.pub_x_len = M->npad;
+    }
+    to_tiles_kernel<<<grid_for(M, M->npad, 256, 8), 256, 0, st>>>(x, w.pub_x, M->g.n, M->tn);
+    CT_CUDA(cudaGetLastError());
+    return launch_forward_f32(M, vk, w.pub_x, y, st);
 }
 
 int launch_adjoint(const ct_matrix* M, ValKind vk, const float* y, float* x, int32_t batch, cudaStream_t st)
@@ -148,6 +174,16 @@ int launch_adjoint(const ct_matrix* M, ValKind vk, const float* y, float* x, int
     }
     CT_CHECK(launch_to_df(M, y, M->row_scale, w.pub_y2, M->rows, st));
     return launch_adjoint_f32(M, vk, y, w.pub_y2, x, st);
+}
+
+int launch_forward_f64(const ct_matrix* M, ValKind, const double* x, double* y, int32_t batch, cudaStream_t st)
+{
+    return product_f64(M, 0, x, y, batch, st);
+}
+
+int launch_adjoint_f64(const ct_matrix* M, ValKind, const double* y, double* x, int32_t batch, cudaStream_t st)
+{
+    return product_f64(M, 1, y, x, batch, st);
 }
 
 }  // namespace ct
