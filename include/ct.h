@@ -64,7 +64,7 @@ enum {
 
 /* Matrix storage flags for ct_build_matrix (Sec. 3: precomputed sparse form). */
 enum {
-    CT_VAL_FP32 = 0,          /* FP32 values, int32 column indices (CSR)         */
+    CT_VAL_FP32 = 0,          /* FP32 values                                      */
     CT_VAL_FP16_ROWSCALE = 1, /* A = diag(s) Q: Q in FP16 (|Q| <= 1), s FP32 per
                                  row; A^T is applied as Q^T (s .* y), so the
                                  quantised normal operator stays symmetric     */
@@ -81,12 +81,17 @@ typedef struct {
 
 typedef struct ct_matrix *ct_matrix_t; /* opaque, library-owned, device-resident */
 
-/* Builds A = M R and A^T for geometry *g on the current CUDA device, as
- * row-sorted CSR (rows padded so that each starts on a 16-byte boundary; the
- * padding entries hold value 0).  Both matrices are computed from the same
- * closed-form chord length, so A^T holds exactly the values of A.
+/* Builds A = M R and A^T for geometry *g on the current CUDA device.  The
+ * device form is internal: both matrices are stored in sliced ELL (slices of
+ * 32 rows, 8-entry chunks per row, padding entries of value 0); A's columns
+ * index a tiled image layout and A^T's rows follow it, with 16-bit column
+ * indices local to each image tile's band of detector bins.  Both matrices
+ * are computed from the same closed-form chord length, so A^T holds exactly
+ * the values of A; ct_matrix_export returns plain CSR.
  * Errors: CT_ERR_ARG (n <= 0, n*n >= 2^31, counts <= 0, NULL out),
- * CT_ERR_OOM, CT_ERR_CUDA.  *out receives the handle (NULL on failure). */
+ * CT_ERR_UNSUPPORTED (a tile's band of kept angles does not fit shared
+ * memory: about 1000 kept angles on this device), CT_ERR_OOM, CT_ERR_CUDA.
+ * *out receives the handle (NULL on failure). */
 int ct_build_matrix(const ct_geometry *g, uint32_t flags, ct_matrix_t *out);
 
 /* rows = n_kept*n_bins, cols = N*N, nnz = number of stored nonzeros (no
@@ -169,6 +174,24 @@ typedef struct {
  * stats may be NULL (then the call does not synchronise). */
 int ct_split_bregman(ct_matrix_t A, const ct_sb_params *params, const float *f, float *u,
                      int32_t batch, ct_sb_stats *stats, void *cuda_stream);
+
+/* Ragged batch: `count` independent split-Bregman problems of possibly
+ * different geometries in one call (Sec. 4's reconstruction, many slices and
+ * scanners at once).  Problem i uses matrix A[i] (its geometry), data f[i]
+ * ([rows_i], device pointer) and image u[i] ([N_i*N_i], device pointer; in =
+ * initial guess, out = reconstruction); every problem runs with the same
+ * params.  Problems that share a handle are solved together as one batch of
+ * that handle (SpMM); the groups' Bregman updates are captured in one CUDA
+ * graph, each group on its own stream so small problems run side by side,
+ * and the graph is replayed outer_iters times.  The u[i] must not overlap
+ * each other or any f[j].  stats: NULL, or an array of `count` entries, one
+ * per problem (then the call synchronises on cuda_stream).  Handles must live
+ * on the current device; calls sharing a handle must be serialised like any
+ * solver call.  Errors: CT_ERR_ARG (count < 1, NULL arrays or pointers, host
+ * pointers, bad params), CT_ERR_OOM, CT_ERR_CUDA, and per problem
+ * CT_ERR_BREAKDOWN / CT_ERR_NONFINITE (the first one met is returned). */
+int ct_split_bregman_ragged(int32_t count, const ct_matrix_t *A, const float *const *f, float *const *u,
+                            const ct_sb_params *params, ct_sb_stats *stats, void *cuda_stream);
 
 /* Allocation-free variant of ct_cg_solve.  The paper has no counterpart.
  *

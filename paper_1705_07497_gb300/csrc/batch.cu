@@ -1,8 +1,8 @@
 // Batched solvers: many slices sharing one geometry (vectors [len][B], the
 // slice index innermost).  The sparse products become SpMMs with the slices
 // as the dense inner dimension: a warp owns one row for a chunk of 32 slices
-// (one slice per lane), reads the row's entries 32 at a time (coalesced),
-// stages them in shared memory and broadcasts them, so each lane gathers the
+// (one slice per lane), reads the row's entries 32 at a time (four 8-entry
+// chunks of the SELL layout), stages them in shared memory and broadcasts them, so each lane gathers the
 // 32 contiguous slice values of every column it meets.  The blocks of all
 // chunks of a row range are adjacent in launch order, so the matrix is read
 // from HBM once and reused from L2 by the other chunks.
@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <vector>
 
 #include "ct_internal.cuh"
@@ -32,16 +33,55 @@ __device__ __forceinline__ void st_y(float* y, int64_t i, float2 v) { y[i] = df_
 __device__ __forceinline__ void st_y(float2* y, int64_t i, float2 v) { y[i] = v; }
 
 struct Grid2 {
-    int rb;      // row blocks
+    int rb;      // row blocks per slice chunk
     int chunks;  // ceil(B / 32)
 };
 
-// Block (rb, chunk) decomposition of a 1-D grid: consecutive blocks share rows.
+// Block (rb, chunk) of a 1-D grid of rb * chunks blocks, chunk-major: the
+// resident blocks work on one chunk of 32 slices at a time, so the chunk's
+// slice vectors stay in L2 while the matrix streams.
 __device__ __forceinline__ void block_coords(int chunks, int& rb, int& chunk)
 {
-    rb = (int)blockIdx.x / chunks;
-    chunk = (int)blockIdx.x % chunks;
+    const int G = (int)gridDim.x / chunks;
+    rb = (int)blockIdx.x % G;
+    chunk = (int)blockIdx.x / G;
 }
+
+// Lanes of a warp over (row, slice).  B >= 32: the warp takes one row for 32
+// slices (slice chunk * 32 + lane).  B < 32: the warp splits into 32 / W
+// sub-groups of W lanes (W = the power of two >= B), one row per sub-group,
+// slice = lane % W, so that small batches keep the lanes busy.
+struct LaneMap {
+    int W;    // lanes per row
+    int g;    // this lane's sub-group
+    int b;    // this lane's slice
+    int rpw;  // rows per warp
+};
+
+__host__ __device__ inline int lanes_per_row(int B)
+{
+    if (B >= 32) return 32;
+    int W = 1;
+    while (W < B) W <<= 1;
+    return W;
+}
+
+__device__ __forceinline__ LaneMap lane_map(int B, int chunk, int lane)
+{
+    LaneMap m;
+    m.W = lanes_per_row(B);
+    m.g = lane / m.W;
+    m.b = B >= 32 ? chunk * 32 + lane : lane % m.W;
+    m.rpw = 32 / m.W;
+    return m;
+}
+
+// First row of the warp (its sub-group 0) and the stride between a warp's rows.
+__device__ __forceinline__ int64_t warp_row0(int rb, int w, const LaneMap& m)
+{
+    return ((int64_t)rb * kWarps + w) * m.rpw;
+}
+__device__ __forceinline__ int64_t row_stride(int G, const LaneMap& m) { return (int64_t)G * kWarps * m.rpw; }
 
 __device__ __forceinline__ bool slice_live(int b, int B, const CgSlice* cg, const SbSlice* sb)
 {
@@ -53,18 +93,29 @@ __device__ __forceinline__ bool slice_live(int b, int B, const CgSlice* cg, cons
 
 // Sum over the block's warps of each lane's value (fixed order), written as
 // the block's partial for slice chunk*32 + lane:  partials[(q*B + b)*G + rb].
+// With sub-groups (W < 32) the lanes of one slice are first combined by a
+// fixed butterfly, and lanes b < B write.
 template <int NQ>
-__device__ __forceinline__ void block_partials(const float2 (&v)[NQ], float2* partials, int B, int G, int rb,
-                                               int chunk)
+__device__ __forceinline__ void block_partials(float2 (&v)[NQ], float2* partials, int B, int G, int rb, int chunk,
+                                               int W)
 {
     __shared__ float2 red[NQ][kWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = W; o < 32; o <<= 1) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            float2 t;
+            t.x = __shfl_xor_sync(0xffffffffu, v[q].x, o);
+            t.y = __shfl_xor_sync(0xffffffffu, v[q].y, o);
+            v[q] = df_add(v[q], t);
+        }
+    }
 #pragma unroll
     for (int q = 0; q < NQ; ++q) red[q][w][lane] = v[q];
     __syncthreads();
     if (w == 0) {
         const int b = chunk * 32 + lane;
-        if (b < B) {
+        if (b < B && lane < W) {
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 float2 s = red[q][0][lane];
@@ -84,11 +135,13 @@ struct BProd {
 };
 
 // Column of an entry: A stores internal pixel indices; A^T stores band-local
-// indices k * W + w that map to sinogram row k * n_bins + band_lo(tile, k) + w.
+// indices off_k + w that map to sinogram row k * n_bins + band_lo(tile, k) + w.
 struct ColMap {
     const int32_t* col;       // A
     const uint16_t* col16;    // A^T (band-local)
     const int32_t* band_lo;
+    const int32_t* band_off;
+    const uint16_t* band_angle;
     int nb, nk;
 };
 
@@ -96,8 +149,8 @@ __device__ __forceinline__ int map_col(const ColMap& cm, int64_t row, int64_t k)
 {
     if (cm.col) return __ldcs(cm.col + k);
     const int c = (int)__ldcs(cm.col16 + k);
-    const int a = c / kBandW;
-    return a * cm.nb + cm.band_lo[(row >> 8) * cm.nk + a] + (c - a * kBandW);
+    const int a = __ldg(cm.band_angle + c);
+    return a * cm.nb + __ldg(cm.band_lo + (row >> 8) * cm.nk + a) + (c - __ldg(cm.band_off + a));
 }
 
 // Output position of (row, slice): internal layout, or for USER_OUT the
@@ -108,8 +161,42 @@ struct OutMap {
 };
 
 // Y[row][b] = scale * sum_k val_k X[col_k][b].
+// Stages up to W entries of each sub-group's row (j0 .. j0 + W - 1) in the
+// warp's shared buffer: lane (g, t) loads entry j0 + t of its sub-group's row.
+template <typename VT>
+__device__ __forceinline__ void stage_entries(const ColMap& cm, const VT* __restrict__ val, int64_t row,
+                                              int64_t base, int len, int j0, int t, int2* stage)
+{
+    int2 e = make_int2(0, 0);
+    if (j0 + t < len) {
+        const int64_t k = chunk_pos(base, j0 + t);
+        e = make_int2(map_col(cm, row, k), __float_as_int(Vals<VT>::one(val, k)));
+    }
+    *stage = e;
+}
+
+// acc += sum over the cnt staged entries of val * X[col][b].
+template <typename XT>
+__device__ __forceinline__ void staged_dot(const int2* st, int cnt, const XT* __restrict__ x, int B, int b,
+                                           float& hs, float& hc)
+{
+    int t = 0;
+    for (; t + 4 <= cnt; t += 4) {
+        int2 e[4];
+        float2 xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) e[u] = st[t + u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = ld_x(x, (int64_t)e[u].x * B + b);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc_fma(hs, hc, __int_as_float(e[u].y), xv[u]);
+    }
+    for (; t < cnt; ++t) acc_fma(hs, hc, __int_as_float(st[t].y), ld_x(x, (int64_t)st[t].x * B + b));
+}
+
+// Y[row][b] = scale * sum_k val_k X[col_k][b].
 template <typename VT, typename XT, typename YT>
-__global__ void __launch_bounds__(256) spmm_df_kernel(CsrView m, ColMap cm, const VT* __restrict__ val,
+__global__ void __launch_bounds__(256) spmm_df_kernel(SellView m, ColMap cm, const VT* __restrict__ val,
                                                       const XT* __restrict__ x, YT* __restrict__ y, int B,
                                                       BProd a, OutMap om)
 {
@@ -119,38 +206,24 @@ __global__ void __launch_bounds__(256) spmm_df_kernel(CsrView m, ColMap cm, cons
     const int chunks = (B + 31) / 32;
     block_coords(chunks, rb, chunk);
     const int G = (int)gridDim.x / chunks;
-    const int b = chunk * 32 + lane;
+    const LaneMap lm = lane_map(B, chunk, lane);
+    const int b = lm.b, t_in = lane % lm.W;
     const bool live = slice_live(b, B, a.cg, a.sb);
-    for (int64_t row = (int64_t)rb * kWarps + w; row < m.rows; row += (int64_t)G * kWarps) {
+    for (int64_t r0 = warp_row0(rb, w, lm); r0 < m.rows; r0 += row_stride(G, lm)) {
+        const int64_t row = r0 + lm.g;
+        const bool rv = row < m.rows;
+        const int len = rv ? m.len[row] : 0;
+        const int64_t base = rv ? row_base(m, row) : 0;
+        const int maxlen = __reduce_max_sync(0xffffffffu, len);
         float hs = 0.0f, hc = 0.0f;
-        const int64_t rs = m.rp[row], re = m.rp[row + 1];
-        for (int64_t k0 = rs; k0 < re; k0 += 32) {
-            const int64_t k = k0 + lane;
-            int2 e = make_int2(0, 0);
-            if (k < re) e = make_int2(map_col(cm, row, k), __float_as_int(Vals<VT>::one(val, k)));
-            stage[w][lane] = e;
+        for (int j0 = 0; j0 < maxlen; j0 += lm.W) {
+            stage_entries<VT>(cm, val, row, base, len, j0, t_in, &stage[w][lane]);
             __syncwarp();
-            const int cnt = (re - k0) < 32 ? (int)(re - k0) : 32;
-            if (live) {
-                int t = 0;
-                for (; t + 4 <= cnt; t += 4) {
-                    int2 st[4];
-                    float2 xv[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) st[u] = stage[w][t + u];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) xv[u] = ld_x(x, (int64_t)st[u].x * B + b);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) acc_fma(hs, hc, __int_as_float(st[u].y), xv[u]);
-                }
-                for (; t < cnt; ++t) {
-                    const int2 st = stage[w][t];
-                    acc_fma(hs, hc, __int_as_float(st.y), ld_x(x, (int64_t)st.x * B + b));
-                }
-            }
+            const int cnt = min(lm.W, len - j0);
+            if (live && cnt > 0) staged_dot<XT>(&stage[w][lm.g * lm.W], cnt, x, B, b, hs, hc);
             __syncwarp();
         }
-        if (live) {
+        if (live && rv) {
             float2 v = acc_value(hs, hc);
             if (a.row_scale) {
                 const float s = a.row_scale[row];
@@ -158,13 +231,14 @@ __global__ void __launch_bounds__(256) spmm_df_kernel(CsrView m, ColMap cm, cons
                 if (a.rpow == 2) v = df_mul_f(v, s);
             }
             int64_t pos = row;
+            bool keep = true;
             if (om.user) {
                 int i, j;
                 tiled_coords(row, om.tn, i, j);
-                if (i >= om.n || j >= om.n) continue;
+                keep = i < om.n && j < om.n;
                 pos = (int64_t)i * om.n + j;
             }
-            st_y(y, pos * B + b, df_mul(a.scale, v));
+            if (keep) st_y(y, pos * B + b, df_mul(a.scale, v));
         }
     }
 }
@@ -233,7 +307,7 @@ __device__ __forceinline__ void bop_epilogue(const BOp& a, int64_t t, int i, int
 
 // A^T y for every slice fused with the operator epilogue (rows = pixels).
 template <typename VT, int MODE>
-__global__ void __launch_bounds__(256) spmm_op_kernel(CsrView m, ColMap cm, const VT* __restrict__ val,
+__global__ void __launch_bounds__(256) spmm_op_kernel(SellView m, ColMap cm, const VT* __restrict__ val,
                                                       const float2* __restrict__ y, int B, BOp a)
 {
     __shared__ int2 stage[kWarps][32];
@@ -242,39 +316,25 @@ __global__ void __launch_bounds__(256) spmm_op_kernel(CsrView m, ColMap cm, cons
     const int chunks = (B + 31) / 32;
     block_coords(chunks, rb, chunk);
     const int G = (int)gridDim.x / chunks;
-    const int b = chunk * 32 + lane;
+    const LaneMap lm = lane_map(B, chunk, lane);
+    const int b = lm.b, t_in = lane % lm.W;
     const bool live = slice_live(b, B, MODE == 2 ? nullptr : a.cg, a.sb);
     float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
-    for (int64_t row = (int64_t)rb * kWarps + w; row < m.rows; row += (int64_t)G * kWarps) {
+    for (int64_t r0 = warp_row0(rb, w, lm); r0 < m.rows; r0 += row_stride(G, lm)) {
+        const int64_t row = r0 + lm.g;
+        const bool rv = row < m.rows;
+        const int len = rv ? m.len[row] : 0;
+        const int64_t base = rv ? row_base(m, row) : 0;
+        const int maxlen = __reduce_max_sync(0xffffffffu, len);
         float hs = 0.0f, hc = 0.0f;
-        const int64_t rs = m.rp[row], re = m.rp[row + 1];
-        for (int64_t k0 = rs; k0 < re; k0 += 32) {
-            const int64_t k = k0 + lane;
-            int2 e = make_int2(0, 0);
-            if (k < re) e = make_int2(map_col(cm, row, k), __float_as_int(Vals<VT>::one(val, k)));
-            stage[w][lane] = e;
+        for (int j0 = 0; j0 < maxlen; j0 += lm.W) {
+            stage_entries<VT>(cm, val, row, base, len, j0, t_in, &stage[w][lane]);
             __syncwarp();
-            const int cnt = (re - k0) < 32 ? (int)(re - k0) : 32;
-            if (live) {
-                int t = 0;
-                for (; t + 4 <= cnt; t += 4) {
-                    int2 st[4];
-                    float2 xv[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) st[u] = stage[w][t + u];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) xv[u] = __ldg(y + (int64_t)st[u].x * B + b);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) acc_fma(hs, hc, __int_as_float(st[u].y), xv[u]);
-                }
-                for (; t < cnt; ++t) {
-                    const int2 st = stage[w][t];
-                    acc_fma(hs, hc, __int_as_float(st.y), __ldg(y + (int64_t)st.x * B + b));
-                }
-            }
+            const int cnt = min(lm.W, len - j0);
+            if (live && cnt > 0) staged_dot<float2>(&stage[w][lm.g * lm.W], cnt, y, B, b, hs, hc);
             __syncwarp();
         }
-        if (live) {
+        if (live && rv) {
             int i, j;
             tiled_coords(row, a.tn, i, j);
             if (i < a.n && j < a.n) {
@@ -286,7 +346,7 @@ __global__ void __launch_bounds__(256) spmm_op_kernel(CsrView m, ColMap cm, cons
         }
     }
     float2 v[2] = {acc_value(s0, c0), acc_value(s1, c1)};
-    block_partials<2>(v, a.partials, B, G, rb, chunk);
+    block_partials<2>(v, a.partials, B, G, rb, chunk, lm.W);
 }
 
 // Surrogate stencil T (Sec. 3.2) for every slice fused with the epilogue.
@@ -307,13 +367,15 @@ __global__ void __launch_bounds__(256) stencil_b_kernel(int B, BOp a, const int3
     const int chunks = (B + 31) / 32;
     block_coords(chunks, rb, chunk);
     const int G = (int)gridDim.x / chunks;
-    const int b = chunk * 32 + lane;
+    const LaneMap lm = lane_map(B, chunk, lane);
+    const int b = lm.b;
+    const int64_t r_first = warp_row0(rb, w, lm) + lm.g, r_step = row_stride(G, lm);
     const bool live = slice_live(b, B, MODE == 2 ? nullptr : a.cg, a.sb);
     const int n = a.n;
     const int64_t npad = padded_pixels(n);
     float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
     if (live) {
-        for (int64_t p = (int64_t)rb * kWarps + w; p < npad; p += (int64_t)G * kWarps) {
+        for (int64_t p = r_first; p < npad; p += r_step) {
             int i, j;
             tiled_coords(p, a.tn, i, j);
             if (i >= n || j >= n) {
@@ -331,7 +393,7 @@ __global__ void __launch_bounds__(256) stencil_b_kernel(int B, BOp a, const int3
         }
     }
     float2 v[2] = {acc_value(s0, c0), acc_value(s1, c1)};
-    block_partials<2>(v, a.partials, B, G, rb, chunk);
+    block_partials<2>(v, a.partials, B, G, rb, chunk, lm.W);
 }
 
 // Element-wise kernels over [n2][B]: thread = (pixel, slice).
@@ -346,11 +408,13 @@ __global__ void __launch_bounds__(256) bcg_update_kernel(float2* __restrict__ u,
     const int chunks = (B + 31) / 32;
     block_coords(chunks, rb, chunk);
     const int G = (int)gridDim.x / chunks;
-    const int b = chunk * 32 + lane;
+    const LaneMap lm = lane_map(B, chunk, lane);
+    const int b = lm.b;
+    const int64_t r_first = warp_row0(rb, w, lm) + lm.g, r_step = row_stride(G, lm);
     float s = 0.0f, c = 0.0f;
     if (slice_live(b, B, cg, sb)) {
         const float2 al = cg[b].alpha_df;
-        for (int64_t px = (int64_t)rb * kWarps + w; px < n2; px += (int64_t)G * kWarps) {
+        for (int64_t px = r_first; px < n2; px += r_step) {
             const int64_t e = px * B + b;
             u[e] = df_add(u[e], df_mul(al, p[e]));
             const float2 rn = df_sub(r[e], df_mul(al, q[e]));
@@ -359,7 +423,7 @@ __global__ void __launch_bounds__(256) bcg_update_kernel(float2* __restrict__ u,
         }
     }
     float2 v[1] = {acc_value(s, c)};
-    block_partials<1>(v, partials, B, G, rb, chunk);
+    block_partials<1>(v, partials, B, G, rb, chunk, lm.W);
 }
 
 __global__ void __launch_bounds__(256) bcg_direction_kernel(float2* __restrict__ p, const float2* __restrict__ r,
@@ -371,10 +435,12 @@ __global__ void __launch_bounds__(256) bcg_direction_kernel(float2* __restrict__
     const int chunks = (B + 31) / 32;
     block_coords(chunks, rb, chunk);
     const int G = (int)gridDim.x / chunks;
-    const int b = chunk * 32 + lane;
+    const LaneMap lm = lane_map(B, chunk, lane);
+    const int b = lm.b;
+    const int64_t r_first = warp_row0(rb, w, lm) + lm.g, r_step = row_stride(G, lm);
     if (!slice_live(b, B, cg, sb)) return;
     const float2 be = cg[b].beta_df;
-    for (int64_t px = (int64_t)rb * kWarps + w; px < n2; px += (int64_t)G * kWarps) {
+    for (int64_t px = r_first; px < n2; px += r_step) {
         const int64_t e = px * B + b;
         p[e] = df_add(r[e], df_mul(be, p[e]));
     }
@@ -397,11 +463,13 @@ __global__ void __launch_bounds__(256) bsb_shrink_kernel(const float2* __restric
     const int chunks = (B + 31) / 32;
     block_coords(chunks, rb, chunk);
     const int G = (int)gridDim.x / chunks;
-    const int b = chunk * 32 + lane;
+    const LaneMap lm = lane_map(B, chunk, lane);
+    const int b = lm.b;
+    const int64_t r_first = warp_row0(rb, w, lm) + lm.g, r_step = row_stride(G, lm);
     const int64_t npad = padded_pixels(n);
     float s = 0.0f, cc = 0.0f;
     if (slice_live(b, B, nullptr, sb)) {
-        for (int64_t p = (int64_t)rb * kWarps + w; p < npad; p += (int64_t)G * kWarps) {
+        for (int64_t p = r_first; p < npad; p += r_step) {
             int i, j;
             tiled_coords(p, tn, i, j);
             if (i >= n || j >= n) continue;
@@ -421,7 +489,7 @@ __global__ void __launch_bounds__(256) bsb_shrink_kernel(const float2* __restric
         }
     }
     float2 v[1] = {acc_value(s, cc)};
-    block_partials<1>(v, partials, B, G, rb, chunk);
+    block_partials<1>(v, partials, B, G, rb, chunk, lm.W);
 }
 
 // Per-slice finalisation: sum the G partials of each quantity (fixed order)
@@ -471,7 +539,26 @@ __global__ void __launch_bounds__(256) finalize_kernel(const float2* __restrict_
 }
 
 // Caller's row-major [n*n][B] (FP32) -> internal tiled [npad][B] double-float.
-__global__ void bwiden_kernel(const float* __restrict__ in, float2* __restrict__ out, int n, int tn, int B)
+// The caller's batch [len][B]: one array with the slice innermost, or one
+// array per slice (ct_split_bregman_ragged).
+struct BatchIn {
+    const float* dense;
+    const float* const* cols;
+    __device__ __forceinline__ float operator()(int64_t i, int B, int b) const
+    {
+        return dense ? dense[i * B + b] : cols[b][i];
+    }
+};
+struct BatchOut {
+    float* dense;
+    float* const* cols;
+    __device__ __forceinline__ float& operator()(int64_t i, int B, int b) const
+    {
+        return dense ? dense[i * B + b] : cols[b][i];
+    }
+};
+
+__global__ void bwiden_kernel(BatchIn in, float2* __restrict__ out, int n, int tn, int B)
 {
     const int64_t len = padded_pixels(n) * B;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
@@ -479,11 +566,11 @@ __global__ void bwiden_kernel(const float* __restrict__ in, float2* __restrict__
         const int b = (int)(e - t * B);
         int i, j;
         tiled_coords(t, tn, i, j);
-        out[e] = (i < n && j < n) ? make_float2(in[((int64_t)i * n + j) * B + b], 0.0f) : make_float2(0.0f, 0.0f);
+        out[e] = (i < n && j < n) ? make_float2(in((int64_t)i * n + j, B, b), 0.0f) : make_float2(0.0f, 0.0f);
     }
 }
 
-__global__ void bnarrow_kernel(const float2* __restrict__ in, float* __restrict__ out, int n, int tn, int B)
+__global__ void bnarrow_kernel(const float2* __restrict__ in, BatchOut out, int n, int tn, int B)
 {
     const int64_t len = padded_pixels(n) * B;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
@@ -491,7 +578,7 @@ __global__ void bnarrow_kernel(const float2* __restrict__ in, float* __restrict_
         const int b = (int)(e - t * B);
         int i, j;
         tiled_coords(t, tn, i, j);
-        if (i < n && j < n) out[((int64_t)i * n + j) * B + b] = df_to_float(in[e]);
+        if (i < n && j < n) out((int64_t)i * n + j, B, b) = df_to_float(in[e]);
     }
 }
 
@@ -509,12 +596,16 @@ __global__ void bpermute_in_kernel(const float* __restrict__ in, float* __restri
 }
 
 // f (FP32, [rows][B]) -> double-float, times the row scale s (FP16 storage).
-__global__ void bto_df_kernel(const float* __restrict__ in, const float* __restrict__ scale, float2* __restrict__ out,
-                              int64_t rows, int B)
+__global__ void bto_df_kernel(BatchIn in, const float* __restrict__ scale, float2* __restrict__ out, int64_t rows,
+                              int B)
 {
     const int64_t len = rows * B;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = scale ? two_prod(in[i], scale[i / B]) : make_float2(in[i], 0.0f);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / B;
+        const int b = (int)(e - i * B);
+        const float v = in(i, B, b);
+        out[e] = scale ? two_prod(v, scale[i]) : make_float2(v, 0.0f);
+    }
 }
 
 struct BPlan {
@@ -536,9 +627,10 @@ Grid2 make_grid(const ct_matrix* M, int64_t rows, int B)
 {
     Grid2 g;
     g.chunks = (B + 31) / 32;
-    const int64_t want = (int64_t)(M->sm_count > 0 ? M->sm_count : 148) * 8 / g.chunks;
-    int64_t rb = (rows + kWarps - 1) / kWarps;
-    if (rb > want) rb = want;
+    const int64_t rows_per_block = (int64_t)kWarps * (32 / lanes_per_row(B));
+    const int64_t cap = (int64_t)(M->sm_count > 0 ? M->sm_count : 148) * 8;
+    int64_t rb = (rows + rows_per_block - 1) / rows_per_block;
+    if (rb > cap) rb = cap;
     if (rb < 1) rb = 1;
     g.rb = (int)rb;
     return g;
@@ -566,8 +658,8 @@ int launch_fin(const BPlan& P, int kind, const Grid2& g, cudaStream_t st)
 
 ColMap colmap_of(const ct_matrix* M, int which)
 {
-    if (which == 0) return ColMap{M->A.col, nullptr, nullptr, M->g.n_bins, M->n_kept};
-    return ColMap{nullptr, M->At.col16, M->band_lo, M->g.n_bins, M->n_kept};
+    if (which == 0) return ColMap{M->A.col, nullptr, nullptr, nullptr, nullptr, M->g.n_bins, M->n_kept};
+    return ColMap{nullptr, M->At.col16, M->band_lo, M->band_off, M->band_angle, M->g.n_bins, M->n_kept};
 }
 
 // which = 0: rows of A (rays); which = 1: rows of A^T (internal pixels).
@@ -575,8 +667,8 @@ template <typename XT, typename YT>
 int launch_spmm(const ct_matrix* M, int which, ValKind vk, const XT* x, YT* y, int B, BProd a, cudaStream_t st,
                 bool user_out = false)
 {
-    const Csr& C = which == 0 ? M->A : M->At;
-    CsrView m{C.row_ptr, nullptr, C.rows};
+    const Sell& C = which == 0 ? M->A : M->At;
+    const SellView m{C.slice_ptr, C.row_len, C.rows};
     const ColMap cm = colmap_of(M, which);
     const OutMap om{user_out ? 1 : 0, M->g.n, M->tn};
     const Grid2 g = make_grid(M, C.rows, B);
@@ -599,8 +691,8 @@ int bapply(const BPlan& P, BOp ep, const float2* in, cudaStream_t st, Grid2& g_u
         BProd a{vk == ValKind::F16 ? P.M->row_scale : nullptr, vk == ValKind::F16 ? 2 : 0,
                 make_float2(1.0f, 0.0f), ep.mode == 2 ? nullptr : w.cg, P.sb};
         CT_CHECK(launch_spmm(P.M, 0, vk, in, w.y, P.B, a, st));
-        const Csr& C = P.M->At;
-        CsrView m{C.row_ptr, nullptr, C.rows};
+        const Sell& C = P.M->At;
+        const SellView m{C.slice_ptr, C.row_len, C.rows};
         const ColMap cm = colmap_of(P.M, 1);
         g_used = P.g_rows_t;
         const int blocks = g_used.rb * g_used.chunks;
@@ -735,7 +827,7 @@ int batched_forward_adjoint(const ct_matrix* M, int which, const float* in, floa
     }
     if (vk == ValKind::F16) {
         // A^T y = Q^T (s .* y): the scaled copy goes through the workspace sinogram buffer
-        bto_df_kernel<<<grid_blocks(M, M->rows * B), 256, 0, st>>>(in, M->row_scale, w.y, M->rows, B);
+        bto_df_kernel<<<grid_blocks(M, M->rows * B), 256, 0, st>>>(BatchIn{in, nullptr}, M->row_scale, w.y, M->rows, B);
         CT_CUDA(cudaGetLastError());
         return launch_spmm(M, 1, vk, (const float2*)w.y, out, B, a, st, true);
     }
@@ -752,11 +844,11 @@ int cg_solve_batched(ct_matrix* M, const ct_cg_params* Pp, const float* rhs, flo
     CT_CHECK(bmake_plan(M, B, Pp->c_id, Pp->c_ata, Pp->c_grad, Pp->rel_tol, Pp->surrogate_r,
                         Pp->surrogate_square, Pp->refresh_every, P));
     const int64_t len = P.n2 * B;
-    bwiden_kernel<<<grid_blocks(M, len), 256, 0, st>>>(rhs, w.rhs, M->g.n, M->tn, B);
-    bwiden_kernel<<<grid_blocks(M, len), 256, 0, st>>>(u, w.u, M->g.n, M->tn, B);
+    bwiden_kernel<<<grid_blocks(M, len), 256, 0, st>>>(BatchIn{rhs, nullptr}, w.rhs, M->g.n, M->tn, B);
+    bwiden_kernel<<<grid_blocks(M, len), 256, 0, st>>>(BatchIn{u, nullptr}, w.u, M->g.n, M->tn, B);
     CT_CUDA(cudaGetLastError());
     CT_CHECK(benqueue_cg(P, w.rhs, Pp->max_iters, st));
-    bnarrow_kernel<<<grid_blocks(M, len), 256, 0, st>>>(w.u, u, M->g.n, M->tn, B);
+    bnarrow_kernel<<<grid_blocks(M, len), 256, 0, st>>>(w.u, BatchOut{u, nullptr}, M->g.n, M->tn, B);
     CT_CUDA(cudaGetLastError());
     if (stats) {
         std::vector<CgSlice> h(B);
@@ -778,12 +870,35 @@ int cg_solve_batched(ct_matrix* M, const ct_cg_params* Pp, const float* rhs, flo
     return CT_OK;
 }
 
-int split_bregman_batched(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u, int32_t B,
-                          ct_sb_stats* stats, cudaStream_t st)
+// Up to kMax device pointers, passed by value to the kernel that stores them.
+struct PtrChunk {
+    static constexpr int kMax = 128;
+    float* p[kMax];
+    int n, offset;
+};
+
+__global__ void set_ptrs_kernel(float** dst, PtrChunk c)
+{
+    if ((int)threadIdx.x < c.n) dst[c.offset + threadIdx.x] = c.p[threadIdx.x];
+}
+
+// One batched split-Bregman run on handle M: set-up, one Bregman update
+// (replayed), and read-out, so that several runs can share one graph.
+struct SbRun {
+    ct_matrix* M = nullptr;
+    const ct_sb_params* Sp = nullptr;
+    BPlan P;
+    int B = 0;
+};
+
+int sb_prepare(ct_matrix* M, const ct_sb_params* Sp, BatchIn f, BatchIn u, int32_t B, SbRun& R, cudaStream_t st)
 {
     CT_CHECK(ensure_workspace(M, B, true));
     Workspace& w = M->ws;
-    BPlan P;
+    R.M = M;
+    R.Sp = Sp;
+    R.B = B;
+    BPlan& P = R.P;
     CT_CHECK(bmake_plan(M, B, 0.0, Sp->alpha, Sp->lambda, 0.0, Sp->surrogate_r, Sp->surrogate_square,
                         Sp->refresh_every, P));
     P.sb = w.sb;
@@ -809,58 +924,157 @@ int split_bregman_batched(ct_matrix* M, const ct_sb_params* Sp, const float* f, 
     CT_CUDA(cudaMemsetAsync(w.vy, 0, len * sizeof(float2), st));
     CT_CUDA(cudaMemsetAsync(w.sb, 0, sizeof(SbSlice) * B, st));
     CT_CUDA(cudaMemcpyAsync(w.u_old, w.u, len * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    return CT_OK;
+}
+
+// One Bregman update: inner CG, shrink and Bregman step, update size and stop rule.
+int sb_update(const SbRun& R, cudaStream_t s)
+{
+    const BPlan& P = R.P;
+    ct_matrix* M = R.M;
+    Workspace& w = M->ws;
     const int pblocks = P.g_pix.rb * P.g_pix.chunks;
-    const float2 gamma = df_from_double(1.0 / Sp->lambda);
-    auto outer = [&](cudaStream_t s) -> int {
-        CT_CHECK(benqueue_cg(P, nullptr, Sp->inner_cg_iters, s));
-        bsb_shrink_kernel<<<pblocks, 256, 0, s>>>(w.u, w.u_old, w.bx, w.by, w.vx, w.vy, M->g.n, M->tn, B, gamma, w.sb,
-                                                  w.partials);
-        CT_CUDA(cudaGetLastError());
-        finalize_kernel<FIN_SB, 1><<<B, 256, 0, s>>>(w.partials, P.g_pix.rb, B, w.cg, w.sb, Sp->stop_rel_update);
-        CT_CUDA(cudaGetLastError());
-        return CT_OK;
-    };
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    CT_CUDA(cudaStreamIsCapturing(st, &cs));
-    if (cs != cudaStreamCaptureStatusNone || Sp->outer_iters <= 2) {
-        for (int k = 0; k < Sp->outer_iters; ++k) CT_CHECK(outer(st));
-    } else {
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        CT_CUDA(cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal));
-        const int rc = outer(w.cap_stream);
-        cudaError_t e = cudaStreamEndCapture(w.cap_stream, &graph);
-        if (rc != CT_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return rc;
-        }
-        CT_CUDA(e);
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        CT_CUDA(e);
-        for (int k = 0; k < Sp->outer_iters; ++k) {
-            e = cudaGraphLaunch(exec, st);
-            if (e != cudaSuccess) break;
-        }
-        cudaGraphExecDestroy(exec);
-        CT_CUDA(e);
-    }
-    bnarrow_kernel<<<grid_blocks(M, len), 256, 0, st>>>(w.u, u, M->g.n, M->tn, B);
+    CT_CHECK(benqueue_cg(P, nullptr, R.Sp->inner_cg_iters, s));
+    bsb_shrink_kernel<<<pblocks, 256, 0, s>>>(w.u, w.u_old, w.bx, w.by, w.vx, w.vy, M->g.n, M->tn, R.B,
+                                              df_from_double(1.0 / R.Sp->lambda), w.sb, w.partials);
     CT_CUDA(cudaGetLastError());
-    if (stats) {
-        std::vector<SbSlice> h(B);
-        CT_CUDA(cudaMemcpyAsync(h.data(), w.sb, sizeof(SbSlice) * B, cudaMemcpyDeviceToHost, st));
-        CT_CUDA(cudaStreamSynchronize(st));
+    finalize_kernel<FIN_SB, 1><<<R.B, 256, 0, s>>>(w.partials, P.g_pix.rb, R.B, w.cg, w.sb, R.Sp->stop_rel_update);
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+// Writes the reconstructions and, if stats is given, waits and fills one
+// ct_sb_stats per slice (per_slice) or one summary (slice 0, min outer_done).
+int sb_finish(const SbRun& R, BatchOut u, ct_sb_stats* stats, bool per_slice, cudaStream_t st)
+{
+    ct_matrix* M = R.M;
+    Workspace& w = M->ws;
+    const int B = R.B;
+    bnarrow_kernel<<<grid_blocks(M, R.P.n2 * B), 256, 0, st>>>(w.u, u, M->g.n, M->tn, B);
+    CT_CUDA(cudaGetLastError());
+    if (!stats) return CT_OK;
+    std::vector<SbSlice> h(B);
+    CT_CUDA(cudaMemcpyAsync(h.data(), w.sb, sizeof(SbSlice) * B, cudaMemcpyDeviceToHost, st));
+    CT_CUDA(cudaStreamSynchronize(st));
+    int status = CT_OK;
+    if (per_slice) {
+        for (int b = 0; b < B; ++b) {
+            stats[b].outer_done = h[b].outer_done;
+            stats[b].first_update_l1 = h[b].first_upd;
+            stats[b].last_update_l1 = h[b].last_upd;
+            stats[b].status = h[b].status;
+            if (h[b].status != CT_OK && status == CT_OK) status = h[b].status;
+        }
+    } else {
         stats->outer_done = h[0].outer_done;
         stats->first_update_l1 = h[0].first_upd;
         stats->last_update_l1 = h[0].last_upd;
-        stats->status = CT_OK;
         for (const SbSlice& s : h) {
             stats->outer_done = std::min(stats->outer_done, s.outer_done);
-            if (s.status != CT_OK && stats->status == CT_OK) stats->status = s.status;
+            if (s.status != CT_OK && status == CT_OK) status = s.status;
         }
-        if (stats->status != CT_OK) return fail(stats->status, "split Bregman inner solve failed");
+        stats->status = status;
     }
+    if (status != CT_OK) return fail(status, "split Bregman inner solve failed");
+    return CT_OK;
+}
+
+int split_bregman_batched(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u, int32_t B,
+                          ct_sb_stats* stats, cudaStream_t st)
+{
+    SbRun R;
+    CT_CHECK(sb_prepare(M, Sp, BatchIn{f, nullptr}, BatchIn{u, nullptr}, B, R, st));
+    CT_CHECK(run_updates({[&R](cudaStream_t s) { return sb_update(R, s); }}, {M->ws.cap_stream}, Sp->outer_iters,
+                         st));
+    return sb_finish(R, BatchOut{u, nullptr}, stats, false, st);
+}
+
+// Groups the problems by handle; a group of one runs the single-slice kernels,
+// larger groups the batched (SpMM) kernels through a per-slice pointer table.
+int split_bregman_ragged(int32_t count, ct_matrix* const* A, const float* const* f, float* const* u,
+                         const ct_sb_params* Sp, ct_sb_stats* stats, cudaStream_t st)
+{
+    std::vector<ct_matrix*> handles;
+    std::vector<std::vector<int>> members;
+    for (int i = 0; i < count; ++i) {
+        size_t g = 0;
+        while (g < handles.size() && handles[g] != A[i]) ++g;
+        if (g == handles.size()) {
+            handles.push_back(A[i]);
+            members.emplace_back();
+        }
+        members[g].push_back(i);
+    }
+    const size_t G = handles.size();
+    std::vector<SbRun> runs(G);
+    struct Free1 {
+        void operator()(Sb1Run* r) const { sb1_free(r); }
+    };
+    std::vector<std::unique_ptr<Sb1Run, Free1>> runs1(G);
+    std::vector<UpdateFn> fns;
+    std::vector<cudaStream_t> caps;
+    for (size_t g = 0; g < G; ++g) {
+        ct_matrix* M = handles[g];
+        const int B = (int)members[g].size();
+        if (B == 1) {
+            Sb1Run* r = nullptr;
+            CT_CHECK(sb1_prepare(M, Sp, f[members[g][0]], u[members[g][0]], &r, st));
+            runs1[g].reset(r);
+            fns.push_back([r](cudaStream_t s) { return sb1_update(r, s); });
+        } else {
+            CT_CHECK(ensure_workspace(M, B, true));
+            Workspace& w = M->ws;
+            if (w.ragged_cap < B) {
+                cudaFree(w.ragged_ptrs);
+                w.ragged_ptrs = nullptr;
+                w.ragged_cap = 0;
+                const cudaError_t e = cudaMalloc(&w.ragged_ptrs, sizeof(float*) * 2 * (size_t)B);
+                if (e == cudaErrorMemoryAllocation) {
+                    (void)cudaGetLastError();
+                    return fail(CT_ERR_OOM, "device allocation of the ragged pointer table failed");
+                }
+                CT_CUDA(e);
+                w.ragged_cap = B;
+            }
+            // the table [f columns | u columns] is written by kernels on st
+            // (pointers passed by value), so it is ordered after any earlier
+            // call on st that still reads it
+            PtrChunk c;
+            for (int b0 = 0; b0 < 2 * B; b0 += PtrChunk::kMax) {
+                c.n = std::min(PtrChunk::kMax, 2 * B - b0);
+                c.offset = b0;
+                for (int k = 0; k < c.n; ++k) {
+                    const int e = b0 + k;
+                    c.p[k] = e < B ? const_cast<float*>(f[members[g][e]]) : u[members[g][e - B]];
+                }
+                set_ptrs_kernel<<<1, PtrChunk::kMax, 0, st>>>(w.ragged_ptrs, c);
+                CT_CUDA(cudaGetLastError());
+            }
+            CT_CHECK(sb_prepare(M, Sp, BatchIn{nullptr, w.ragged_ptrs}, BatchIn{nullptr, w.ragged_ptrs + B}, B,
+                                runs[g], st));
+            SbRun* r = &runs[g];
+            fns.push_back([r](cudaStream_t s) { return sb_update(*r, s); });
+        }
+        caps.push_back(M->ws.cap_stream);
+    }
+    CT_CHECK(run_updates(fns, caps, Sp->outer_iters, st));
+    int status = CT_OK;
+    std::vector<ct_sb_stats> gs;
+    for (size_t g = 0; g < G; ++g) {
+        const int B = (int)members[g].size();
+        gs.assign(B, ct_sb_stats{});
+        int rc;
+        if (B == 1)
+            rc = sb1_finish(runs1[g].get(), u[members[g][0]], stats ? gs.data() : nullptr, st);
+        else
+            rc = sb_finish(runs[g], BatchOut{nullptr, handles[g]->ws.ragged_ptrs + B}, stats ? gs.data() : nullptr,
+                           true, st);
+        if (rc != CT_OK && rc != CT_ERR_BREAKDOWN && rc != CT_ERR_NONFINITE) return rc;
+        if (rc != CT_OK && status == CT_OK) status = rc;
+        if (stats)
+            for (int b = 0; b < B; ++b) stats[members[g][b]] = gs[b];
+    }
+    if (status != CT_OK) return fail(status, "split Bregman inner solve failed");
     return CT_OK;
 }
 

@@ -81,12 +81,15 @@ __device__ __forceinline__ __half f16_from_bits(uint16_t b)
     return __half(r);
 }
 
+// Position of entry j of a row whose entry 0 sits at `base` (SELL layout).
+__device__ __forceinline__ int64_t entry_pos(int64_t base, int64_t j) { return base + ((j >> 3) << 8) + (j & 7); }
+
 // One thread per ray q = k*n_bins + b: sweep the image rows, evaluate the
 // pixels of each row the line can reach, keep lengths >= kMinLen.
 template <bool FILL>
 __global__ void a_rows_kernel(int n, int tn, int nb, int n_kept, const AngleRow* __restrict__ ang,
                               int32_t* __restrict__ row_len, float* __restrict__ row_max,
-                              const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col,
+                              const int64_t* __restrict__ slice_ptr, int32_t* __restrict__ col,
                               float* __restrict__ val, __half* __restrict__ qval,
                               const float* __restrict__ scale)
 {
@@ -101,7 +104,7 @@ __global__ void a_rows_kernel(int n, int tn, int nb, int n_kept, const AngleRow*
     int64_t base = 0;
     double sq = 1.0;
     if (FILL) {
-        base = row_ptr[q];
+        base = slice_ptr[q >> 5] + ((q & 31) << 3);
         if (qval) sq = (double)scale[q];
     }
     int32_t last = 0;
@@ -127,9 +130,10 @@ __global__ void a_rows_kernel(int n, int tn, int nb, int n_kept, const AngleRow*
             if (len < kMinLen) continue;
             last = (int32_t)tiled_index(i, j, tn);
             if (FILL) {
-                col[base + cnt] = last;
-                if (val) val[base + cnt] = (float)len;
-                if (qval) qval[base + cnt] = f16_from_bits(f64_to_f16_bits(len / sq));
+                const int64_t e = entry_pos(base, cnt);
+                col[e] = last;
+                if (val) val[e] = (float)len;
+                if (qval) qval[e] = f16_from_bits(f64_to_f16_bits(len / sq));
             } else {
                 mx = fmax(mx, len);
             }
@@ -140,8 +144,9 @@ __global__ void a_rows_kernel(int n, int tn, int nb, int n_kept, const AngleRow*
         row_len[q] = cnt;
         if (row_max) row_max[q] = (float)mx;
     } else {
-        const int64_t end = row_ptr[q + 1];
-        for (int64_t e = base + cnt; e < end; ++e) {
+        // the rest of the row's last chunk repeats the last column with value 0
+        for (int j = cnt; j % kChunk != 0; ++j) {
+            const int64_t e = entry_pos(base, j);
             col[e] = last;
             if (val) val[e] = 0.0f;
             if (qval) qval[e] = __float2half(0.0f);
@@ -152,11 +157,12 @@ __global__ void a_rows_kernel(int n, int tn, int nb, int n_kept, const AngleRow*
 // One thread per internal pixel index t (tile order): for every kept angle,
 // evaluate the bins whose rays can cross the pixel; entries come out by angle,
 // then bin, with the column written as the band-local index
-// k * W + (b - band_lo(tile, k)).  Padding pixels get empty rows.
+// off_k + (b - band_lo(tile, k)).  Padding pixels get empty rows.
 template <bool FILL>
 __global__ void at_rows_kernel(int n, int tn, int nb, int n_kept, const AngleRow* __restrict__ ang,
-                               const int32_t* __restrict__ band_lo, int64_t npad,
-                               int32_t* __restrict__ row_len, const int64_t* __restrict__ row_ptr,
+                               const int32_t* __restrict__ band_lo, const int32_t* __restrict__ band_off,
+                               int64_t npad,
+                               int32_t* __restrict__ row_len, const int64_t* __restrict__ slice_ptr,
                                uint16_t* __restrict__ col16, float* __restrict__ val,
                                __half* __restrict__ qval, const float* __restrict__ scale,
                                int32_t* __restrict__ bad)
@@ -174,7 +180,7 @@ __global__ void at_rows_kernel(int n, int tn, int nb, int n_kept, const AngleRow
     const double xc = j - half + 0.5, yc = i - half + 0.5;
     const double mid = 0.5 * (nb - 1);
     int cnt = 0;
-    int64_t base = FILL ? row_ptr[t] : 0;
+    const int64_t base = FILL ? slice_ptr[t >> 5] + ((t & 31) << 3) : 0;
     uint16_t last = 0;
     for (int k = 0; k < n_kept; ++k) {
         const AngleRow g = ang[k];
@@ -186,15 +192,16 @@ __global__ void at_rows_kernel(int n, int tn, int nb, int n_kept, const AngleRow
             const double len = chord(ray_offset(xc, yc, g.c, g.s, sb), g);
             if (len < kMinLen) continue;
             const int w = b - blo[k];
-            if (w < 0 || w >= kBandW) {
+            if (w < 0 || w >= band_off[k + 1] - band_off[k]) {
                 atomicExch(bad, 1);
                 continue;
             }
-            last = (uint16_t)(k * kBandW + w);
+            last = (uint16_t)(band_off[k] + w);
             if (FILL) {
-                col16[base + cnt] = last;
-                if (val) val[base + cnt] = (float)len;
-                if (qval) qval[base + cnt] = f16_from_bits(f64_to_f16_bits(len / (double)scale[(int64_t)k * nb + b]));
+                const int64_t e = entry_pos(base, cnt);
+                col16[e] = last;
+                if (val) val[e] = (float)len;
+                if (qval) qval[e] = f16_from_bits(f64_to_f16_bits(len / (double)scale[(int64_t)k * nb + b]));
             }
             ++cnt;
         }
@@ -202,8 +209,8 @@ __global__ void at_rows_kernel(int n, int tn, int nb, int n_kept, const AngleRow
     if (!FILL) {
         row_len[t] = cnt;
     } else {
-        const int64_t end = row_ptr[t + 1];
-        for (int64_t e = base + cnt; e < end; ++e) {
+        for (int j = cnt; j % kChunk != 0; ++j) {
+            const int64_t e = entry_pos(base, j);
             col16[e] = last;
             if (val) val[e] = 0.0f;
             if (qval) qval[e] = __float2half(0.0f);
@@ -264,27 +271,33 @@ int alloc_dev(void** p, size_t bytes)
     return CT_OK;
 }
 
-// Turns per-row lengths into padded row pointers on the host.
-int finish_layout(Csr& m, const std::vector<int32_t>& len)
+// Slice offsets of the SELL layout from the row lengths (host).
+int finish_layout(Sell& m, const std::vector<int32_t>& len)
 {
-    std::vector<int64_t> rp(len.size() + 1, 0);
+    const int64_t nslices = ((int64_t)len.size() + kSliceRows - 1) / kSliceRows;
+    std::vector<int64_t> sp(nslices + 1, 0);
     int64_t nnz = 0;
-    for (size_t i = 0; i < len.size(); ++i) {
-        nnz += len[i];
-        rp[i + 1] = rp[i] + ((int64_t)len[i] + kRowPad - 1) / kRowPad * kRowPad;
+    for (int64_t s = 0; s < nslices; ++s) {
+        int64_t longest = 0;
+        for (int64_t r = s * kSliceRows; r < (s + 1) * kSliceRows && r < (int64_t)len.size(); ++r) {
+            nnz += len[r];
+            longest = len[r] > longest ? len[r] : longest;
+        }
+        sp[s + 1] = sp[s] + (longest + kChunk - 1) / kChunk * kChunk * kSliceRows;
     }
     m.nnz = nnz;
-    m.nnz_pad = rp.back();
-    CT_CHECK(alloc_dev((void**)&m.row_ptr, rp.size() * sizeof(int64_t)));
-    CT_CUDA(cudaMemcpy(m.row_ptr, rp.data(), rp.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    m.nnz_pad = sp.back();
+    CT_CHECK(alloc_dev((void**)&m.slice_ptr, sp.size() * sizeof(int64_t)));
+    CT_CUDA(cudaMemcpy(m.slice_ptr, sp.data(), sp.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
     return CT_OK;
 }
 
-// First bin of every (tile, angle) band: the bins whose rays can cross any
-// point of the tile's square lie within [floor(t_min + mid), ceil(t_max + mid)]
-// where t runs over the projections of the square's corners; one more bin of
-// margin below, and the band has kBandW bins (a 16-pixel square projects to
-// at most 16 sqrt(2) < 22.7 detector units).
+// First bin of every (tile, angle) band.  The tile's square projects onto
+// [t_min, t_min + L_k], L_k = 16 (|cos| + |sin|), t over the square's corners;
+// a ray at s_b can give the tile a nonzero length only for s_b in that closed
+// interval (on its ends only along an edge, by the edge reading).  The band
+// starts at ceil(t_min + mid - 1e-6) and has floor(L_k + 2e-6) + 2 bins,
+// which covers the interval with a margin of 1e-6 at either end.
 std::vector<int32_t> band_table(const ct_geometry& g, const std::vector<double>& hc,
                                 const std::vector<double>& hs, int tn)
 {
@@ -299,12 +312,23 @@ std::vector<int32_t> band_table(const ct_geometry& g, const std::vector<double>&
                 for (int cx = 0; cx < 2; ++cx)
                     for (int cy = 0; cy < 2; ++cy)
                         tmin = std::fmin(tmin, (x0 + cx * kTile) * hc[k] + (y0 + cy * kTile) * hs[k]);
-                const double b = std::floor(tmin + mid) - 1.0;
+                const double b = std::ceil(tmin + mid - 1e-6);
                 lo[((size_t)ti * tn + tj) * nk + k] = (int32_t)std::fmax(b, 0.0);
             }
         }
     }
     return lo;
+}
+
+// Offsets of the angles' slots within a band: off[k+1] - off[k] = W_k.
+std::vector<int32_t> band_offsets(const std::vector<double>& hc, const std::vector<double>& hs)
+{
+    std::vector<int32_t> off(hc.size() + 1, 0);
+    for (size_t k = 0; k < hc.size(); ++k) {
+        const double len = kTile * (std::fabs(hc[k]) + std::fabs(hs[k]));
+        off[k + 1] = off[k] + (int32_t)std::floor(len + 2e-6) + 2;
+    }
+    return off;
 }
 
 std::vector<AngleRow> angle_table(const ct_geometry& g, std::vector<double>& hc, std::vector<double>& hs)
@@ -338,15 +362,15 @@ std::vector<AngleRow> angle_table(const ct_geometry& g, std::vector<double>& hc,
 
 }  // namespace
 
-void free_csr(Csr& c)
+void free_sell(Sell& c)
 {
-    cudaFree(c.row_ptr);
+    cudaFree(c.slice_ptr);
     cudaFree(c.row_len);
     cudaFree(c.col);
     cudaFree(c.col16);
     cudaFree(c.val);
     cudaFree(c.qval);
-    c = Csr{};
+    c = Sell{};
 }
 
 int build_matrices(ct_matrix* M)
@@ -368,22 +392,48 @@ int build_matrices(ct_matrix* M)
     M->tn = tiles_per_side(n);
     M->npad = padded_pixels(n);
     const int tn = M->tn;
-    if ((int64_t)nk * kBandW > 65536)
-        return fail(CT_ERR_UNSUPPORTED, "more than 2340 kept angles do not fit 16-bit band indices");
+    M->h_band_off = band_offsets(M->h_cos, M->h_sin);
+    M->band_total = M->h_band_off.back();
+    for (int k = 0; k < nk; ++k)
+        if (M->h_band_off[k + 1] - M->h_band_off[k] > kBandMax)
+            return fail(CT_ERR_CUDA, "internal: band wider than kBandMax");
+    if (M->band_total > 65536)
+        return fail(CT_ERR_UNSUPPORTED, "too many kept angles for 16-bit band indices (" +
+                                             std::to_string(M->band_total) + " band slots > 65536)");
+    {
+        // the adjoint stages one tile's band (double-float values and the
+        // band starts) in shared memory, beside 4 KB of fixed buffers
+        int smem_max = 0;
+        CT_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, M->device));
+        const size_t need = ((size_t)M->band_total * 8 + 15) / 16 * 16 + (size_t)nk * 4 + 4096;
+        if (need > (size_t)smem_max)
+            return fail(CT_ERR_UNSUPPORTED, std::to_string(nk) + " kept angles need " + std::to_string(need) +
+                                                " bytes of shared memory per tile band; the device allows " +
+                                                std::to_string(smem_max));
+    }
+    M->h_band_angle.resize(M->band_total);
+    for (int k = 0; k < nk; ++k)
+        for (int c = M->h_band_off[k]; c < M->h_band_off[k + 1]; ++c) M->h_band_angle[c] = (uint16_t)k;
     M->h_band_lo = band_table(g, M->h_cos, M->h_sin, tn);
     CT_CHECK(alloc_dev((void**)&M->band_lo, M->h_band_lo.size() * sizeof(int32_t)));
     CT_CUDA(cudaMemcpy(M->band_lo, M->h_band_lo.data(), M->h_band_lo.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice));
+    CT_CHECK(alloc_dev((void**)&M->band_off, M->h_band_off.size() * sizeof(int32_t)));
+    CT_CUDA(cudaMemcpy(M->band_off, M->h_band_off.data(), M->h_band_off.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice));
+    CT_CHECK(alloc_dev((void**)&M->band_angle, M->h_band_angle.size() * sizeof(uint16_t)));
+    CT_CUDA(cudaMemcpy(M->band_angle, M->h_band_angle.data(), M->h_band_angle.size() * sizeof(uint16_t),
                        cudaMemcpyHostToDevice));
     int32_t* d_bad = nullptr;
     CT_CHECK(alloc_dev((void**)&d_bad, sizeof(int32_t)));
     CT_CUDA(cudaMemset(d_bad, 0, sizeof(int32_t)));
 
-    Csr& A = M->A;
-    Csr& T = M->At;
+    Sell& A = M->A;
+    Sell& T = M->At;
     A.rows = M->rows;
     A.cols = M->npad;
     T.rows = M->npad;
-    T.cols = (int64_t)nk * kBandW;
+    T.cols = M->band_total;
     CT_CHECK(alloc_dev((void**)&A.row_len, A.rows * sizeof(int32_t)));
     CT_CHECK(alloc_dev((void**)&T.row_len, T.rows * sizeof(int32_t)));
     if (f16) CT_CHECK(alloc_dev((void**)&M->row_scale, A.rows * sizeof(float)));
@@ -395,7 +445,7 @@ int build_matrices(ct_matrix* M)
         nullptr, nullptr);
     CT_CUDA(cudaGetLastError());
     at_rows_kernel<false><<<(unsigned)((T.rows + tpb - 1) / tpb), tpb>>>(
-        n, tn, nb, nk, d_ang, M->band_lo, M->npad, T.row_len, nullptr, nullptr, nullptr, nullptr, nullptr, d_bad);
+        n, tn, nb, nk, d_ang, M->band_lo, M->band_off, M->npad, T.row_len, nullptr, nullptr, nullptr, nullptr, nullptr, d_bad);
     CT_CUDA(cudaGetLastError());
     std::vector<int32_t> la(A.rows), lt(T.rows);
     CT_CUDA(cudaMemcpy(la.data(), A.row_len, A.rows * sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -407,16 +457,24 @@ int build_matrices(ct_matrix* M)
                                      " vs " + std::to_string(T.nnz) + ")");
     CT_CHECK(alloc_dev((void**)&A.col, A.nnz_pad * sizeof(int32_t)));
     CT_CHECK(alloc_dev((void**)&T.col16, T.nnz_pad * sizeof(uint16_t)));
-    for (Csr* m : {&A, &T}) {
-        if (f32) CT_CHECK(alloc_dev((void**)&m->val, m->nnz_pad * sizeof(float)));
-        if (f16) CT_CHECK(alloc_dev((void**)&m->qval, m->nnz_pad * sizeof(__half)));
+    CT_CUDA(cudaMemset(A.col, 0, A.nnz_pad * sizeof(int32_t)));
+    CT_CUDA(cudaMemset(T.col16, 0, T.nnz_pad * sizeof(uint16_t)));
+    for (Sell* m : {&A, &T}) {
+        if (f32) {
+            CT_CHECK(alloc_dev((void**)&m->val, m->nnz_pad * sizeof(float)));
+            CT_CUDA(cudaMemset(m->val, 0, m->nnz_pad * sizeof(float)));
+        }
+        if (f16) {
+            CT_CHECK(alloc_dev((void**)&m->qval, m->nnz_pad * sizeof(__half)));
+            CT_CUDA(cudaMemset(m->qval, 0, m->nnz_pad * sizeof(__half)));
+        }
     }
     // pass 2: fill
     a_rows_kernel<true><<<(unsigned)((A.rows + tpb - 1) / tpb), tpb>>>(
-        n, tn, nb, nk, d_ang, nullptr, nullptr, A.row_ptr, A.col, A.val, A.qval, M->row_scale);
+        n, tn, nb, nk, d_ang, nullptr, nullptr, A.slice_ptr, A.col, A.val, A.qval, M->row_scale);
     CT_CUDA(cudaGetLastError());
     at_rows_kernel<true><<<(unsigned)((T.rows + tpb - 1) / tpb), tpb>>>(
-        n, tn, nb, nk, d_ang, M->band_lo, M->npad, nullptr, T.row_ptr, T.col16, T.val, T.qval, M->row_scale, d_bad);
+        n, tn, nb, nk, d_ang, M->band_lo, M->band_off, M->npad, nullptr, T.slice_ptr, T.col16, T.val, T.qval, M->row_scale, d_bad);
     CT_CUDA(cudaGetLastError());
     int32_t bad = 0;
     CT_CUDA(cudaMemcpy(&bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost));

@@ -93,8 +93,8 @@ int ct_build_matrix(const ct_geometry* g, uint32_t flags, ct_matrix_t* out)
     if (!g) return fail(CT_ERR_ARG, "NULL geometry");
     if (g->n <= 0 || g->n_angles_total <= 0 || g->keep_every <= 0 || g->n_bins <= 0)
         return fail(CT_ERR_ARG, "geometry sizes must be positive");
-    if ((int64_t)g->n * g->n >= ((int64_t)1 << 31))
-        return fail(CT_ERR_ARG, "N*N must be below 2^31");
+    if ((int64_t)g->n * g->n >= ((int64_t)1 << 31) || padded_pixels(g->n) >= ((int64_t)1 << 31))
+        return fail(CT_ERR_ARG, "N*N (padded to whole 16 x 16 tiles) must be below 2^31");
     const int64_t n_kept = (g->n_angles_total + g->keep_every - 1) / g->keep_every;
     if (n_kept * g->n_bins >= ((int64_t)1 << 31))
         return fail(CT_ERR_ARG, "kept angles * bins must be below 2^31");
@@ -139,11 +139,13 @@ void ct_destroy_matrix(ct_matrix_t A)
     cudaDeviceSynchronize();
     free_workspace(A->ws);
     for (auto& kv : A->stencils) free_stencil(kv.second);
-    free_csr(A->A);
-    free_csr(A->At);
+    free_sell(A->A);
+    free_sell(A->At);
     cudaFree(A->row_scale);
     cudaFree(A->dirs);
     cudaFree(A->band_lo);
+    cudaFree(A->band_off);
+    cudaFree(A->band_angle);
     if (prev >= 0 && prev != A->device) cudaSetDevice(prev);
     delete A;
 }
@@ -254,20 +256,37 @@ int ct_split_bregman(ct_matrix_t A, const ct_sb_params* params, const float* f, 
     return rc;
 }
 
+int ct_split_bregman_ragged(int32_t count, const ct_matrix_t* A, const float* const* f, float* const* u,
+                            const ct_sb_params* params, ct_sb_stats* stats, void* cuda_stream)
+{
+    if (count < 1) return fail(CT_ERR_ARG, "count must be >= 1");
+    if (!A || !f || !u) return fail(CT_ERR_ARG, "NULL array of handles or vector pointers");
+    if (!params) return fail(CT_ERR_ARG, "NULL params");
+    if (!(params->lambda > 0.0) || params->outer_iters < 0 || params->inner_cg_iters < 0)
+        return fail(CT_ERR_ARG, "split Bregman needs lambda > 0 and non-negative iteration counts");
+    for (int32_t i = 0; i < count; ++i) {
+        CT_CHECK(check_handle(A[i]));
+        if (!f[i] || !u[i]) return fail(CT_ERR_ARG, "NULL vector pointer for problem " + std::to_string(i));
+        if (!is_device_ptr(f[i]) || !is_device_ptr(u[i]))
+            return fail(CT_ERR_ARG, "ct_split_bregman_ragged needs device pointers (problem " + std::to_string(i) + ")");
+    }
+    return split_bregman_ragged(count, A, f, u, params, stats, (cudaStream_t)cuda_stream);
+}
+
 int ct_matrix_export(ct_matrix_t A, int32_t which, int64_t* row_ptr, int32_t* cols, float* vals)
 {
     CT_CHECK(check_handle(A));
     if (which != 0 && which != 1) return fail(CT_ERR_ARG, "which must be 0 (A) or 1 (A^T)");
     if (!row_ptr || !cols || !vals) return fail(CT_ERR_ARG, "NULL output array");
-    const Csr& C = which == 0 ? A->A : A->At;
+    const Sell& C = which == 0 ? A->A : A->At;
     const int n = A->g.n, tn = A->tn, nb = A->g.n_bins, nk = A->n_kept;
-    std::vector<int64_t> rp(C.rows + 1);
+    std::vector<int64_t> sp((C.rows + kSliceRows - 1) / kSliceRows + 1);
     std::vector<int32_t> len(C.rows), col;
     std::vector<uint16_t> col16;
     std::vector<float> val(C.nnz_pad);
     std::vector<uint16_t> q;
     std::vector<float> s;
-    CT_CUDA(cudaMemcpy(rp.data(), C.row_ptr, rp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    CT_CUDA(cudaMemcpy(sp.data(), C.slice_ptr, sp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
     CT_CUDA(cudaMemcpy(len.data(), C.row_len, len.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
     if (which == 0) {
         col.resize(C.nnz_pad);
@@ -296,7 +315,8 @@ int ct_matrix_export(ct_matrix_t A, int32_t which, int64_t* row_ptr, int32_t* co
     if (which == 0) {
         // entries are stored in row-major pixel order; columns are tile-order indices
         for (int64_t r = 0; r < C.rows; ++r) {
-            for (int64_t k = rp[r]; k < rp[r] + len[r]; ++k, ++o) {
+            for (int64_t e = 0; e < len[r]; ++e, ++o) {
+                const int64_t k = sell_pos(sp.data(), r, e);
                 int i, j;
                 tiled_coords(col[k], tn, i, j);
                 cols[o] = i * n + j;
@@ -315,10 +335,12 @@ int ct_matrix_export(ct_matrix_t A, int32_t which, int64_t* row_ptr, int32_t* co
     }
     for (int64_t p = 0; p < (int64_t)n * n; ++p) {
         const int64_t t = row_of[p];
-        for (int64_t k = rp[t]; k < rp[t] + len[t]; ++k, ++o) {
+        for (int64_t e = 0; e < len[t]; ++e, ++o) {
+            const int64_t k = sell_pos(sp.data(), t, e);
             const int c = col16[k];
-            const int a = c / kBandW;
-            const int64_t ray = (int64_t)a * nb + A->h_band_lo[(size_t)(t >> 8) * nk + a] + (c - a * kBandW);
+            const int a = A->h_band_angle[c];
+            const int64_t ray =
+                (int64_t)a * nb + A->h_band_lo[(size_t)(t >> 8) * nk + a] + (c - A->h_band_off[a]);
             cols[o] = (int32_t)ray;
             vals[o] = value(k, ray);
         }
@@ -332,17 +354,17 @@ int ct_matrix_export_fp16(ct_matrix_t A, uint16_t* q_bits, float* scale)
     CT_CHECK(check_handle(A));
     if (!(A->flags & CT_VAL_FP16_ROWSCALE)) return fail(CT_ERR_UNSUPPORTED, "matrix has no FP16 storage");
     if (!q_bits || !scale) return fail(CT_ERR_ARG, "NULL output array");
-    const Csr& C = A->A;
-    std::vector<int64_t> rp(C.rows + 1);
+    const Sell& C = A->A;
+    std::vector<int64_t> sp((C.rows + kSliceRows - 1) / kSliceRows + 1);
     std::vector<int32_t> len(C.rows);
     std::vector<uint16_t> q(C.nnz_pad);
-    CT_CUDA(cudaMemcpy(rp.data(), C.row_ptr, rp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    CT_CUDA(cudaMemcpy(sp.data(), C.slice_ptr, sp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
     CT_CUDA(cudaMemcpy(len.data(), C.row_len, len.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
     CT_CUDA(cudaMemcpy(q.data(), C.qval, q.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost));
     CT_CUDA(cudaMemcpy(scale, A->row_scale, A->rows * sizeof(float), cudaMemcpyDeviceToHost));
     int64_t o = 0;
     for (int64_t r = 0; r < C.rows; ++r)
-        for (int64_t k = rp[r]; k < rp[r] + len[r]; ++k) q_bits[o++] = q[k];
+        for (int64_t e = 0; e < len[r]; ++e) q_bits[o++] = q[sell_pos(sp.data(), r, e)];
     return CT_OK;
 }
 

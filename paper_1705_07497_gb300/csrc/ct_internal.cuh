@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <map>
 #include <string>
 #include <utility>
@@ -19,7 +20,8 @@ namespace ct {
 // Rows of both CSR matrices are padded to a multiple of this many entries so
 // that every row starts on a 16-byte boundary for int32/FP32 (and FP16) vector
 // loads; padding entries repeat the row's last column with value 0.
-constexpr int kRowPad = 8;
+constexpr int kSliceRows = 32;  // rows per SELL slice (one warp, one row per lane)
+constexpr int kChunk = 8;       // entries per lane-contiguous chunk (16/32-byte loads)
 
 // ---------------------------------------------------------------------------
 // error reporting
@@ -43,17 +45,29 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 // ---------------------------------------------------------------------------
 // device data
 // ---------------------------------------------------------------------------
-struct Csr {
+// Sparse matrix in sliced-ELL form (SELL-32): rows are grouped in slices of
+// 32 consecutive rows; slice s stores 32 * L_s entries, L_s = its longest row
+// rounded up to kChunk, and entry j of row r sits at
+//     slice_ptr[r / 32] + (j / 8) * 256 + (r % 32) * 8 + j % 8,
+// so a warp with one row per lane reads 32 contiguous 8-entry chunks per step
+// and a lane reads its own 8 entries with one vector load.  Entries past a
+// row's length have value 0 and a valid column.
+struct Sell {
     int64_t rows = 0, cols = 0;
     int64_t nnz = 0;       // stored nonzeros
-    int64_t nnz_pad = 0;   // entries including row padding
-    int64_t* row_ptr = nullptr;  // [rows+1] padded offsets
-    int32_t* row_len = nullptr;  // [rows] unpadded lengths
+    int64_t nnz_pad = 0;   // entries including padding
+    int64_t* slice_ptr = nullptr;  // [ceil(rows/32)+1] slice offsets
+    int32_t* row_len = nullptr;    // [rows] lengths
     int32_t* col = nullptr;      // [nnz_pad] column indices (A: internal pixel index)
-    uint16_t* col16 = nullptr;   // [nnz_pad] A^T: local band index k*W + (b - band_lo)
+    uint16_t* col16 = nullptr;   // [nnz_pad] A^T: local band index off_k + (b - band_lo)
     float* val = nullptr;        // [nnz_pad] FP32 values (may be null)
     __half* qval = nullptr;      // [nnz_pad] FP16 Q values (may be null)
 };
+
+__host__ __device__ inline int64_t sell_pos(const int64_t* slice_ptr, int64_t r, int64_t j)
+{
+    return slice_ptr[r >> 5] + ((j >> 3) << 8) + ((r & 31) << 3) + (j & 7);
+}
 
 // Per-slice conjugate-gradient scalars, resident on the device.
 struct CgSlice {
@@ -109,6 +123,9 @@ struct Workspace {
     float *stage_a = nullptr, *stage_b = nullptr;
     int64_t stage_a_len = 0, stage_b_len = 0;
     cudaStream_t cap_stream = nullptr;
+    // ct_split_bregman_ragged: per-slice f and u pointers of one group [2][cap]
+    float** ragged_ptrs = nullptr;
+    int32_t ragged_cap = 0;
 };
 
 }  // namespace ct
@@ -123,10 +140,14 @@ struct ct_matrix {
     int tn = 0;              // image tiles per side
     int64_t npad = 0;        // padded internal image length (tn * 16)^2
     int32_t* band_lo = nullptr;  // device [tn*tn][n_kept]: first bin of each (tile, angle) band
-    std::vector<int32_t> h_band_lo;
+    int32_t* band_off = nullptr; // device [n_kept+1]: offset of each angle's slots in a band
+    uint16_t* band_angle = nullptr;  // device [band_total]: kept angle of each band slot
+    int band_total = 0;          // slots of one tile's band (sum of the angles' widths)
+    std::vector<int32_t> h_band_lo, h_band_off;
+    std::vector<uint16_t> h_band_angle;
     double* dirs = nullptr;  // device [n_kept][2]: cos, sin
     std::vector<double> h_cos, h_sin;
-    ct::Csr A, At;
+    ct::Sell A, At;
     float* row_scale = nullptr;  // FP16 form: s [rows]
     std::map<std::pair<int, int>, ct::Stencil> stencils;
     ct::Workspace ws;
@@ -136,7 +157,7 @@ namespace ct {
 
 // build.cu
 int build_matrices(ct_matrix* M);
-void free_csr(Csr& c);
+void free_sell(Sell& c);
 int make_stencil(ct_matrix* M, int r, int square, Stencil** out);
 void free_stencil(Stencil& s);
 
@@ -209,6 +230,21 @@ int batched_forward_adjoint(const ct_matrix* M, int which, const float* in, floa
                             cudaStream_t st);
 int cg_solve_batched(ct_matrix* M, const ct_cg_params* P, const float* rhs, float* u, int32_t B,
                      ct_cg_stats* stats, cudaStream_t st);
+// Bregman updates of one or more runs, outer_iters times: one captured graph
+// with every run on its own capture stream caps[i] (forked from caps[0]),
+// replayed on st; or directly on st when st is capturing or outer_iters <= 2.
+using UpdateFn = std::function<int(cudaStream_t)>;
+int run_updates(const std::vector<UpdateFn>& fns, const std::vector<cudaStream_t>& caps, int outer_iters,
+                cudaStream_t st);
+// single-slice split Bregman in phases (solve.cu)
+struct Sb1Run;
+int sb1_prepare(ct_matrix* M, const ct_sb_params* Sp, const float* f, const float* u, Sb1Run** out,
+                cudaStream_t st);
+int sb1_update(Sb1Run* r, cudaStream_t s);
+int sb1_finish(Sb1Run* r, float* u, ct_sb_stats* stats, cudaStream_t st);
+void sb1_free(Sb1Run* r);
+int split_bregman_ragged(int32_t count, ct_matrix* const* A, const float* const* f, float* const* u,
+                         const ct_sb_params* Sp, ct_sb_stats* stats, cudaStream_t st);
 int split_bregman_batched(ct_matrix* M, const ct_sb_params* P, const float* f, float* u, int32_t B,
                           ct_sb_stats* stats, cudaStream_t st);
 

@@ -8,10 +8,13 @@
 // padding pixels belong to no ray and stay zero.
 //
 // A^T is stored by image tiles: for tile T and kept angle k, the bins whose
-// rays can cross T form a contiguous band [band_lo(T, k), band_lo(T, k) + W)
-// of W = kBandW bins, and an entry of A^T for a pixel of T is addressed by its
-// local band index k * W + (b - band_lo(T, k)) (16 bits).  A tile's band of
-// the sinogram is staged in shared memory once and then read per entry.
+// rays can cross T form a contiguous band [band_lo(T, k), band_lo(T, k) + W_k)
+// with W_k = floor(16 (|cos| + |sin|)) + 2 <= kBandMax bins (the tile's
+// projection is 16 (|cos| + |sin|) detector units long), and an entry of A^T
+// for a pixel of T is addressed by its local band index
+// off_k + (b - band_lo(T, k)) (16 bits), off_k = W_0 + ... + W_{k-1}.  A
+// tile's band of the sinogram is staged in shared memory once and then read
+// per entry.
 #pragma once
 
 #include <cstdint>
@@ -20,7 +23,7 @@ namespace ct {
 
 constexpr int kTile = 16;        // pixels per tile side
 constexpr int kTilePix = 256;    // pixels per tile
-constexpr int kBandW = 28;       // bins per (tile, angle) band: >= 16 sqrt(2) + 4
+constexpr int kBandMax = 32;     // bound on the bins of one (tile, angle) band (<= 24 are used)
 
 __host__ __device__ inline int tiles_per_side(int n) { return (n + kTile - 1) / kTile; }
 

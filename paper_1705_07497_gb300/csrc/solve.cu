@@ -13,6 +13,9 @@
 #include <cmath>
 #include <cstring>
 
+#include <memory>
+#include <new>
+
 #include "ct_internal.cuh"
 #include "dfloat.cuh"
 #include "reduce.cuh"
@@ -246,6 +249,7 @@ void free_workspace(Workspace& w)
     cudaFree(w.counter);
     cudaFree(w.cg);
     cudaFree(w.sb);
+    cudaFree(w.ragged_ptrs);
     if (w.cap_stream) cudaStreamDestroy(w.cap_stream);
     w = Workspace{};
 }
@@ -256,17 +260,22 @@ int ensure_workspace(ct_matrix* M, int32_t batch, bool /*solver*/)
     if (w.batch >= batch && w.r) return CT_OK;
     CT_CUDA(cudaDeviceSynchronize());
     cudaStream_t keep = w.cap_stream;
+    float** rptr = w.ragged_ptrs;
+    const int32_t rcap = w.ragged_cap;
     float* sa = w.stage_a;
     float* sb = w.stage_b;
     float2* py = w.pub_y2;
     float* pxx = w.pub_x;
     const int64_t la = w.stage_a_len, lb = w.stage_b_len, lp = w.pub_y2_len, lxx = w.pub_x_len;
     w.cap_stream = nullptr;
+    w.ragged_ptrs = nullptr;
     w.stage_a = w.stage_b = nullptr;
     w.pub_y2 = nullptr;
     w.pub_x = nullptr;
     free_workspace(w);
     w.cap_stream = keep;
+    w.ragged_ptrs = rptr;
+    w.ragged_cap = rcap;
     w.stage_a = sa;
     w.stage_b = sb;
     w.pub_y2 = py;
@@ -346,15 +355,28 @@ int enqueue_sb_outer(const Plan& P, const ct_sb_params* Sp, cudaStream_t st)
 
 }  // namespace
 
-int split_bregman(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u, int32_t batch,
-                  ct_sb_stats* stats, cudaStream_t st)
+// Single-slice split Bregman in phases: set-up, one Bregman update (replayed
+// by run_updates), read-out.
+struct Sb1Run {
+    ct_matrix* M = nullptr;
+    const ct_sb_params* Sp = nullptr;
+    Plan P;
+};
+
+void sb1_free(Sb1Run* r) { delete r; }
+
+int sb1_prepare(ct_matrix* M, const ct_sb_params* Sp, const float* f, const float* u, Sb1Run** out,
+                cudaStream_t st)
 {
-    if (!(Sp->lambda > 0.0) || Sp->outer_iters < 0 || Sp->inner_cg_iters < 0)
-        return fail(CT_ERR_ARG, "split Bregman needs lambda > 0 and non-negative iteration counts");
-    if (batch != 1) return split_bregman_batched(M, Sp, f, u, batch, stats, st);
+    *out = nullptr;
+    const int32_t batch = 1;
+    std::unique_ptr<Sb1Run> R(new (std::nothrow) Sb1Run());
+    if (!R) return fail(CT_ERR_OOM, "host allocation failed");
+    R->M = M;
+    R->Sp = Sp;
     CT_CHECK(ensure_workspace(M, batch, true));
     Workspace& w = M->ws;
-    Plan P;
+    Plan& P = R->P;
     CT_CHECK(make_plan(M, &w, 0.0, Sp->alpha, Sp->lambda, 0.0, Sp->surrogate_r, Sp->surrogate_square,
                        Sp->refresh_every, P));
     P.base.gate = &w.sb->stopped;
@@ -378,32 +400,17 @@ int split_bregman(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u
     CT_CUDA(cudaMemsetAsync(w.sb, 0, sizeof(SbSlice), st));
     CT_CUDA(cudaMemcpyAsync(w.u_old, w.u, n2 * sizeof(float2), cudaMemcpyDeviceToDevice, st));
 
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    CT_CUDA(cudaStreamIsCapturing(st, &cs));
-    if (cs != cudaStreamCaptureStatusNone || Sp->outer_iters <= 2) {
-        for (int k = 0; k < Sp->outer_iters; ++k) CT_CHECK(enqueue_sb_outer(P, Sp, st));
-    } else {
-        // capture one Bregman update and replay it
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        CT_CUDA(cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal));
-        int rc = enqueue_sb_outer(P, Sp, w.cap_stream);
-        cudaError_t e = cudaStreamEndCapture(w.cap_stream, &graph);
-        if (rc != CT_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return rc;
-        }
-        CT_CUDA(e);
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        CT_CUDA(e);
-        for (int k = 0; k < Sp->outer_iters; ++k) {
-            e = cudaGraphLaunch(exec, st);
-            if (e != cudaSuccess) break;
-        }
-        cudaGraphExecDestroy(exec);
-        CT_CUDA(e);
-    }
+    *out = R.release();
+    return CT_OK;
+}
+
+int sb1_update(Sb1Run* r, cudaStream_t s) { return enqueue_sb_outer(r->P, r->Sp, s); }
+
+int sb1_finish(Sb1Run* r, float* u, ct_sb_stats* stats, cudaStream_t st)
+{
+    ct_matrix* M = r->M;
+    Workspace& w = M->ws;
+    const int gv = grid_for(M, r->P.n2, 256, 8);
     narrow_kernel<<<gv, 256, 0, st>>>(w.u, u, M->g.n, M->tn);
     CT_CUDA(cudaGetLastError());
     if (stats) {
@@ -417,6 +424,80 @@ int split_bregman(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u
         if (stats->status != CT_OK) return fail(stats->status, "split Bregman inner solve failed");
     }
     return CT_OK;
+}
+
+int run_updates(const std::vector<UpdateFn>& fns, const std::vector<cudaStream_t>& caps, int outer_iters,
+                cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CT_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone || outer_iters <= 2) {
+        for (int k = 0; k < outer_iters; ++k)
+            for (const UpdateFn& f : fns) CT_CHECK(f(st));
+        return CT_OK;
+    }
+    const int nr = (int)fns.size();
+    std::vector<cudaEvent_t> ev(nr, nullptr);
+    auto destroy_events = [&]() {
+        for (cudaEvent_t x : ev)
+            if (x) cudaEventDestroy(x);
+    };
+    for (int i = 0; i < nr; ++i) {
+        const cudaError_t e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            destroy_events();
+            return cuda_fail(e, "cudaEventCreateWithFlags", __FILE__, __LINE__);
+        }
+    }
+    cudaStream_t origin = caps[0];
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        destroy_events();
+        return cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+    }
+    // fork every further run onto its own capture stream, join them back
+    int rc = CT_OK;
+    if (nr > 1) e = cudaEventRecord(ev[0], origin);
+    for (int i = 1; i < nr && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(caps[i], ev[0], 0);
+    for (int i = 0; i < nr && e == cudaSuccess && rc == CT_OK; ++i) rc = fns[i](caps[i]);
+    for (int i = 1; i < nr && e == cudaSuccess && rc == CT_OK; ++i) {
+        e = cudaEventRecord(ev[i], caps[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, ev[i], 0);
+    }
+    const cudaError_t e_end = cudaStreamEndCapture(origin, &graph);
+    if (rc != CT_OK || e != cudaSuccess || e_end != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        destroy_events();
+        if (rc != CT_OK) return rc;
+        return cuda_fail(e != cudaSuccess ? e : e_end, "graph capture of a Bregman update", __FILE__, __LINE__);
+    }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    destroy_events();
+    CT_CUDA(e);
+    for (int k = 0; k < outer_iters; ++k) {
+        e = cudaGraphLaunch(exec, st);
+        if (e != cudaSuccess) break;
+    }
+    cudaGraphExecDestroy(exec);
+    CT_CUDA(e);
+    return CT_OK;
+}
+
+int split_bregman(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u, int32_t batch,
+                  ct_sb_stats* stats, cudaStream_t st)
+{
+    if (!(Sp->lambda > 0.0) || Sp->outer_iters < 0 || Sp->inner_cg_iters < 0)
+        return fail(CT_ERR_ARG, "split Bregman needs lambda > 0 and non-negative iteration counts");
+    if (batch != 1) return split_bregman_batched(M, Sp, f, u, batch, stats, st);
+    Sb1Run* r = nullptr;
+    CT_CHECK(sb1_prepare(M, Sp, f, u, &r, st));
+    std::unique_ptr<Sb1Run> hold(r);
+    CT_CHECK(run_updates({[r](cudaStream_t s) { return sb1_update(r, s); }}, {M->ws.cap_stream}, Sp->outer_iters,
+                         st));
+    return sb1_finish(r, u, stats, st);
 }
 
 }  // namespace ct

@@ -11,19 +11,25 @@
 // product.  No FP64 instruction runs per entry or per row: on this part the
 // FP64 pipe is far too narrow for that.
 //
-// y = A x: a warp owns a group of 16 consecutive rays and computes their dot
-// products one after the other; lanes stream the row interleaved (8
-// independent entries per lane in flight, evict-first) and gather x from the
-// tiled image layout (layout.cuh), where a run of pixels along any ray stays
-// within a few cache lines; a shuffle reduction per row, and lane r keeps
-// row r's total so the 16 stores run side by side.
+// Both matrices are stored in SELL-32 (ct_internal.cuh): a warp takes one
+// slice of 32 rows, one row per lane, and each lane walks its own row in
+// 8-entry chunks with vector loads (the warp's loads for one chunk are 32
+// contiguous chunks), two chunks in flight, accumulating in a double-float
+// pair.  No shuffles or per-row reductions; lanes past their row's length
+// stop loading.
 //
-// x = A^T y: one CTA per 16 x 16 image tile.  The CTA first copies the tile's
-// sinogram band (kBandW bins per kept angle) into shared memory with
-// coalesced loads; every entry of the tile's rows then reads its operand from
-// shared memory through its 16-bit band index.  Each warp computes 32 pixels
-// (two groups of 16), and the operator epilogue for a group runs lane-parallel.
-// Grid-wide dot products finish in the last block (reduce.cuh).
+// y = A x: slices of 32 consecutive rays; x is gathered from the tiled image
+// layout (layout.cuh), where a run of pixels along any ray stays within a few
+// cache lines.
+//
+// x = A^T y: one CTA of 8 warps per 16 x 16 image tile, one warp per slice
+// of 32 pixels.  The CTA first copies the tile's sinogram band (W_k bins per
+// kept angle, layout.cuh) into shared memory; every entry then reads its
+// operand there through its 16-bit band index.  The operator epilogue runs
+// with one pixel per lane.  Grid-wide dot products finish in the last block
+// (reduce.cuh).  At 180 kept angles the double-float band is 30.75 KB, so
+// seven CTAs fit an SM and a 512 x 512 image (1024 tiles) runs in one wave
+// on 152 SMs.
 #include "ct_internal.cuh"
 #include "dfloat.cuh"
 #include "layout.cuh"
@@ -33,12 +39,21 @@
 namespace ct {
 namespace {
 
-constexpr int kRowsPerWarp = 16;
+constexpr int kFwdWarps = 8;   // warps per block (= per slice of rays) of y = A x
+constexpr int kAdjWarps = kTilePix / kSliceRows;  // warps per CTA of x = A^T y (one per pixel slice)
+constexpr int kAdjMinBlocks = 7;                    // CTAs per SM the register budget allows
+constexpr int64_t kStep = kSliceRows * kChunk;      // entries between a lane's consecutive chunks
+
+// Bytes of a staged band of `slots` values.
+__host__ __device__ inline size_t band_bytes(int slots, size_t elem) { return (size_t)slots * elem; }
 
 struct BandView {
-    const int64_t* rp;
+    const int64_t* sp;    // slice offsets of A^T
+    const int32_t* len;   // row lengths of A^T
     const uint16_t* col16;
-    const int32_t* band_lo;
+    const int32_t* band_lo;   // [tiles][nk] first bin of each band
+    const int32_t* band_off;  // [nk+1] slot offsets of the angles
+    int slots;                // band_off[nk]
     int n, tn, nb, nk;
 };
 
@@ -52,39 +67,15 @@ __device__ __forceinline__ float2 gather_x(const float2* __restrict__ x, int64_t
 __device__ __forceinline__ void store_y(float* y, int64_t i, float2 v) { y[i] = df_to_float(v); }
 __device__ __forceinline__ void store_y(float2* y, int64_t i, float2 v) { y[i] = v; }
 
-// Dot product of one CSR row with a gathered vector; every lane gets it.
-// Lane l takes entries s + l, s + l + 32, ...: at each step the warp reads 32
-// consecutive entries (coalesced) and gathers 32 consecutive columns.
-template <typename VT, typename XT>
-__device__ __forceinline__ float2 row_dot(const CsrView& m, const VT* __restrict__ val, int64_t row,
-                                          const XT* __restrict__ x, int lane)
+__device__ __forceinline__ void load8_col(const int32_t* p, int64_t k, int (&c)[8])
 {
-    const int64_t s = m.rp[row], e = m.rp[row + 1];
-    float hs = 0.0f, hc = 0.0f;
-    for (int64_t k0 = s + lane; k0 < e; k0 += 8 * 32) {
-        int c[8];
-        float v[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int64_t k = k0 + 32 * t;
-            c[t] = k < e ? __ldcs(m.col + k) : -1;
-            v[t] = k < e ? Vals<VT>::one(val, k) : 0.0f;
-        }
-        float2 xv[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) xv[t] = c[t] >= 0 ? gather_x(x, c[t]) : make_float2(0.0f, 0.0f);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) acc_fma(hs, hc, v[t], xv[t]);
-    }
-    return warp_sum_df(acc_value(hs, hc));
+    const int4 a = __ldcs(reinterpret_cast<const int4*>(p + k));
+    const int4 b = __ldcs(reinterpret_cast<const int4*>(p + k + 4));
+    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+    c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
 }
 
-// Dot product of one A^T row with the tile's staged sinogram band, computed by
-// a half-warp: each of its 16 lanes takes 8 consecutive entries per step with
-// 16-byte loads (rows are padded to multiples of 8 entries); the operands come
-// from shared memory, so consecutive entries per lane cost nothing in
-// coalescing.  Every lane of the half-warp gets the total.
-__device__ __forceinline__ void load8_col16(const uint16_t* p, int64_t k, int (&c)[8])
+__device__ __forceinline__ void load8_col(const uint16_t* p, int64_t k, int (&c)[8])
 {
     const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p + k));
     const uint32_t w[4] = {v.x, v.y, v.z, v.w};
@@ -95,49 +86,59 @@ __device__ __forceinline__ void load8_col16(const uint16_t* p, int64_t k, int (&
     }
 }
 
-template <typename VT>
-__device__ __forceinline__ float2 band_row_dot_half(const int64_t* __restrict__ rp, const uint16_t* __restrict__ col16,
-                                                    const VT* __restrict__ val, int64_t row,
-                                                    const float2* __restrict__ band, int hl)
-{
-    const int64_t s = rp[row], e = rp[row + 1];
-    float hs = 0.0f, hc = 0.0f;
-    for (int64_t k = s + hl * 8; k < e; k += 128) {
-        int c[8];
-        float v[8];
-        load8_col16(col16, k, c);
-        Vals<VT>::load8(val, k, v);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) acc_fma(hs, hc, v[t], band[c[t]]);
-    }
-    float2 r = acc_value(hs, hc);
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {
-        float2 w;
-        w.x = __shfl_xor_sync(0xffffffffu, r.x, o);
-        w.y = __shfl_xor_sync(0xffffffffu, r.y, o);
-        r = df_add(r, w);
-    }
-    return r;
-}
+// Operand of an entry: a gathered vector element (A) or a staged band value (A^T).
+template <typename XT>
+struct Gather {
+    const XT* x;
+    __device__ __forceinline__ float2 operator()(int c) const { return gather_x(x, c); }
+};
+// (shared memory: plain loads)
+__device__ __forceinline__ float2 band_value(const float* band, int c) { return make_float2(band[c], 0.0f); }
+__device__ __forceinline__ float2 band_value(const float2* band, int c) { return band[c]; }
+template <typename BT>
+struct BandGather {
+    const BT* band;
+    __device__ __forceinline__ float2 operator()(int c) const { return band_value(band, c); }
+};
 
-// The 16 dot products of rows first .. first + 15 of the tile, two rows at a
-// time (one per half-warp); lane r (< 16) returns row first + r's total.
-template <typename VT>
-__device__ __forceinline__ float2 band_group_dots(const BandView& bv, const VT* __restrict__ val, int64_t first,
-                                                  const float2* __restrict__ band, int lane)
+// Part of the dot product of the lane's row (entry 0 at `base`, nch chunks)
+// with the operands `g` gives: chunk pairs (c, c+1) for c = c_first,
+// c_first + c_step, ...; both chunks' loads are issued before either's
+// arithmetic.  Accumulates into the double-float pair (hs, hc).
+template <typename VT, typename CT, typename G>
+__device__ __forceinline__ void row_part(const CT* __restrict__ col, const VT* __restrict__ val, int64_t base,
+                                         int nch, int c_first, int c_step, const G& g, float& hs, float& hc)
 {
-    const int half = lane >> 4, hl = lane & 15;
-    float2 mine = df_zero();
-#pragma unroll 2
-    for (int r = 0; r < kRowsPerWarp; r += 2) {
-        const float2 d = band_row_dot_half<VT>(bv.rp, bv.col16, val, first + r + half, band, hl);
-        const float2 d0 = make_float2(__shfl_sync(0xffffffffu, d.x, 0), __shfl_sync(0xffffffffu, d.y, 0));
-        const float2 d1 = make_float2(__shfl_sync(0xffffffffu, d.x, 16), __shfl_sync(0xffffffffu, d.y, 16));
-        if (lane == r) mine = d0;
-        if (lane == r + 1) mine = d1;
+    for (int c = c_first; c < nch; c += c_step) {
+        const int64_t p = base + c * kStep;
+        if (c + 1 < nch) {
+            int c0[8], c1[8];
+            float v0[8], v1[8];
+            load8_col(col, p, c0);
+            load8_col(col, p + kStep, c1);
+            Vals<VT>::load8(val, p, v0);
+            Vals<VT>::load8(val, p + kStep, v1);
+            float2 x0[8], x1[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) x0[t] = g(c0[t]);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) x1[t] = g(c1[t]);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) acc_fma(hs, hc, v0[t], x0[t]);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) acc_fma(hs, hc, v1[t], x1[t]);
+        } else {
+            int c0[8];
+            float v0[8];
+            load8_col(col, p, c0);
+            Vals<VT>::load8(val, p, v0);
+            float2 x0[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) x0[t] = g(c0[t]);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) acc_fma(hs, hc, v0[t], x0[t]);
+        }
     }
-    return mine;
 }
 
 // (grad^T grad u) at pixel (i, j), Neumann forward differences, tiled layout.
@@ -208,47 +209,77 @@ struct ProdArgs {
     const int32_t* gate;
 };
 
-// y = scale * A x, one warp per group of rays (x in the tiled layout).
+// y = scale * A x (x in the tiled layout).  One block per slice of 32 rays:
+// its kFwdWarps warps split every row's chunks (warp w takes chunk pairs
+// 2w, 2w+1, 2w+2*kFwdWarps, ...), so that at any time the block streams a
+// contiguous run of the slice, and the per-warp partial sums are combined in
+// a fixed order.
 template <typename VT, typename XT, typename YT>
-__global__ void __launch_bounds__(256) csr_df_kernel(CsrView m, const VT* __restrict__ val,
-                                                     const XT* __restrict__ x, YT* __restrict__ y,
-                                                     ProdArgs a)
+__global__ void __launch_bounds__(kFwdWarps * 32) sell_fwd_kernel(SellView m, const int32_t* __restrict__ col,
+                                                                  const VT* __restrict__ val,
+                                                                  const XT* __restrict__ x, YT* __restrict__ y,
+                                                                  ProdArgs a)
 {
     if (a.gate && *a.gate) return;
     if (a.cg && !a.cg->active) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t first = warp * kRowsPerWarp; first < m.rows; first += nw * kRowsPerWarp) {
-        const int nrows = (m.rows - first) < kRowsPerWarp ? (int)(m.rows - first) : kRowsPerWarp;
-        float2 mine = df_zero();
-        for (int r = 0; r < nrows; ++r) {
-            const float2 d = row_dot<VT, XT>(m, val, first + r, x, lane);
-            if (lane == r) mine = d;
-        }
-        if (lane < nrows) {
-            const int64_t row = first + lane;
+    __shared__ float2 part[kFwdWarps][kSliceRows];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nslices = (m.rows + kSliceRows - 1) / kSliceRows;
+    const Gather<XT> g{x};
+    for (int64_t s = blockIdx.x; s < nslices; s += gridDim.x) {
+        const int64_t row = s * kSliceRows + lane;
+        const int len = row < m.rows ? m.len[row] : 0;
+        const int nch = (len + kChunk - 1) / kChunk;
+        const int64_t base = m.sp[s] + lane * kChunk;
+        float hs = 0.0f, hc = 0.0f;
+        row_part<VT>(col, val, base, nch, 2 * w, 2 * kFwdWarps, g, hs, hc);
+        part[w][lane] = acc_value(hs, hc);
+        __syncthreads();
+        if (w == 0 && row < m.rows) {
+            float2 d = part[0][lane];
+#pragma unroll
+            for (int k = 1; k < kFwdWarps; ++k) d = df_add(d, part[k][lane]);
             if (a.row_scale) {
-                const float s = a.row_scale[row];
-                mine = df_mul_f(mine, s);
-                if (a.rpow == 2) mine = df_mul_f(mine, s);
+                const float sc = a.row_scale[row];
+                d = df_mul_f(d, sc);
+                if (a.rpow == 2) d = df_mul_f(d, sc);
             }
-            store_y(y, row, df_mul(a.scale, mine));
+            store_y(y, row, df_mul(a.scale, d));
         }
+        __syncthreads();
     }
 }
 
-// Copies the tile's sinogram band into shared memory.
+// Asynchronous 4- or 8-byte global -> shared copy; src_bytes = 0 writes zeros.
+__device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes, int src_bytes)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Copies the tile's sinogram band into shared memory: every angle's W_k bins
+// (one warp per angle, one lane per bin), all copies in flight at once; bins
+// past the detector read as zero.  Ends with the block synchronised.
 template <typename YT>
-__device__ __forceinline__ void stage_band(const BandView& bv, int tile, const YT* __restrict__ y, float2* band)
+__device__ __forceinline__ void stage_band(const BandView& bv, int tile, const YT* __restrict__ y, YT* band)
 {
     const int32_t* blo = bv.band_lo + (int64_t)tile * bv.nk;
-    const int total = bv.nk * kBandW;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        const int k = idx / kBandW;
-        const int b = blo[k] + (idx - k * kBandW);
-        band[idx] = b < bv.nb ? gather_x(y, (int64_t)k * bv.nb + b) : make_float2(0.0f, 0.0f);
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int k = threadIdx.x >> 5; k < bv.nk; k += nwarps) {
+        const int off = __ldg(bv.band_off + k);
+        if (lane < __ldg(bv.band_off + k + 1) - off) {
+            const int b = __ldg(blo + k) + lane;
+            const bool in = b < bv.nb;
+            cp_async(band + off + lane, y + (in ? (int64_t)k * bv.nb + b : 0), (int)sizeof(YT),
+                     in ? (int)sizeof(YT) : 0);
+        }
     }
+    cp_async_wait_all();
+    __syncthreads();
 }
 
 // Plain store of an A^T row total: OT = float2 writes the internal layout;
@@ -259,58 +290,60 @@ __device__ __forceinline__ void store_pix(float* out, int64_t t, int i, int j, i
     out[(int64_t)i * n + j] = df_to_float(v);
 }
 
-template <typename VT, typename YT, typename OT>
-__global__ void __launch_bounds__(256) band_adj_kernel(BandView bv, const VT* __restrict__ val,
-                                                       const YT* __restrict__ y, OT* __restrict__ out,
-                                                       float2 scale)
+// Dot product of A^T row t = tile * 256 + warp * 32 + lane with the staged band.
+template <typename VT, typename BT>
+__device__ __forceinline__ float2 band_dot(const BandView& bv, const VT* __restrict__ val, int tile,
+                                           const BT* __restrict__ band, int64_t& t)
 {
-    extern __shared__ float2 band[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    t = (int64_t)tile * kTilePix + w * kSliceRows + lane;
+    const int len = bv.len[t];
+    float hs = 0.0f, hc = 0.0f;
+    row_part<VT>(bv.col16, val, bv.sp[t >> 5] + lane * kChunk, (len + kChunk - 1) / kChunk, 0, 2,
+                 BandGather<BT>{band}, hs, hc);
+    return acc_value(hs, hc);
+}
+
+template <typename VT, typename YT, typename OT>
+__global__ void __launch_bounds__(kAdjWarps * 32, kAdjMinBlocks)
+    band_adj_kernel(BandView bv, const VT* __restrict__ val, const YT* __restrict__ y, OT* __restrict__ out,
+                    float2 scale)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    YT* band = reinterpret_cast<YT*>(smem);
     const int ntiles = bv.tn * bv.tn;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         stage_band(bv, tile, y, band);
-        __syncthreads();
-        for (int g = 0; g < 2; ++g) {
-            const int64_t first = (int64_t)tile * kTilePix + w * 32 + g * kRowsPerWarp;
-            const float2 mine = band_group_dots<VT>(bv, val, first, band, lane);
-            if (lane < kRowsPerWarp) {
-                const int64_t t = first + lane;
-                int i, j;
-                tiled_coords(t, bv.tn, i, j);
-                if (i < bv.n && j < bv.n) store_pix(out, t, i, j, bv.n, df_mul(scale, mine));
-            }
-        }
+        int64_t t;
+        const float2 d = band_dot<VT>(bv, val, tile, band, t);
+        int i, j;
+        tiled_coords(t, bv.tn, i, j);
+        if (i < bv.n && j < bv.n) store_pix(out, t, i, j, bv.n, df_mul(scale, d));
         __syncthreads();
     }
 }
 
 template <typename VT, int MODE>
-__global__ void __launch_bounds__(256) band_op_kernel(BandView bv, const VT* __restrict__ val,
-                                                      const float2* __restrict__ y, OpEpilogue a)
+__global__ void __launch_bounds__(kAdjWarps * 32, kAdjMinBlocks)
+    band_op_kernel(BandView bv, const VT* __restrict__ val, const float2* __restrict__ y, OpEpilogue a)
 {
     if (a.gate && *a.gate) return;
     if (MODE != 2 && !a.cg->active) return;
-    extern __shared__ float2 band[];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* band = reinterpret_cast<float2*>(smem);
     const int ntiles = bv.tn * bv.tn;
     float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         stage_band(bv, tile, y, band);
-        __syncthreads();
-        for (int g = 0; g < 2; ++g) {
-            const int64_t first = (int64_t)tile * kTilePix + w * 32 + g * kRowsPerWarp;
-            const float2 mine = band_group_dots<VT>(bv, val, first, band, lane);
-            if (lane < kRowsPerWarp) {
-                const int64_t t = first + lane;
-                int i, j;
-                tiled_coords(t, bv.tn, i, j);
-                if (i < bv.n && j < bv.n) {
-                    op_epilogue<MODE>(a, bv.n, bv.tn, t, i, j, mine, s0, c0, s1, c1);
-                } else {
-                    a.out[t] = df_zero();  // padding stays zero
-                    if (MODE == 2) a.p_out[t] = df_zero();
-                }
-            }
+        int64_t t;
+        const float2 d = band_dot<VT>(bv, val, tile, band, t);
+        int i, j;
+        tiled_coords(t, bv.tn, i, j);
+        if (i < bv.n && j < bv.n) {
+            op_epilogue<MODE>(a, bv.n, bv.tn, t, i, j, d, s0, c0, s1, c1);
+        } else {
+            a.out[t] = df_zero();  // padding stays zero
+            if (MODE == 2) a.p_out[t] = df_zero();
         }
         __syncthreads();
     }
@@ -365,25 +398,29 @@ __global__ void to_df_kernel(const float* __restrict__ in, const float* __restri
 }
 
 template <typename XT, typename YT>
-int launch_csr(const ct_matrix* M, ValKind vk, const XT* x, YT* y, ProdArgs a, cudaStream_t st)
+int launch_fwd(const ct_matrix* M, ValKind vk, const XT* x, YT* y, ProdArgs a, cudaStream_t st)
 {
-    const Csr& C = M->A;
-    CsrView m{C.row_ptr, C.col, C.rows};
-    const int grid = grid_for(M, C.rows, 8 * kRowsPerWarp, 8);
+    const Sell& C = M->A;
+    const SellView m{C.slice_ptr, C.row_len, C.rows};
+    // one block per slice: the block scheduler evens out slices of unequal
+    // length across SMs
+    const int64_t nslices = (C.rows + kSliceRows - 1) / kSliceRows;
+    const int grid = (int)(nslices < (1 << 30) ? nslices : (1 << 30));
     if (vk == ValKind::F16)
-        csr_df_kernel<__half, XT, YT><<<grid, 256, 0, st>>>(m, C.qval, x, y, a);
+        sell_fwd_kernel<__half, XT, YT><<<grid, kFwdWarps * 32, 0, st>>>(m, C.col, C.qval, x, y, a);
     else
-        csr_df_kernel<float, XT, YT><<<grid, 256, 0, st>>>(m, C.val, x, y, a);
+        sell_fwd_kernel<float, XT, YT><<<grid, kFwdWarps * 32, 0, st>>>(m, C.col, C.val, x, y, a);
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
 
 BandView band_view(const ct_matrix* M)
 {
-    return BandView{M->At.row_ptr, M->At.col16, M->band_lo, M->g.n, M->tn, M->g.n_bins, M->n_kept};
+    return BandView{M->At.slice_ptr, M->At.row_len, M->At.col16, M->band_lo, M->band_off, M->band_total,
+                    M->g.n, M->tn, M->g.n_bins, M->n_kept};
 }
 
-size_t band_smem(const ct_matrix* M) { return (size_t)M->n_kept * kBandW * sizeof(float2); }
+size_t band_smem(const ct_matrix* M, size_t elem) { return band_bytes(M->band_total, elem); }
 
 int band_grid(const ct_matrix* M) { return M->tn * M->tn; }
 
@@ -398,9 +435,9 @@ int allow_smem(K kernel, size_t smem)
 template <typename VT, typename YT, typename OT>
 int launch_band_adj(const ct_matrix* M, const VT* val, const YT* y, OT* out, float2 scale, cudaStream_t st)
 {
-    const size_t smem = band_smem(M);
+    const size_t smem = band_smem(M, sizeof(YT));
     CT_CHECK(allow_smem(band_adj_kernel<VT, YT, OT>, smem));
-    band_adj_kernel<VT, YT, OT><<<band_grid(M), 256, smem, st>>>(band_view(M), val, y, out, scale);
+    band_adj_kernel<VT, YT, OT><<<band_grid(M), kAdjWarps * 32, smem, st>>>(band_view(M), val, y, out, scale);
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -408,9 +445,9 @@ int launch_band_adj(const ct_matrix* M, const VT* val, const YT* y, OT* out, flo
 template <typename VT, int MODE>
 int launch_band_op(const ct_matrix* M, const VT* val, const float2* y, const OpEpilogue& ep, cudaStream_t st)
 {
-    const size_t smem = band_smem(M);
+    const size_t smem = band_smem(M, sizeof(float2));
     CT_CHECK(allow_smem(band_op_kernel<VT, MODE>, smem));
-    band_op_kernel<VT, MODE><<<band_grid(M), 256, smem, st>>>(band_view(M), val, y, ep);
+    band_op_kernel<VT, MODE><<<band_grid(M), kAdjWarps * 32, smem, st>>>(band_view(M), val, y, ep);
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -421,7 +458,7 @@ int launch_forward_df(const ct_matrix* M, ValKind vk, const float2* x, float2* y
                       const CgSlice* cg, const int32_t* gate, cudaStream_t st)
 {
     ProdArgs a{vk == ValKind::F16 ? M->row_scale : nullptr, rpow, make_float2(1.0f, 0.0f), cg, gate};
-    return launch_csr(M, vk, x, y, a, st);
+    return launch_fwd(M, vk, x, y, a, st);
 }
 
 int launch_adjoint_df(const ct_matrix* M, ValKind vk, const float2* y, float2* out, double scale,
@@ -435,7 +472,7 @@ int launch_adjoint_df(const ct_matrix* M, ValKind vk, const float2* y, float2* o
 int launch_forward_f32(const ct_matrix* M, ValKind vk, const float* x_tiled, float* y, cudaStream_t st)
 {
     ProdArgs a{vk == ValKind::F16 ? M->row_scale : nullptr, 1, make_float2(1.0f, 0.0f), nullptr, nullptr};
-    return launch_csr(M, vk, x_tiled, y, a, st);
+    return launch_fwd(M, vk, x_tiled, y, a, st);
 }
 
 int launch_adjoint_f32(const ct_matrix* M, ValKind vk, const float* y, const float2* y_scaled, float* x,

@@ -1,15 +1,22 @@
-// CSR view and value loaders shared by the sparse-product kernels.
+// SELL view and value loaders shared by the sparse-product kernels.
 #pragma once
 
 #include "ct_internal.cuh"
 
 namespace ct {
 
-struct CsrView {
-    const int64_t* rp;
-    const int32_t* col;
+struct SellView {
+    const int64_t* sp;   // slice offsets
+    const int32_t* len;  // row lengths
     int64_t rows;
 };
+
+// Position of entry 0 of `row`; entry j sits at base + (j / 8) * 256 + j % 8.
+__device__ __forceinline__ int64_t row_base(const SellView& m, int64_t row)
+{
+    return m.sp[row >> 5] + ((row & 31) << 3);
+}
+__device__ __forceinline__ int64_t chunk_pos(int64_t base, int64_t j) { return base + ((j >> 3) << 8) + (j & 7); }
 
 template <typename VT>
 struct Vals;

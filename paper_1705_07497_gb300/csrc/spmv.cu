@@ -44,6 +44,8 @@ struct F64Map {
     const int32_t* col;
     const uint16_t* col16;
     const int32_t* band_lo;
+    const int32_t* band_off;
+    const uint16_t* band_angle;
     int n, tn, nb, nk;
 };
 
@@ -56,8 +58,8 @@ __device__ __forceinline__ int64_t f64_col(const F64Map& fm, int64_t row, int64_
         return (int64_t)i * fm.n + j;
     }
     const int c = (int)__ldg(fm.col16 + k);
-    const int a = c / kBandW;
-    return (int64_t)a * fm.nb + fm.band_lo[(row >> 8) * fm.nk + a] + (c - a * kBandW);
+    const int a = __ldg(fm.band_angle + c);
+    return (int64_t)a * fm.nb + fm.band_lo[(row >> 8) * fm.nk + a] + (c - __ldg(fm.band_off + a));
 }
 
 // Output position of a row in the caller's vector (-1: padding pixel).
@@ -69,10 +71,11 @@ __device__ __forceinline__ int64_t f64_row(const F64Map& fm, int64_t row)
     return (i < fm.n && j < fm.n) ? (int64_t)i * fm.n + j : -1;
 }
 
-// One warp per (row, 32-slice chunk), lane = slice (B = 1 uses lanes over entries).
+// B = 1: one lane per row (a warp per SELL slice, the lane's row entries in
+// order).  B > 1: one warp per (row, 32-slice chunk), lane = slice.
 template <typename VT>
-__global__ void __launch_bounds__(256) f64_kernel(const int64_t* __restrict__ rp, F64Map fm, const VT* __restrict__ val,
-                                                  int64_t rows, const double* __restrict__ x, double* __restrict__ y,
+__global__ void __launch_bounds__(256) f64_kernel(SellView m, F64Map fm, const VT* __restrict__ val,
+                                                  const double* __restrict__ x, double* __restrict__ y,
                                                   int B, const float* __restrict__ row_scale,
                                                   const float* __restrict__ in_scale)
 {
@@ -80,29 +83,37 @@ __global__ void __launch_bounds__(256) f64_kernel(const int64_t* __restrict__ rp
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     if (B == 1) {
-        for (int64_t row = warp; row < rows; row += nw) {
+        const int64_t nslices = (m.rows + kSliceRows - 1) / kSliceRows;
+        for (int64_t s = warp; s < nslices; s += nw) {
+            const int64_t row = s * kSliceRows + lane;
+            if (row >= m.rows) continue;
+            const int64_t pos = f64_row(fm, row);
+            if (pos < 0) continue;
+            const int64_t base = row_base(m, row);
+            const int len = m.len[row];
             double acc = 0.0;
-            for (int64_t k = rp[row] + lane; k < rp[row + 1]; k += 32) {
+            for (int e = 0; e < len; ++e) {
+                const int64_t k = chunk_pos(base, e);
                 const int64_t c = f64_col(fm, row, k);
                 double xv = __ldg(x + c);
                 if (in_scale) xv *= (double)__ldg(in_scale + c);
                 acc = fma(val64<VT>(val, k), xv, acc);
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            const int64_t pos = f64_row(fm, row);
-            if (lane == 0 && pos >= 0) y[pos] = row_scale ? acc * (double)row_scale[row] : acc;
+            y[pos] = row_scale ? acc * (double)row_scale[row] : acc;
         }
         return;
     }
     const int chunks = (B + 31) / 32;
-    for (int64_t task = warp; task < rows * chunks; task += nw) {
+    for (int64_t task = warp; task < m.rows * chunks; task += nw) {
         const int64_t row = task / chunks;
         const int b = (int)(task % chunks) * 32 + lane;
         const int64_t pos = f64_row(fm, row);
         if (b >= B || pos < 0) continue;
+        const int64_t base = row_base(m, row);
+        const int len = m.len[row];
         double acc = 0.0;
-        for (int64_t k = rp[row]; k < rp[row + 1]; ++k) {
+        for (int e = 0; e < len; ++e) {
+            const int64_t k = chunk_pos(base, e);
             const int64_t c = f64_col(fm, row, k);
             double xv = __ldg(x + c * B + b);
             if (in_scale) xv *= (double)__ldg(in_scale + c);
@@ -114,18 +125,20 @@ __global__ void __launch_bounds__(256) f64_kernel(const int64_t* __restrict__ rp
 
 int product_f64(const ct_matrix* M, int which, const double* in, double* out, int32_t B, cudaStream_t st)
 {
-    const Csr& C = which == 0 ? M->A : M->At;
+    const Sell& C = which == 0 ? M->A : M->At;
     const bool f16 = (M->flags & CT_VAL_FP16_ROWSCALE) != 0;
     // FP16 storage: A = diag(s) Q, A^T y = Q^T (s .* y)
     const float* row_scale = (f16 && which == 0) ? M->row_scale : nullptr;
     const float* in_scale = (f16 && which == 1) ? M->row_scale : nullptr;
-    const F64Map fm{which, M->A.col, M->At.col16, M->band_lo, M->g.n, M->tn, M->g.n_bins, M->n_kept};
-    const int64_t tasks = C.rows * (B == 1 ? 1 : (B + 31) / 32);
+    const F64Map fm{which, M->A.col, M->At.col16, M->band_lo, M->band_off, M->band_angle,
+                    M->g.n, M->tn, M->g.n_bins, M->n_kept};
+    const SellView m{C.slice_ptr, C.row_len, C.rows};
+    const int64_t tasks = B == 1 ? (C.rows + kSliceRows - 1) / kSliceRows : C.rows * ((B + 31) / 32);
     const int grid = grid_for(M, tasks, 8, 8);
     if (f16)
-        f64_kernel<__half><<<grid, 256, 0, st>>>(C.row_ptr, fm, C.qval, C.rows, in, out, B, row_scale, in_scale);
+        f64_kernel<__half><<<grid, 256, 0, st>>>(m, fm, C.qval, in, out, B, row_scale, in_scale);
     else
-        f64_kernel<float><<<grid, 256, 0, st>>>(C.row_ptr, fm, C.val, C.rows, in, out, B, row_scale, in_scale);
+        f64_kernel<float><<<grid, 256, 0, st>>>(m, fm, C.val, in, out, B, row_scale, in_scale);
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }

@@ -43,6 +43,7 @@ SYMBOLS = (
     "ct_cg_solve",
     "ct_cg_solve_noalloc",
     "ct_split_bregman",
+    "ct_split_bregman_ragged",
     "ct_matrix_export",
     "ct_matrix_export_fp16",
     "ct_surrogate_stencil",
@@ -134,6 +135,7 @@ def lib():
         L.ct_cg_solve.argtypes = [vp, P(CgParams), vp, vp, i32, P(CgStats), vp]
         L.ct_cg_solve_noalloc.argtypes = [vp, P(CgParams), vp, vp, P(CgStats), vp]
         L.ct_split_bregman.argtypes = [vp, P(SbParams), vp, vp, i32, P(SbStats), vp]
+        L.ct_split_bregman_ragged.argtypes = [i32, vp, vp, vp, P(SbParams), vp, vp]
         L.ct_matrix_export.argtypes = [vp, i32, vp, vp, vp]
         L.ct_matrix_export_fp16.argtypes = [vp, vp, vp]
         L.ct_surrogate_stencil.argtypes = [vp, i32, i32, i32, vp, vp, vp, P(i32)]
@@ -243,6 +245,25 @@ def ct_split_bregman(h, params, f, u, batch, stats=None, stream=None):
     return _check(lib().ct_split_bregman(h, ctypes.byref(params), pf, pu, batch, sp, sf if stream is None else stream))
 
 
+def ct_split_bregman_ragged(handles, params, fs, us, stats=None, stream=None):
+    """One call over len(handles) problems: (handles[i], fs[i], us[i]); stats:
+    None or a ctypes array of len(handles) SbStats."""
+    count = len(handles)
+    if not (len(fs) == len(us) == count):
+        raise ValueError("handles, fs and us must have the same length")
+    hs = (ctypes.c_void_p * count)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    pf = (ctypes.c_void_p * count)()
+    pu = (ctypes.c_void_p * count)()
+    sf = None
+    for i in range(count):
+        pf[i], s_i = _vec(fs[i])
+        pu[i], _ = _vec(us[i])
+        sf = s_i if sf is None else sf
+    sp = stats if stats is not None else None
+    return _check(lib().ct_split_bregman_ragged(count, hs, pf, pu, ctypes.byref(params), sp,
+                                                sf if stream is None else stream))
+
+
 def ct_matrix_export(h, which):
     rows, cols, nnz = ct_matrix_info(h)
     n_rows = rows if which == 0 else cols
@@ -347,3 +368,17 @@ class Matrix:
 
     def surrogate_stencil(self, r, square=False):
         return ct_surrogate_stencil(self.handle, r, square)
+
+
+def split_bregman_ragged(matrices, fs, us, alpha, lam, outer, inner, stop_rel_update=0.0, surrogate_r=0,
+                         refresh_every=0, square=False, stats=True):
+    """Split Bregman over problems of possibly different geometries in one
+    call: problem i reconstructs us[i] (N_i*N_i, in = initial guess) from
+    fs[i] with matrices[i].  Returns per-problem stats (or None)."""
+    p = SbParams(alpha, lam, outer, inner, stop_rel_update, surrogate_r, refresh_every, int(square))
+    st = (SbStats * len(matrices))() if stats else None
+    ct_split_bregman_ragged([m.handle for m in matrices], p, fs, us, st)
+    if st is None:
+        return None
+    return [{"outer_done": s.outer_done, "first_update_l1": s.first_update_l1,
+             "last_update_l1": s.last_update_l1, "status": s.status} for s in st]

@@ -33,15 +33,35 @@ WORKLOADS = {
     "slice_512": dict(n=512, n_angles_total=720, keep_every=4, n_bins=725, batch=1,
                       outer=50, inner=20, alpha=1.0, lam=1.0, noise="gauss", sigma_rel=0.01,
                       seed=1000),
-    # 256 slices of 512x512 on the same geometry, Poisson noise at 1e4 counts/bin
+    # 256 slices of 512x512 on the same geometry, Poisson noise at 1e4 counts/bin,
+    # FP16 storage with a per-row FP32 scale (no FP32 residual refresh: it
+    # measured worse than none with double-float recurrences)
     "batch_512x256": dict(n=512, n_angles_total=720, keep_every=4, n_bins=725, batch=256,
                           outer=50, inner=20, alpha=1.0, lam=1.0, noise="poisson",
-                          counts=1e4, seed=2000, refresh_every=5),
+                          counts=1e4, seed=2000, refresh_every=0, fp16=True),
+    # 64 problems of different geometries in one call: N and the angle count
+    # drawn uniformly per problem (ragged_problems), all angles kept,
+    # ceil(sqrt(2) N) bins, FP16 storage, 1% Gaussian noise
+    "ragged_64": dict(count=64, sizes=(128, 256, 512, 1024), angle_counts=(60, 120, 360, 900),
+                      outer=50, inner=20, alpha=1.0, lam=1.0, noise="gauss", sigma_rel=0.01,
+                      seed=4000, fp16=True),
     # 16 slices of 256x256, 360 angles keeping every 2nd, 363 bins, 10 unrolled updates
     "grad_256x16": dict(n=256, n_angles_total=360, keep_every=2, n_bins=363, batch=16,
                         outer=10, inner=10, alpha=1.0, lam=1.0, noise="gauss", sigma_rel=0.01,
                         seed=3000),
 }
+
+
+def ragged_problems(wl):
+    """(n, n_angles_total, keep_every, n_bins, seed) of every problem of a ragged workload:
+    N and the angle count drawn uniformly (PCG64, seed + i) from the workload's lists."""
+    out = []
+    for i in range(wl["count"]):
+        rng = np.random.Generator(np.random.PCG64(wl["seed"] + i))
+        n = int(wl["sizes"][rng.integers(len(wl["sizes"]))])
+        a = int(wl["angle_counts"][rng.integers(len(wl["angle_counts"]))])
+        out.append((n, a, 1, n_bins_for(n), wl["seed"] + i))
+    return out
 
 
 def ellipse_params(seed, n_ellipses=10):

@@ -72,3 +72,15 @@ def test_binding_refuses_wrong_dtypes(lib):
         ct._vec(np.zeros(4, dtype=np.float64))
     with pytest.raises(TypeError):
         ct._vec([1.0, 2.0])
+
+
+def test_ragged_argument_errors(lib):
+    p = ct.SbParams(1.0, 1.0, 3, 3, 0.0, 0, 0, 0)
+    arr = (ctypes.c_void_p * 1)()
+    assert lib.ct_split_bregman_ragged(0, arr, arr, arr, ctypes.byref(p), None, None) == ct.CT_ERR_ARG
+    assert lib.ct_split_bregman_ragged(1, None, arr, arr, ctypes.byref(p), None, None) == ct.CT_ERR_ARG
+    assert lib.ct_split_bregman_ragged(1, arr, arr, arr, None, None, None) == ct.CT_ERR_ARG
+    bad = ct.SbParams(1.0, 0.0, 3, 3, 0.0, 0, 0, 0)  # lambda must be positive
+    assert lib.ct_split_bregman_ragged(1, arr, arr, arr, ctypes.byref(bad), None, None) == ct.CT_ERR_ARG
+    with pytest.raises(ValueError):
+        ct.ct_split_bregman_ragged([None], p, [], [])

@@ -63,8 +63,10 @@ def _data(geom, seeds, A):
     return truths, np.stack([A @ t.ravel() for t in truths], axis=1)
 
 
-@pytest.mark.parametrize("B", [3, 40])
+@pytest.mark.parametrize("B", [2, 3, 5, 17, 40, 64])
 def test_batched_cg_matches_per_slice_oracle(dev, B):
+    """Batch sizes below 32 run several rows per warp (sub-groups of 2, 4, 8, 32
+    lanes); 40 and 64 run two slice chunks."""
     ref = oracle_A(*GEOM64)
     M = gpu_A(GEOM64)
     n2 = M.cols

@@ -356,3 +356,22 @@ def test_zero_iterations_and_zero_rhs(dev):
     u = torch.zeros(M.cols, device=dev)
     s = M.cg_solve(torch.zeros(M.cols, device=dev), u, 0.0, 1.0, 1.0, 7)
     assert s["iters"] == 0 and s["status"] == 0 and float(u.abs().max()) == 0.0
+
+
+def test_surrogate_warm_start_then_exact(dev):
+    """Sec. 5's warm-start strategy: surrogate-T updates, then exact updates
+    started from that reconstruction (initial guess only), against the oracle
+    doing the same."""
+    geom = (64, 90, 3, 91)
+    A = radon.siddon_matrix(*geom)
+    M = ct.Matrix(*geom)
+    f = A @ inputs.ellipse_phantom(64, 21).ravel()
+    T = tv.surrogate_matrix(tv.surrogate_stencil(tv.point_response(A, 64), 3), 64)
+    u1 = tv.split_bregman(A, f, (64, 64), 1.0, 0.1, 8, 10, normal=lambda x: T @ x)["u"]
+    want = tv.split_bregman(A, f, (64, 64), 1.0, 0.1, 6, 10, u0=u1.ravel())["u"].ravel()
+    u = torch.zeros(64 * 64, dtype=torch.float32, device=dev)
+    ft = torch.tensor(f, dtype=torch.float32, device=dev)
+    M.split_bregman(ft, u, 1.0, 0.1, 8, 10, surrogate_r=3)
+    M.split_bregman(ft, u, 1.0, 0.1, 6, 10)
+    got = u.cpu().double().numpy()
+    assert np.linalg.norm(got - want) <= 1e-3 * np.linalg.norm(want)
