@@ -181,15 +181,15 @@ __device__ __forceinline__ void staged_dot(const int2* st, int cnt, const XT* __
                                            float& hs, float& hc)
 {
     int t = 0;
-    for (; t + 4 <= cnt; t += 4) {
-        int2 e[4];
-        float2 xv[4];
+    for (; t + 8 <= cnt; t += 8) {
+        int2 e[8];
+        float2 xv[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) e[u] = st[t + u];
+        for (int u = 0; u < 8; ++u) e[u] = st[t + u];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) xv[u] = ld_x(x, (int64_t)e[u].x * B + b);
+        for (int u = 0; u < 8; ++u) xv[u] = ld_x(x, (int64_t)e[u].x * B + b);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc_fma(hs, hc, __int_as_float(e[u].y), xv[u]);
+        for (int u = 0; u < 8; ++u) acc_fma(hs, hc, __int_as_float(e[u].y), xv[u]);
     }
     for (; t < cnt; ++t) acc_fma(hs, hc, __int_as_float(st[t].y), ld_x(x, (int64_t)st[t].x * B + b));
 }
