@@ -33,7 +33,7 @@ import numpy as np  # noqa: E402
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1705_07497_gb300 import inputs  # noqa: E402
+from paper_1705_07497_gb300 import inputs, replicas  # noqa: E402
 
 METRIC = "TV recon slices/s at <=1e-3 rel err vs FP64 oracle; SpMV/SpMM HBM GB/s"
 WORKLOAD = "slice_512"
@@ -205,9 +205,7 @@ def bench_ours(args):
 
     from paper_1705_07497_gb300 import ct
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = replicas.rank_info()
     if world > 1:
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
@@ -215,7 +213,7 @@ def bench_ours(args):
     wl = inputs.WORKLOADS[args.workload]
     n = wl["n"]
     M = ct.Matrix(n, wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
-    truth, f_host = make_data(wl, M, dev, wl["seed"] + rank)
+    truth, f_host = make_data(wl, M, dev, replicas.rank_seed(wl["seed"], rank))
     f = torch.tensor(f_host, dtype=torch.float32, device=dev)
     u = torch.zeros(n * n, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -233,8 +231,7 @@ def bench_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    if world > 1:
-        dist.barrier()
+    replicas.barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed_steps")  # lets a profiler select exactly the timed launches
@@ -244,15 +241,10 @@ def bench_ours(args):
     e1.record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    replicas.barrier(world)
     clocks = sampler.stop()
-    secs = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        t = torch.tensor([secs], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs = float(t.item())
-    value = world * args.steps / secs
+    secs = replicas.max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
+    value = replicas.job_throughput(world, args.steps, secs)
 
     # dominant kernels: the forward and adjoint CSR products, timed with CUDA
     # events on this stream, back to back, same matrix and vectors
@@ -310,17 +302,12 @@ def bench_ours(args):
     f_pin = torch.tensor(f_host, dtype=torch.float32).pin_memory()
     u_pin = torch.zeros(n * n, dtype=torch.float32).pin_memory()
     M.split_bregman(f_pin, u_pin, wl["alpha"], wl["lam"], wl["outer"], wl["inner"], stats=False)
-    if world > 1:
-        dist.barrier()
+    replicas.barrier(world)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         u_pin.zero_()
         M.split_bregman(f_pin, u_pin, wl["alpha"], wl["lam"], wl["outer"], wl["inner"], stats=False)
-    e2e_secs = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_secs], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_secs = float(t.item())
+    e2e_secs = replicas.max_over_ranks(time.perf_counter() - t0, world, dev)
 
     # to_split + A^T f + widen, per update (A u, residual, inner x 4, shrink), narrow
     launches_per_step = 3 + wl["outer"] * (2 + 4 * wl["inner"] + 1) + 1
@@ -371,7 +358,7 @@ def bench_ours(args):
                         "ms": round(t_cg * 1e3, 4), "algorithmic_bytes": int(bytes_cg)},
         },
         "e2e": {
-            "value": round(world * args.steps / e2e_secs, 4),
+            "value": round(replicas.job_throughput(world, args.steps, e2e_secs), 4),
             "unit": "slices/s",
             "h2d_bytes_per_step": int(f_pin.numel() * 4 + u_pin.numel() * 4),
             "d2h_bytes_per_step": int(u_pin.numel() * 4),
@@ -532,6 +519,109 @@ def bench_batch(args):
         "clocks": clocks,
     }
     print(json.dumps(out))
+    M.close()
+
+
+def bench_grad(args):
+    """Differentiable workload: one step = the unrolled, checkpointed split
+    Bregman of every slice (FP64 products through the autograd Functions)
+    and the backward pass of a weighted sum of the reconstructions."""
+    import torch
+
+    from paper_1705_07497_gb300 import ct
+    from paper_1705_07497_gb300.autograd import split_bregman_unrolled
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = inputs.WORKLOADS[args.workload]
+    n, B = wl["n"], wl["batch"]
+    M = ct.Matrix(n, wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
+    X = torch.empty((n * n, B), dtype=torch.float32, device=dev)
+    for b in range(B):
+        X[:, b] = torch.tensor(inputs.ellipse_phantom(n, wl["seed"] + b).ravel(), dtype=torch.float32)
+    Y = torch.empty((M.rows, B), dtype=torch.float32, device=dev)
+    M.forward(X, Y)
+    clean = Y.double().cpu().numpy()
+    F = torch.tensor(np.stack([noisy(wl, clean[:, b], wl["seed"] + 100 + b) for b in range(B)], axis=1),
+                     dtype=torch.float64, device=dev)
+    W = torch.tensor(inputs.random_vector(n * n * B, wl["seed"] + 2).reshape(n * n, B), dtype=torch.float64,
+                     device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        f = F.clone().requires_grad_(True)
+        u = split_bregman_unrolled(M, f, wl["alpha"], wl["lam"], wl["outer"], wl["inner"])
+        (W * u).sum().backward()
+        return f.grad
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed_steps")
+    e0.record(stream)
+    for _ in range(args.steps):
+        g = step()
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    secs = e0.elapsed_time(e1) / 1e3
+    assert torch.isfinite(g).all()
+    # the FP64 forward product alone: one FP64 FMA per entry and slice
+    Xd = torch.zeros((n * n, B), dtype=torch.float64, device=dev)
+    Yd = torch.empty((M.rows, B), dtype=torch.float64, device=dev)
+    for _ in range(2):
+        M.forward(Xd, Yd)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(5):
+        M.forward(Xd, Yd)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_f64 = a.elapsed_time(b) / 1e3 / 5
+    # FP64 pipe: 2 FMA per clock per SM on this part (1/64 of the FP32 rate)
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = sm_count(dev) * 2 * mhz * 1e6 / 1e12
+    ach = M.nnz * B / t_f64 / 1e12
+    print(json.dumps({
+        "metric": METRIC,
+        "value": round(B * args.steps / secs, 4),
+        "unit": "slices/s",
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1e3 * secs / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic: %d seeded random-ellipse phantoms, projected by A, 1%% Gaussian noise" % B,
+        "config": {
+            "workload": args.workload + ": %d slices of %dx%d, %d of %d angles, %d bins, unrolled split Bregman "
+                        "%d x %d CG with a checkpoint per update, forward + backward"
+                        % (B, n, n, M.rows // wl["n_bins"], wl["n_angles_total"], wl["n_bins"], wl["outer"],
+                           wl["inner"]),
+            "matrix": "SELL-32 A and A^T, FP32 values, nnz %d each" % M.nnz,
+            "l2": "inputs near L2 size (A and A^T %.0f MB)" % (M.nnz * 14 / 1e6),
+        },
+        "roofline": {
+            "kernel": "f64_kernel<float> (y = A X for %d slices, FP64 gathers and FMA)" % B,
+            "bound": "alu",
+            "achieved": round(ach, 4),
+            "peak": round(peak, 4),
+            "unit": "T FP64 FMA/s",
+            "frac": round(ach / peak, 4),
+            "traffic": None,
+            "launch_ms": round(t_f64 * 1e3, 3),
+        },
+        "e2e": None,
+        "gpu_launches": None,
+        "clocks": clocks,
+    }))
     M.close()
 
 
@@ -751,6 +841,8 @@ def main():
         bench_reference(args)
     elif "count" in wl:
         bench_ragged(args)
+    elif args.workload.startswith("grad_"):
+        bench_grad(args)
     elif wl.get("batch", 1) > 1:
         bench_batch(args)
     else:

@@ -193,6 +193,19 @@ int ct_split_bregman(ct_matrix_t A, const ct_sb_params *params, const float *f, 
 int ct_split_bregman_ragged(int32_t count, const ct_matrix_t *A, const float *const *f, float *const *u,
                             const ct_sb_params *params, ct_sb_stats *stats, void *cuda_stream);
 
+/* Launch tuning of the batched products (no counterpart in the paper).  The
+ * batched sparse products (batch >= 2) come in variants that differ only in
+ * how many staged matrix entries each lane keeps in flight (4 or 8); they
+ * compute bit-identical results.  By default the first batched solve with a
+ * given batch size on a handle times the variants on its own data (a few
+ * launches of the forward product, synchronising the stream once, never
+ * inside a stream capture) and keeps the fastest.  ct_set_spmm_unroll pins
+ * the choice for a batch size (4 or 8; 0 returns it to automatic);
+ * ct_get_spmm_unroll reports it (0 = not chosen yet).
+ * Errors: CT_ERR_ARG (batch < 2, other unroll values, NULL output). */
+int ct_set_spmm_unroll(ct_matrix_t A, int32_t batch, int32_t unroll);
+int ct_get_spmm_unroll(ct_matrix_t A, int32_t batch, int32_t *unroll);
+
 /* Allocation-free variant of ct_cg_solve.  The paper has no counterpart.
  *
  * Some callers cannot allocate device memory at the moment they need a solve:

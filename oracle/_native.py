@@ -47,6 +47,10 @@ def lib():
         ]
         L.oracle_directions.restype = None
         L.oracle_directions.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.POINTER(ctypes.c_double)] * 2
+        L.oracle_siddon_rows.restype = ctypes.c_int64
+        L.oracle_siddon_rows.argtypes = [ctypes.c_int] * 4 + [ctypes.c_int64, i64p, i64p, i64p,
+                                                              ctypes.POINTER(ctypes.c_int32),
+                                                              ctypes.POINTER(ctypes.c_double)]
         L.oracle_num_kept.restype = ctypes.c_int
         L.oracle_num_kept.argtypes = [ctypes.c_int, ctypes.c_int]
         _lib = L

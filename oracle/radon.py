@@ -83,6 +83,30 @@ def siddon_matrix(n, n_total, keep_every, n_bins):
     return sp.csr_matrix((vals, cols, row_ptr), shape=(rows, n * n))
 
 
+def siddon_rows(n, n_total, keep_every, n_bins, rows):
+    """Rows `rows` of A (same tracer as siddon_matrix) as a CSR matrix of
+    len(rows) x N^2, for geometries too large to build whole."""
+    L = _native.lib()
+    ct = _native.ctypes
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    i64p = ct.POINTER(ct.c_int64)
+    nnz = np.zeros(len(rows), dtype=np.int64)
+    total = L.oracle_siddon_rows(n, n_total, keep_every, n_bins, len(rows), rows.ctypes.data_as(i64p), None,
+                                 nnz.ctypes.data_as(i64p), None, None)
+    if total < 0:
+        raise ValueError("invalid geometry or row")
+    row_ptr = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum(nnz, out=row_ptr[1:])
+    cols = np.zeros(total, dtype=np.int32)
+    vals = np.zeros(total, dtype=np.float64)
+    rc = L.oracle_siddon_rows(n, n_total, keep_every, n_bins, len(rows), rows.ctypes.data_as(i64p),
+                              row_ptr.ctypes.data_as(i64p), nnz.ctypes.data_as(i64p),
+                              cols.ctypes.data_as(ct.POINTER(ct.c_int32)), vals.ctypes.data_as(ct.POINTER(ct.c_double)))
+    if rc < 0:
+        raise RuntimeError("oracle_siddon_rows failed (%d)" % rc)
+    return sp.csr_matrix((vals, cols, row_ptr), shape=(len(rows), n * n))
+
+
 def _clip_length(x0, y0, dx, dy, bx0, bx1, by0, by1):
     """Length of the line (x0 + t dx, y0 + t dy) inside the box (Liang-Barsky).
 

@@ -256,6 +256,58 @@ int oracle_siddon_fill(int n, int n_total, int keep_every, int n_bins,
     return rc;
 }
 
+/* The listed rays only (row indices q = kept angle * n_bins + bin), for
+ * checking matrices too large to build whole.  Pass 1 (cols == NULL): writes
+ * row_nnz[r], the entries of ray rows[r], and returns their total.  Pass 2:
+ * writes each ray's entries at row_ptr[r] of cols/vals.  Returns -1 on an
+ * invalid geometry or row, -2 if a ray's count differs from row_ptr. */
+int64_t oracle_siddon_rows(int n, int n_total, int keep_every, int n_bins, int64_t nrows,
+                           const int64_t *rows, const int64_t *row_ptr, int64_t *row_nnz,
+                           int32_t *cols, double *vals)
+{
+    if (check_geometry(n, n_total, keep_every, n_bins)) return -1;
+    const int n_kept = oracle_num_kept(n_total, keep_every);
+    oracle_entry *e = (oracle_entry *)malloc(sizeof(oracle_entry) * (size_t)(3 * n + 8) * 2);
+    double *tx = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+    double *ty = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+    if (!e || !tx || !ty) {
+        free(e);
+        free(tx);
+        free(ty);
+        return -1;
+    }
+    int64_t total = 0;
+    for (int64_t r = 0; r < nrows; ++r) {
+        const int64_t q = rows[r];
+        if (q < 0 || q >= (int64_t)n_kept * n_bins) {
+            total = -1;
+            break;
+        }
+        const int kk = (int)(q / n_bins), b = (int)(q % n_bins);
+        double c, s;
+        oracle_direction(kk * keep_every, n_total, &c, &s);
+        const double sb = (double)b - 0.5 * (double)(n_bins - 1);
+        const int m = trace_ray(n, c, s, sb, e, tx, ty);
+        if (!cols) {
+            row_nnz[r] = m;
+        } else {
+            if (row_ptr[r + 1] - row_ptr[r] != m) {
+                total = -2;
+                break;
+            }
+            for (int t = 0; t < m; ++t) {
+                cols[row_ptr[r] + t] = e[t].col;
+                vals[row_ptr[r] + t] = e[t].val;
+            }
+        }
+        total += m;
+    }
+    free(e);
+    free(tx);
+    free(ty);
+    return total;
+}
+
 /* Direction cosines of every kept angle (for tests of the angle reading). */
 void oracle_directions(int n_total, int keep_every, double *cs, double *sn)
 {

@@ -160,7 +160,6 @@ struct OutMap {
     int n, tn;
 };
 
-// Y[row][b] = scale * sum_k val_k X[col_k][b].
 // Stages up to W entries of each sub-group's row (j0 .. j0 + W - 1) in the
 // warp's shared buffer: lane (g, t) loads entry j0 + t of its sub-group's row.
 template <typename VT>
@@ -175,27 +174,28 @@ __device__ __forceinline__ void stage_entries(const ColMap& cm, const VT* __rest
     *stage = e;
 }
 
-// acc += sum over the cnt staged entries of val * X[col][b].
-template <typename XT>
+// acc += sum over the cnt staged entries of val * X[col][b], U entries per
+// step (U gathers in flight); every U gives the same bits.
+template <typename XT, int U>
 __device__ __forceinline__ void staged_dot(const int2* st, int cnt, const XT* __restrict__ x, int B, int b,
                                            float& hs, float& hc)
 {
     int t = 0;
-    for (; t + 8 <= cnt; t += 8) {
-        int2 e[8];
-        float2 xv[8];
+    for (; t + U <= cnt; t += U) {
+        int2 e[U];
+        float2 xv[U];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) e[u] = st[t + u];
+        for (int u = 0; u < U; ++u) e[u] = st[t + u];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) xv[u] = ld_x(x, (int64_t)e[u].x * B + b);
+        for (int u = 0; u < U; ++u) xv[u] = ld_x(x, (int64_t)e[u].x * B + b);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc_fma(hs, hc, __int_as_float(e[u].y), xv[u]);
+        for (int u = 0; u < U; ++u) acc_fma(hs, hc, __int_as_float(e[u].y), xv[u]);
     }
     for (; t < cnt; ++t) acc_fma(hs, hc, __int_as_float(st[t].y), ld_x(x, (int64_t)st[t].x * B + b));
 }
 
 // Y[row][b] = scale * sum_k val_k X[col_k][b].
-template <typename VT, typename XT, typename YT>
+template <typename VT, typename XT, typename YT, int U>
 __global__ void __launch_bounds__(256) spmm_df_kernel(SellView m, ColMap cm, const VT* __restrict__ val,
                                                       const XT* __restrict__ x, YT* __restrict__ y, int B,
                                                       BProd a, OutMap om)
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256) spmm_df_kernel(SellView m, ColMap cm, con
             stage_entries<VT>(cm, val, row, base, len, j0, t_in, &stage[w][lane]);
             __syncwarp();
             const int cnt = min(lm.W, len - j0);
-            if (live && cnt > 0) staged_dot<XT>(&stage[w][lm.g * lm.W], cnt, x, B, b, hs, hc);
+            if (live && cnt > 0) staged_dot<XT, U>(&stage[w][lm.g * lm.W], cnt, x, B, b, hs, hc);
             __syncwarp();
         }
         if (live && rv) {
@@ -306,7 +306,7 @@ __device__ __forceinline__ void bop_epilogue(const BOp& a, int64_t t, int i, int
 }
 
 // A^T y for every slice fused with the operator epilogue (rows = pixels).
-template <typename VT, int MODE>
+template <typename VT, int MODE, int U>
 __global__ void __launch_bounds__(256) spmm_op_kernel(SellView m, ColMap cm, const VT* __restrict__ val,
                                                       const float2* __restrict__ y, int B, BOp a)
 {
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(256) spmm_op_kernel(SellView m, ColMap cm, con
             stage_entries<VT>(cm, val, row, base, len, j0, t_in, &stage[w][lane]);
             __syncwarp();
             const int cnt = min(lm.W, len - j0);
-            if (live && cnt > 0) staged_dot<float2>(&stage[w][lm.g * lm.W], cnt, y, B, b, hs, hc);
+            if (live && cnt > 0) staged_dot<float2, U>(&stage[w][lm.g * lm.W], cnt, y, B, b, hs, hc);
             __syncwarp();
         }
         if (live && rv) {
@@ -662,10 +662,18 @@ ColMap colmap_of(const ct_matrix* M, int which)
     return ColMap{nullptr, M->At.col16, M->band_lo, M->band_off, M->band_angle, M->g.n_bins, M->n_kept};
 }
 
+// Staged-entry unroll of the batched products for batch size B: the tuned or
+// pinned choice, else 8.
+int spmm_unroll(const ct_matrix* M, int B)
+{
+    auto it = M->spmm_unroll.find(B);
+    return it != M->spmm_unroll.end() && it->second > 0 ? it->second : 8;
+}
+
 // which = 0: rows of A (rays); which = 1: rows of A^T (internal pixels).
 template <typename XT, typename YT>
 int launch_spmm(const ct_matrix* M, int which, ValKind vk, const XT* x, YT* y, int B, BProd a, cudaStream_t st,
-                bool user_out = false)
+                bool user_out = false, int unroll = 0)
 {
     const Sell& C = which == 0 ? M->A : M->At;
     const SellView m{C.slice_ptr, C.row_len, C.rows};
@@ -673,12 +681,59 @@ int launch_spmm(const ct_matrix* M, int which, ValKind vk, const XT* x, YT* y, i
     const OutMap om{user_out ? 1 : 0, M->g.n, M->tn};
     const Grid2 g = make_grid(M, C.rows, B);
     const int blocks = g.rb * g.chunks;
-    if (vk == ValKind::F16)
-        spmm_df_kernel<__half, XT, YT><<<blocks, 256, 0, st>>>(m, cm, C.qval, x, y, B, a, om);
-    else
-        spmm_df_kernel<float, XT, YT><<<blocks, 256, 0, st>>>(m, cm, C.val, x, y, B, a, om);
+    const bool u4 = (unroll ? unroll : spmm_unroll(M, B)) == 4;
+    if (vk == ValKind::F16) {
+        if (u4) spmm_df_kernel<__half, XT, YT, 4><<<blocks, 256, 0, st>>>(m, cm, C.qval, x, y, B, a, om);
+        else spmm_df_kernel<__half, XT, YT, 8><<<blocks, 256, 0, st>>>(m, cm, C.qval, x, y, B, a, om);
+    } else {
+        if (u4) spmm_df_kernel<float, XT, YT, 4><<<blocks, 256, 0, st>>>(m, cm, C.val, x, y, B, a, om);
+        else spmm_df_kernel<float, XT, YT, 8><<<blocks, 256, 0, st>>>(m, cm, C.val, x, y, B, a, om);
+    }
     CT_CUDA(cudaGetLastError());
     return CT_OK;
+}
+
+// Chooses the staged-entry unroll for batch size B on this handle by timing
+// the forward SpMM (x -> y, both workspace buffers) with each candidate; the
+// candidates give identical bits, so only speed depends on the choice.  Runs
+// once per (handle, B), never while st is being captured, and keeps a
+// pinned choice.
+int tune_spmm(ct_matrix* M, ValKind vk, int B, const float2* x, float2* y, cudaStream_t st)
+{
+    if (M->spmm_unroll.count(B)) return CT_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CT_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return CT_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CT_CUDA(cudaEventCreate(&e0));
+    const cudaError_t ec = cudaEventCreate(&e1);
+    if (ec != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ec, "cudaEventCreate", __FILE__, __LINE__);
+    }
+    BProd a{vk == ValKind::F16 ? M->row_scale : nullptr, 1, make_float2(1.0f, 0.0f), nullptr, nullptr};
+    const int cand[2] = {4, 8};
+    float best_ms = 0.0f;
+    int best = 8, rc = CT_OK;
+    for (int c = 0; c < 2 && rc == CT_OK; ++c) {
+        rc = launch_spmm(M, 0, vk, x, y, B, a, st, false, cand[c]);  // warm-up
+        cudaError_t e = cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && rc == CT_OK && e == cudaSuccess; ++r)
+            rc = launch_spmm(M, 0, vk, x, y, B, a, st, false, cand[c]);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess && rc == CT_OK) rc = cuda_fail(e, "timing the batched product", __FILE__, __LINE__);
+        if (rc == CT_OK && (c == 0 || ms < best_ms)) {
+            best_ms = ms;
+            best = cand[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == CT_OK) M->spmm_unroll[B] = best;
+    return rc;
 }
 
 // Op(in) with the epilogue of `mode`; partials land in w.partials (layout of g).
@@ -696,16 +751,25 @@ int bapply(const BPlan& P, BOp ep, const float2* in, cudaStream_t st, Grid2& g_u
         const ColMap cm = colmap_of(P.M, 1);
         g_used = P.g_rows_t;
         const int blocks = g_used.rb * g_used.chunks;
-#define CT_BOP(VT, VAL)                                                                              \
-    switch (ep.mode) {                                                                               \
-    case 1: spmm_op_kernel<VT, 1><<<blocks, 256, 0, st>>>(m, cm, VAL, w.y, P.B, ep); break;         \
-    case 2: spmm_op_kernel<VT, 2><<<blocks, 256, 0, st>>>(m, cm, VAL, w.y, P.B, ep); break;         \
-    default: spmm_op_kernel<VT, 3><<<blocks, 256, 0, st>>>(m, cm, VAL, w.y, P.B, ep); break;        \
+#define CT_BOP(VT, VAL, U)                                                                  \
+    switch (ep.mode) {                                                                      \
+    case 1: spmm_op_kernel<VT, 1, U><<<blocks, 256, 0, st>>>(m, cm, VAL, w.y, P.B, ep); break; \
+    case 2: spmm_op_kernel<VT, 2, U><<<blocks, 256, 0, st>>>(m, cm, VAL, w.y, P.B, ep); break; \
+    default: spmm_op_kernel<VT, 3, U><<<blocks, 256, 0, st>>>(m, cm, VAL, w.y, P.B, ep); break; \
     }
+        const bool u4 = spmm_unroll(P.M, P.B) == 4;
         if (vk == ValKind::F16) {
-            CT_BOP(__half, C.qval)
+            if (u4) {
+                CT_BOP(__half, C.qval, 4)
+            } else {
+                CT_BOP(__half, C.qval, 8)
+            }
         } else {
-            CT_BOP(float, C.val)
+            if (u4) {
+                CT_BOP(float, C.val, 4)
+            } else {
+                CT_BOP(float, C.val, 8)
+            }
         }
 #undef CT_BOP
     } else {
@@ -847,6 +911,7 @@ int cg_solve_batched(ct_matrix* M, const ct_cg_params* Pp, const float* rhs, flo
     bwiden_kernel<<<grid_blocks(M, len), 256, 0, st>>>(BatchIn{rhs, nullptr}, w.rhs, M->g.n, M->tn, B);
     bwiden_kernel<<<grid_blocks(M, len), 256, 0, st>>>(BatchIn{u, nullptr}, w.u, M->g.n, M->tn, B);
     CT_CUDA(cudaGetLastError());
+    if (P.sparse) CT_CHECK(tune_spmm(M, P.vk, B, w.u, w.y, st));
     CT_CHECK(benqueue_cg(P, w.rhs, Pp->max_iters, st));
     bnarrow_kernel<<<grid_blocks(M, len), 256, 0, st>>>(w.u, BatchOut{u, nullptr}, M->g.n, M->tn, B);
     CT_CUDA(cudaGetLastError());
@@ -918,6 +983,7 @@ int sb_prepare(ct_matrix* M, const ct_sb_params* Sp, BatchIn f, BatchIn u, int32
     }
     bwiden_kernel<<<grid_blocks(M, len), 256, 0, st>>>(u, w.u, M->g.n, M->tn, B);
     CT_CUDA(cudaGetLastError());
+    if (P.sparse) CT_CHECK(tune_spmm(M, P.vk, B, w.u, w.y, st));
     CT_CUDA(cudaMemsetAsync(w.bx, 0, len * sizeof(float2), st));
     CT_CUDA(cudaMemsetAsync(w.by, 0, len * sizeof(float2), st));
     CT_CUDA(cudaMemsetAsync(w.vx, 0, len * sizeof(float2), st));

@@ -273,6 +273,27 @@ int ct_split_bregman_ragged(int32_t count, const ct_matrix_t* A, const float* co
     return split_bregman_ragged(count, A, f, u, params, stats, (cudaStream_t)cuda_stream);
 }
 
+int ct_set_spmm_unroll(ct_matrix_t A, int32_t batch, int32_t unroll)
+{
+    CT_CHECK(check_handle(A));
+    if (batch < 2) return fail(CT_ERR_ARG, "batch must be >= 2 (batch 1 does not use the batched products)");
+    if (unroll != 0 && unroll != 4 && unroll != 8) return fail(CT_ERR_ARG, "unroll must be 0, 4 or 8");
+    if (unroll == 0)
+        A->spmm_unroll.erase(batch);
+    else
+        A->spmm_unroll[batch] = unroll;
+    return CT_OK;
+}
+
+int ct_get_spmm_unroll(ct_matrix_t A, int32_t batch, int32_t* unroll)
+{
+    CT_CHECK(check_handle(A));
+    if (!unroll) return fail(CT_ERR_ARG, "NULL output pointer");
+    auto it = A->spmm_unroll.find(batch);
+    *unroll = it == A->spmm_unroll.end() ? 0 : it->second;
+    return CT_OK;
+}
+
 int ct_matrix_export(ct_matrix_t A, int32_t which, int64_t* row_ptr, int32_t* cols, float* vals)
 {
     CT_CHECK(check_handle(A));

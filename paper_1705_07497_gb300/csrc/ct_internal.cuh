@@ -150,6 +150,7 @@ struct ct_matrix {
     ct::Sell A, At;
     float* row_scale = nullptr;  // FP16 form: s [rows]
     std::map<std::pair<int, int>, ct::Stencil> stencils;
+    std::map<int, int> spmm_unroll;  // batch size -> staged-entry unroll of the batched products (tuned or pinned)
     ct::Workspace ws;
 };
 

@@ -72,7 +72,7 @@ __device__ __forceinline__ int64_t f64_row(const F64Map& fm, int64_t row)
 }
 
 // B = 1: one lane per row (a warp per SELL slice, the lane's row entries in
-// order).  B > 1: one warp per (row, 32-slice chunk), lane = slice.
+// order).  B > 1: see below.
 template <typename VT>
 __global__ void __launch_bounds__(256) f64_kernel(SellView m, F64Map fm, const VT* __restrict__ val,
                                                   const double* __restrict__ x, double* __restrict__ y,
@@ -103,23 +103,44 @@ __global__ void __launch_bounds__(256) f64_kernel(SellView m, F64Map fm, const V
         }
         return;
     }
-    const int chunks = (B + 31) / 32;
-    for (int64_t task = warp; task < m.rows * chunks; task += nw) {
-        const int64_t row = task / chunks;
-        const int b = (int)(task % chunks) * 32 + lane;
-        const int64_t pos = f64_row(fm, row);
-        if (b >= B || pos < 0) continue;
-        const int64_t base = row_base(m, row);
-        const int len = m.len[row];
+    // B > 1: sub-groups of W lanes (W = the power of two >= B, at most 32),
+    // one row per sub-group and one slice per lane; the sub-group stages W
+    // entries at a time (the input index and the value in FP64, converted
+    // once) and every lane then does one gather and one FP64 FMA per entry.
+    __shared__ double sval[8][32];
+    __shared__ int64_t scol[8][32];
+    int W = 1;
+    while (W < B && W < 32) W <<= 1;
+    const int rpw = 32 / W, g = lane / W, t_in = lane % W, wib = threadIdx.x >> 5;
+    const int chunks = (B + W - 1) / W;
+    const int64_t groups = (m.rows + rpw - 1) / rpw;
+    for (int64_t task = warp; task < groups * chunks; task += nw) {
+        const int64_t row = (task / chunks) * rpw + g;
+        const int b = (int)(task % chunks) * W + t_in;
+        const bool rv = row < m.rows;
+        const int64_t pos = rv ? f64_row(fm, row) : -1;
+        const int len = (rv && pos >= 0) ? m.len[row] : 0;
+        const int64_t base = rv ? row_base(m, row) : 0;
+        const int maxlen = __reduce_max_sync(0xffffffffu, len);
         double acc = 0.0;
-        for (int e = 0; e < len; ++e) {
-            const int64_t k = chunk_pos(base, e);
-            const int64_t c = f64_col(fm, row, k);
-            double xv = __ldg(x + c * B + b);
-            if (in_scale) xv *= (double)__ldg(in_scale + c);
-            acc = fma(val64<VT>(val, k), xv, acc);
+        for (int j0 = 0; j0 < maxlen; j0 += W) {
+            if (j0 + t_in < len) {
+                const int64_t k = chunk_pos(base, j0 + t_in);
+                const int64_t c = f64_col(fm, row, k);
+                double v = val64<VT>(val, k);
+                if (in_scale) v *= (double)__ldg(in_scale + c);
+                scol[wib][lane] = c;
+                sval[wib][lane] = v;
+            }
+            __syncwarp();
+            const int cnt = min(W, len - j0);
+            if (b < B)
+                for (int t = 0; t < cnt; ++t)
+                    acc = fma(sval[wib][g * W + t], __ldg(x + scol[wib][g * W + t] * B + b), acc);
+            __syncwarp();
         }
-        y[pos * B + b] = row_scale ? acc * (double)row_scale[row] : acc;
+        if (len > 0 && b < B) y[pos * B + b] = row_scale ? acc * (double)row_scale[row] : acc;
+        else if (rv && pos >= 0 && b < B) y[pos * B + b] = 0.0;
     }
 }
 
@@ -133,7 +154,10 @@ int product_f64(const ct_matrix* M, int which, const double* in, double* out, in
     const F64Map fm{which, M->A.col, M->At.col16, M->band_lo, M->band_off, M->band_angle,
                     M->g.n, M->tn, M->g.n_bins, M->n_kept};
     const SellView m{C.slice_ptr, C.row_len, C.rows};
-    const int64_t tasks = B == 1 ? (C.rows + kSliceRows - 1) / kSliceRows : C.rows * ((B + 31) / 32);
+    int W = 1;
+    while (W < B && W < 32) W <<= 1;
+    const int64_t tasks = B == 1 ? (C.rows + kSliceRows - 1) / kSliceRows
+                                 : (C.rows + 32 / W - 1) / (32 / W) * ((B + W - 1) / W);
     const int grid = grid_for(M, tasks, 8, 8);
     if (f16)
         f64_kernel<__half><<<grid, 256, 0, st>>>(m, fm, C.qval, in, out, B, row_scale, in_scale);

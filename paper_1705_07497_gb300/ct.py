@@ -44,6 +44,8 @@ SYMBOLS = (
     "ct_cg_solve_noalloc",
     "ct_split_bregman",
     "ct_split_bregman_ragged",
+    "ct_set_spmm_unroll",
+    "ct_get_spmm_unroll",
     "ct_matrix_export",
     "ct_matrix_export_fp16",
     "ct_surrogate_stencil",
@@ -136,6 +138,8 @@ def lib():
         L.ct_cg_solve_noalloc.argtypes = [vp, P(CgParams), vp, vp, P(CgStats), vp]
         L.ct_split_bregman.argtypes = [vp, P(SbParams), vp, vp, i32, P(SbStats), vp]
         L.ct_split_bregman_ragged.argtypes = [i32, vp, vp, vp, P(SbParams), vp, vp]
+        L.ct_set_spmm_unroll.argtypes = [vp, i32, i32]
+        L.ct_get_spmm_unroll.argtypes = [vp, i32, P(i32)]
         L.ct_matrix_export.argtypes = [vp, i32, vp, vp, vp]
         L.ct_matrix_export_fp16.argtypes = [vp, vp, vp]
         L.ct_surrogate_stencil.argtypes = [vp, i32, i32, i32, vp, vp, vp, P(i32)]
@@ -359,6 +363,16 @@ class Matrix:
             return None
         return {"outer_done": st.outer_done, "first_update_l1": st.first_update_l1,
                 "last_update_l1": st.last_update_l1, "status": st.status}
+
+    def set_spmm_unroll(self, batch, unroll):
+        """Pins the batched products' staged-entry unroll (4 or 8; 0 = automatic)."""
+        _check(lib().ct_set_spmm_unroll(self.handle, batch, unroll))
+
+    def spmm_unroll(self, batch):
+        """The batched products' unroll for this batch size (0 = not chosen yet)."""
+        v = ctypes.c_int32()
+        _check(lib().ct_get_spmm_unroll(self.handle, batch, ctypes.byref(v)))
+        return v.value
 
     def export(self, which=0):
         return ct_matrix_export(self.handle, which)

@@ -84,3 +84,9 @@ def test_ragged_argument_errors(lib):
     assert lib.ct_split_bregman_ragged(1, arr, arr, arr, ctypes.byref(bad), None, None) == ct.CT_ERR_ARG
     with pytest.raises(ValueError):
         ct.ct_split_bregman_ragged([None], p, [], [])
+
+
+def test_spmm_unroll_argument_errors(lib):
+    v = ctypes.c_int32()
+    assert lib.ct_set_spmm_unroll(None, 4, 4) == ct.CT_ERR_ARG
+    assert lib.ct_get_spmm_unroll(None, 4, ctypes.byref(v)) == ct.CT_ERR_ARG

@@ -157,3 +157,15 @@ def test_quantize_rowscale_bounds():
     assert np.float16(1.0 / 3.0).view(np.uint16) == 0x3555
     assert np.float16(0.1).view(np.uint16) == 0x2E66
     assert np.float16(1.0 + 2.0 ** -11).view(np.uint16) == 0x3C00  # tie -> even
+
+
+@pytest.mark.parametrize("geom", [(16, 12, 1, 23), (33, 37, 2, 47), (64, 90, 3, 91)])
+def test_siddon_rows_equal_the_full_matrix(geom):
+    """The per-ray entry point (used at sizes too large to build whole) returns
+    exactly the rows of the full matrix."""
+    A = radon.siddon_matrix(*geom)
+    rows = np.random.Generator(np.random.PCG64(5)).choice(A.shape[0], 40, replace=False)
+    R = radon.siddon_rows(*geom, rows)
+    assert (R != A[rows]).nnz == 0
+    with pytest.raises(ValueError):
+        radon.siddon_rows(*geom, [A.shape[0]])
