@@ -1055,8 +1055,15 @@ int split_bregman_batched(ct_matrix* M, const ct_sb_params* Sp, const float* f, 
     return sb_finish(R, BatchOut{u, nullptr}, stats, false, st);
 }
 
-// Groups the problems by handle; a group of one runs the single-slice kernels,
-// larger groups the batched (SpMM) kernels through a per-slice pointer table.
+// Groups the problems by handle.  A group of at most kRaggedSingles problems
+// runs as that many single-slice runs (one workspace each: the handle's own
+// and extra ones kept with the handle), side by side in the graph: at such
+// batch sizes the single-slice kernels, each streaming the matrix at close to
+// HBM speed, beat the batched SpMM (measured: 5 problems of 1024 x 1024 with
+// 900 angles, 33 ms per CG step as one SpMM against about 16 ms for five
+// single-slice products).  Larger groups run the batched kernels through a
+// per-slice pointer table.
+constexpr int kRaggedSingles = 8;
 int split_bregman_ragged(int32_t count, ct_matrix* const* A, const float* const* f, float* const* u,
                          const ct_sb_params* Sp, ct_sb_stats* stats, cudaStream_t st)
 {
@@ -1076,17 +1083,26 @@ int split_bregman_ragged(int32_t count, ct_matrix* const* A, const float* const*
     struct Free1 {
         void operator()(Sb1Run* r) const { sb1_free(r); }
     };
-    std::vector<std::unique_ptr<Sb1Run, Free1>> runs1(G);
+    std::vector<std::vector<std::unique_ptr<Sb1Run, Free1>>> runs1(G);
     std::vector<UpdateFn> fns;
     std::vector<cudaStream_t> caps;
     for (size_t g = 0; g < G; ++g) {
         ct_matrix* M = handles[g];
         const int B = (int)members[g].size();
-        if (B == 1) {
-            Sb1Run* r = nullptr;
-            CT_CHECK(sb1_prepare(M, Sp, f[members[g][0]], u[members[g][0]], &r, st));
-            runs1[g].reset(r);
-            fns.push_back([r](cudaStream_t s) { return sb1_update(r, s); });
+        if (B <= kRaggedSingles) {
+            while ((int)M->ws_pool.size() < B - 1) {
+                std::unique_ptr<Workspace> w(new (std::nothrow) Workspace());
+                if (!w) return fail(CT_ERR_OOM, "host allocation failed");
+                M->ws_pool.push_back(std::move(w));
+            }
+            for (int b = 0; b < B; ++b) {
+                Workspace& w = b == 0 ? M->ws : *M->ws_pool[b - 1];
+                Sb1Run* r = nullptr;
+                CT_CHECK(sb1_prepare(M, w, Sp, f[members[g][b]], u[members[g][b]], &r, st));
+                runs1[g].emplace_back(r);
+                fns.push_back([r](cudaStream_t s) { return sb1_update(r, s); });
+                caps.push_back(w.cap_stream);
+            }
         } else {
             CT_CHECK(ensure_workspace(M, B, true));
             Workspace& w = M->ws;
@@ -1120,8 +1136,8 @@ int split_bregman_ragged(int32_t count, ct_matrix* const* A, const float* const*
                                 runs[g], st));
             SbRun* r = &runs[g];
             fns.push_back([r](cudaStream_t s) { return sb_update(*r, s); });
+            caps.push_back(M->ws.cap_stream);
         }
-        caps.push_back(M->ws.cap_stream);
     }
     CT_CHECK(run_updates(fns, caps, Sp->outer_iters, st));
     int status = CT_OK;
@@ -1129,12 +1145,17 @@ int split_bregman_ragged(int32_t count, ct_matrix* const* A, const float* const*
     for (size_t g = 0; g < G; ++g) {
         const int B = (int)members[g].size();
         gs.assign(B, ct_sb_stats{});
-        int rc;
-        if (B == 1)
-            rc = sb1_finish(runs1[g].get(), u[members[g][0]], stats ? gs.data() : nullptr, st);
-        else
+        int rc = CT_OK;
+        if (B <= kRaggedSingles) {
+            for (int b = 0; b < B; ++b) {
+                const int rb = sb1_finish(runs1[g][b].get(), u[members[g][b]], stats ? &gs[b] : nullptr, st);
+                if (rb != CT_OK && rc == CT_OK) rc = rb;
+                if (rb != CT_OK && rb != CT_ERR_BREAKDOWN && rb != CT_ERR_NONFINITE) return rb;
+            }
+        } else {
             rc = sb_finish(runs[g], BatchOut{nullptr, handles[g]->ws.ragged_ptrs + B}, stats ? gs.data() : nullptr,
                            true, st);
+        }
         if (rc != CT_OK && rc != CT_ERR_BREAKDOWN && rc != CT_ERR_NONFINITE) return rc;
         if (rc != CT_OK && status == CT_OK) status = rc;
         if (stats)

@@ -138,6 +138,7 @@ void ct_destroy_matrix(ct_matrix_t A)
     if (prev != A->device) cudaSetDevice(A->device);
     cudaDeviceSynchronize();
     free_workspace(A->ws);
+    for (auto& w : A->ws_pool) free_workspace(*w);
     for (auto& kv : A->stencils) free_stencil(kv.second);
     free_sell(A->A);
     free_sell(A->At);

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <functional>
 #include <map>
+#include <memory>
 #include <string>
 #include <utility>
 #include <vector>
@@ -152,6 +153,9 @@ struct ct_matrix {
     std::map<std::pair<int, int>, ct::Stencil> stencils;
     std::map<int, int> spmm_unroll;  // batch size -> staged-entry unroll of the batched products (tuned or pinned)
     ct::Workspace ws;
+    // extra single-slice workspaces: ct_split_bregman_ragged runs the
+    // problems of a small group on one handle side by side
+    std::vector<std::unique_ptr<ct::Workspace>> ws_pool;
 };
 
 namespace ct {
@@ -164,6 +168,7 @@ void free_stencil(Stencil& s);
 
 // workspace.cu (in solve.cu)
 int ensure_workspace(ct_matrix* M, int32_t batch, bool solver);
+int ensure_workspace_in(ct_matrix* M, Workspace& w, int32_t batch);
 void free_workspace(Workspace& w);
 
 // spmv.cu
@@ -239,7 +244,7 @@ int run_updates(const std::vector<UpdateFn>& fns, const std::vector<cudaStream_t
                 cudaStream_t st);
 // single-slice split Bregman in phases (solve.cu)
 struct Sb1Run;
-int sb1_prepare(ct_matrix* M, const ct_sb_params* Sp, const float* f, const float* u, Sb1Run** out,
+int sb1_prepare(ct_matrix* M, Workspace& w, const ct_sb_params* Sp, const float* f, const float* u, Sb1Run** out,
                 cudaStream_t st);
 int sb1_update(Sb1Run* r, cudaStream_t s);
 int sb1_finish(Sb1Run* r, float* u, ct_sb_stats* stats, cudaStream_t st);

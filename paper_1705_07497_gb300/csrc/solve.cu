@@ -254,9 +254,10 @@ void free_workspace(Workspace& w)
     w = Workspace{};
 }
 
-int ensure_workspace(ct_matrix* M, int32_t batch, bool /*solver*/)
+int ensure_workspace(ct_matrix* M, int32_t batch, bool /*solver*/) { return ensure_workspace_in(M, M->ws, batch); }
+
+int ensure_workspace_in(ct_matrix* M, Workspace& w, int32_t batch)
 {
-    Workspace& w = M->ws;
     if (w.batch >= batch && w.r) return CT_OK;
     CT_CUDA(cudaDeviceSynchronize());
     cudaStream_t keep = w.cap_stream;
@@ -365,7 +366,7 @@ struct Sb1Run {
 
 void sb1_free(Sb1Run* r) { delete r; }
 
-int sb1_prepare(ct_matrix* M, const ct_sb_params* Sp, const float* f, const float* u, Sb1Run** out,
+int sb1_prepare(ct_matrix* M, Workspace& w, const ct_sb_params* Sp, const float* f, const float* u, Sb1Run** out,
                 cudaStream_t st)
 {
     *out = nullptr;
@@ -374,8 +375,7 @@ int sb1_prepare(ct_matrix* M, const ct_sb_params* Sp, const float* f, const floa
     if (!R) return fail(CT_ERR_OOM, "host allocation failed");
     R->M = M;
     R->Sp = Sp;
-    CT_CHECK(ensure_workspace(M, batch, true));
-    Workspace& w = M->ws;
+    CT_CHECK(ensure_workspace_in(M, w, batch));
     Plan& P = R->P;
     CT_CHECK(make_plan(M, &w, 0.0, Sp->alpha, Sp->lambda, 0.0, Sp->surrogate_r, Sp->surrogate_square,
                        Sp->refresh_every, P));
@@ -409,7 +409,7 @@ int sb1_update(Sb1Run* r, cudaStream_t s) { return enqueue_sb_outer(r->P, r->Sp,
 int sb1_finish(Sb1Run* r, float* u, ct_sb_stats* stats, cudaStream_t st)
 {
     ct_matrix* M = r->M;
-    Workspace& w = M->ws;
+    Workspace& w = *r->P.w;
     const int gv = grid_for(M, r->P.n2, 256, 8);
     narrow_kernel<<<gv, 256, 0, st>>>(w.u, u, M->g.n, M->tn);
     CT_CUDA(cudaGetLastError());
@@ -493,7 +493,7 @@ int split_bregman(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u
         return fail(CT_ERR_ARG, "split Bregman needs lambda > 0 and non-negative iteration counts");
     if (batch != 1) return split_bregman_batched(M, Sp, f, u, batch, stats, st);
     Sb1Run* r = nullptr;
-    CT_CHECK(sb1_prepare(M, Sp, f, u, &r, st));
+    CT_CHECK(sb1_prepare(M, M->ws, Sp, f, u, &r, st));
     std::unique_ptr<Sb1Run> hold(r);
     CT_CHECK(run_updates({[r](cudaStream_t s) { return sb1_update(r, s); }}, {M->ws.cap_stream}, Sp->outer_iters,
                          st));

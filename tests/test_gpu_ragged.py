@@ -107,3 +107,18 @@ def test_ragged_rejects_host_pointers(dev):
         ct.split_bregman_ragged([M], [f.astype(np.float32)], [np.zeros(g[0] * g[0], np.float32)],
                                 1.0, 1.0, 3, 3)
     assert e.value.code == ct.CT_ERR_ARG
+
+
+def test_ragged_large_group_uses_the_batched_products(dev):
+    """Ten problems on one handle (above the single-run limit of eight: the
+    batched SpMM path) beside two problems on another handle."""
+    probs = _problems([0] * 10 + [1, 1], 4400)
+    mats = [gpu_A(g) for g, _ in probs]
+    fs = [torch.tensor(f, dtype=torch.float32, device=dev) for _, f in probs]
+    us = [torch.zeros(g[0] * g[0], dtype=torch.float32, device=dev) for g, _ in probs]
+    stats = ct.split_bregman_ragged(mats, fs, us, 1.0, 0.5, 5, 8)
+    for k, (geom, f) in enumerate(probs):
+        n = geom[0]
+        want = tv.split_bregman(oracle_A(*geom), f, (n, n), 1.0, 0.5, 5, 8)
+        assert rel(us[k].cpu().numpy(), want["u"].ravel()) <= 1e-4, k
+        assert stats[k]["outer_done"] == 5
