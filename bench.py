@@ -438,7 +438,10 @@ def bench_batch(args):
         U.zero_()
         M.split_bregman(F, U, wl["alpha"], wl["lam"], wl["outer"], wl["inner"], stats=False)
 
-    for _ in range(args.warmup):
+    U.zero_()
+    st = M.split_bregman(F, U, wl["alpha"], wl["lam"], wl["outer"], wl["inner"])
+    assert st["status"] == 0 and st["outer_done"] == wl["outer"], st
+    for _ in range(args.warmup - 1):
         step()
     torch.cuda.synchronize()
     sampler = ClockSampler(0)
@@ -625,6 +628,99 @@ def bench_grad(args):
     M.close()
 
 
+def bench_cp(args):
+    """Chambolle-Pock workload: one step = one primal-dual reconstruction of
+    the slice through ct_chambolle_pock (A, A^T and the data resident)."""
+    import torch
+
+    from paper_1705_07497_gb300 import ct
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = inputs.WORKLOADS[args.workload]
+    n = wl["n"]
+    M = ct.Matrix(n, wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
+    truth, f_host = make_data(wl, M, dev, wl["seed"])
+    f = torch.tensor(f_host, dtype=torch.float32, device=dev)
+    u = torch.zeros(n * n, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    prm = (wl["alpha"], wl["tau"], wl["sigma"], wl["outer"], wl["inner"])
+
+    def step():
+        u.zero_()
+        M.chambolle_pock(f, u, *prm, theta=wl["theta"], stats=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed_steps")
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    secs = e0.elapsed_time(e1) / 1e3
+    f_pin = torch.tensor(f_host, dtype=torch.float32).pin_memory()
+    u_pin = torch.zeros(n * n, dtype=torch.float32).pin_memory()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u_pin.zero_()
+        M.chambolle_pock(f_pin, u_pin, *prm, theta=wl["theta"], stats=False)
+    e2e_secs = time.perf_counter() - t0
+    out = {
+        "metric": METRIC,
+        "value": round(args.steps / secs, 4),
+        "unit": "slices/s",
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1e3 * secs / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic: seeded random-ellipse phantom, projected by A, 1% Gaussian noise",
+        "config": {
+            "workload": args.workload + ": %dx%d slice, %d of %d angles, %d bins, Chambolle-Pock %d updates x %d CG "
+                        "(tau = sigma = %g, theta = %g, alpha = %g)"
+                        % (n, n, M.rows // wl["n_bins"], wl["n_angles_total"], wl["n_bins"], wl["outer"],
+                           wl["inner"], wl["tau"], wl["theta"], wl["alpha"]),
+            "l2": "inputs larger than L2",
+        },
+        "e2e": {"value": round(args.steps / e2e_secs, 4), "unit": "slices/s",
+                "h2d_bytes_per_step": int(f_pin.numel() * 4 + u_pin.numel() * 4),
+                "d2h_bytes_per_step": int(u_pin.numel() * 4)},
+        "gpu_launches": None,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        # the oracle on the first two updates, timed, and the GPU against it
+        from oracle import radon, tv
+
+        A = radon.siddon_matrix(n, wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
+        t0 = time.perf_counter()
+        ref = tv.chambolle_pock(A, f_host, (n, n), wl["alpha"], wl["tau"], wl["sigma"], 2, wl["inner"],
+                                theta=wl["theta"])
+        secs_cpu = time.perf_counter() - t0
+        u2 = torch.zeros(n * n, dtype=torch.float32, device=dev)
+        M.chambolle_pock(f, u2, wl["alpha"], wl["tau"], wl["sigma"], 2, wl["inner"], theta=wl["theta"])
+        got = u2.cpu().double().numpy()
+        out["parity"] = {"after_2_updates": float(np.linalg.norm(got - ref["u"].ravel()) /
+                                                   np.linalg.norm(ref["u"].ravel()))}
+        out["cpu_baseline"] = {"value": round(2 / wl["outer"] / secs_cpu, 6), "unit": "slices/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": "2 of %d updates, FP64 numpy/scipy (sparse products and element-wise "
+                                         "work, single-threaded); %.1f s" % (wl["outer"], secs_cpu)}
+    print(json.dumps(out))
+    M.close()
+
+
 def bench_ragged(args):
     """Ragged workload: one step = every problem reconstructed by one
     ct_split_bregman_ragged call (matrices resident, one per geometry)."""
@@ -655,12 +751,16 @@ def bench_ragged(args):
         us.append(torch.zeros(n * n, dtype=torch.float32, device=dev))
     stream = torch.cuda.current_stream(dev)
 
-    def step():
+    def step(stats=False):
         for u in us:
             u.zero_()
-        ct.split_bregman_ragged(Ms, fs, us, wl["alpha"], wl["lam"], wl["outer"], wl["inner"], stats=False)
+        return ct.split_bregman_ragged(Ms, fs, us, wl["alpha"], wl["lam"], wl["outer"], wl["inner"], stats=stats)
 
-    for _ in range(args.warmup):
+    # the first warm-up step checks every problem's status
+    sts = step(stats=True)
+    bad = [i for i, st in enumerate(sts) if st["status"] != 0 or st["outer_done"] != wl["outer"]]
+    assert not bad, ("problems that did not complete", bad)
+    for _ in range(args.warmup - 1):
         step()
     torch.cuda.synchronize()
     sampler = ClockSampler(0)
@@ -843,6 +943,8 @@ def main():
         bench_ragged(args)
     elif args.workload.startswith("grad_"):
         bench_grad(args)
+    elif wl.get("solver") == "cp":
+        bench_cp(args)
     elif wl.get("batch", 1) > 1:
         bench_batch(args)
     else:

@@ -89,8 +89,8 @@ typedef struct ct_matrix *ct_matrix_t; /* opaque, library-owned, device-resident
  * are computed from the same closed-form chord length, so A^T holds exactly
  * the values of A; ct_matrix_export returns plain CSR.
  * Errors: CT_ERR_ARG (n <= 0, n*n >= 2^31, counts <= 0, NULL out),
- * CT_ERR_UNSUPPORTED (a tile's band of kept angles does not fit shared
- * memory: about 1000 kept angles on this device), CT_ERR_OOM, CT_ERR_CUDA.
+ * CT_ERR_UNSUPPORTED (more band slots per image tile than 16-bit indices
+ * address: about 3000 kept angles), CT_ERR_OOM, CT_ERR_CUDA.
  * *out receives the handle (NULL on failure). */
 int ct_build_matrix(const ct_geometry *g, uint32_t flags, ct_matrix_t *out);
 
@@ -174,6 +174,31 @@ typedef struct {
  * stats may be NULL (then the call does not synchronise). */
 int ct_split_bregman(ct_matrix_t A, const ct_sb_params *params, const float *f, float *u,
                      int32_t batch, ct_sb_stats *stats, void *cuda_stream);
+
+/* Chambolle-Pock primal-dual method (the method Sec. 2 cites; Chambolle and
+ * Pock 2011, Algorithm 1) for min alpha/2 ||A u - g||^2 + ||grad u||_1 (Eq.
+ * objmin with p = 1, K = grad, anisotropic TV):
+ *   p    = clip(p + sigma grad ubar, -1, 1)                   (dual, per component)
+ *   u    = (I + tau alpha A^T A)^{-1} (u - tau grad^T p + tau alpha A^T g)
+ *                                   (Eq. PD_resolve, inner_cg_iters CG steps from u)
+ *   ubar = u + theta (u - u_old)
+ * with ubar = u (the initial guess) and p = 0 at the start.  Converges for
+ * sigma tau ||grad||^2 < 1, ||grad||^2 <= 8.  g: [rows] measured data; u:
+ * [N*N] in = initial guess, out = reconstruction.  batch must be 1.  stats
+ * (NULL or one entry): updates done and the L1 size of the first and last
+ * update; the call then synchronises.  Errors: CT_ERR_ARG (tau, sigma <= 0,
+ * alpha < 0, theta outside [0, 1], negative counts), CT_ERR_UNSUPPORTED
+ * (batch != 1), CT_ERR_BREAKDOWN / CT_ERR_NONFINITE from a resolvent solve. */
+typedef struct {
+    double alpha;           /* data weight                                     */
+    double tau, sigma;      /* primal and dual step sizes                      */
+    double theta;           /* extrapolation, 1 in Algorithm 1                 */
+    int32_t outer_iters;    /* primal-dual updates                             */
+    int32_t inner_cg_iters; /* CG steps per resolvent                          */
+} ct_cp_params;
+
+int ct_chambolle_pock(ct_matrix_t A, const ct_cp_params *params, const float *g, float *u, int32_t batch,
+                      ct_sb_stats *stats, void *cuda_stream);
 
 /* Ragged batch: `count` independent split-Bregman problems of possibly
  * different geometries in one call (Sec. 4's reconstruction, many slices and

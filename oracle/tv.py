@@ -214,6 +214,37 @@ def resolvent(A, shape, tau, alpha, u_tilde, g, iters, u0=None):
     return cg(op, rhs, start, iters)
 
 
+def chambolle_pock(A, g, shape, alpha, tau, sigma, outer, inner, theta=1.0, u0=None):
+    """Primal-dual method of Chambolle and Pock (cited in Sec. 2; their 2011
+    paper, Algorithm 1) for min_u alpha/2 ||A u - g||^2 + ||grad u||_1
+    (anisotropic TV).  With K = grad, F the l1 norm (F* the indicator of the
+    box |p_x|, |p_y| <= 1, whose prox is the projection) and G the data term,
+    whose prox is the resolvent of Eq. PD_resolve solved by `inner` CG steps
+    warm-started at the previous iterate:
+        p^{k+1}    = clip(p^k + sigma grad(ubar^k), -1, 1)
+        u^{k+1}    = (I + tau alpha A^T A)^{-1} (u^k - tau grad^T p^{k+1} + tau alpha A^T g)
+        ubar^{k+1} = u^{k+1} + theta (u^{k+1} - u^k)
+    with u^0 = ubar^0 = u0 (else 0) and p^0 = 0; converges for
+    sigma tau ||grad||^2 < 1 (||grad||^2 <= 8 here).  Returns u, the dual
+    (px, py), the L1 size of every update and the number of updates."""
+    ny, nx = shape
+    u = np.zeros(ny * nx) if u0 is None else np.array(u0, dtype=np.float64).ravel().copy()
+    ubar = u.copy()
+    px = np.zeros(shape)
+    py = np.zeros(shape)
+    updates = []
+    for _ in range(outer):
+        gx, gy = grad(ubar.reshape(shape))
+        px = np.clip(px + sigma * gx, -1.0, 1.0)
+        py = np.clip(py + sigma * gy, -1.0, 1.0)
+        ut = u - tau * grad_adj(px, py).ravel()
+        u_new, _ = resolvent(A, shape, tau, alpha, ut, g, inner, u0=u)
+        updates.append(float(np.abs(u_new - u).sum()))
+        ubar = u_new + theta * (u_new - u)
+        u = u_new
+    return {"u": u.reshape(shape), "px": px, "py": py, "updates": updates, "outer_done": outer}
+
+
 # --------------------------------------------------------------------------
 # Sparse surrogate T, Sec. 3.2 (Eq. def_sparse_surr)
 # --------------------------------------------------------------------------

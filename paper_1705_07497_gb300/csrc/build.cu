@@ -15,6 +15,7 @@
 // (rows = pixels, ray index ascending), so neither needs a transpose or
 // atomics; both evaluate the same function with the same operation order, so
 // A^T holds bit-identical values.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -400,17 +401,22 @@ int build_matrices(ct_matrix* M)
     if (M->band_total > 65536)
         return fail(CT_ERR_UNSUPPORTED, "too many kept angles for 16-bit band indices (" +
                                              std::to_string(M->band_total) + " band slots > 65536)");
-    {
-        // the adjoint stages one tile's band (double-float values and the
-        // band starts) in shared memory, beside 4 KB of fixed buffers
-        int smem_max = 0;
-        CT_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, M->device));
-        const size_t need = ((size_t)M->band_total * 8 + 15) / 16 * 16 + (size_t)nk * 4 + 4096;
-        if (need > (size_t)smem_max)
-            return fail(CT_ERR_UNSUPPORTED, std::to_string(nk) + " kept angles need " + std::to_string(need) +
-                                                " bytes of shared memory per tile band; the device allows " +
-                                                std::to_string(smem_max));
+    // Angle chunks of the band: the adjoint stages one chunk of a tile's band
+    // at a time in shared memory, so chunks stay within kBandChunkSlots slots
+    // (at 180 angles the whole band is one chunk).
+    M->h_band_chunk.assign(1, 0);
+    for (int k = 0; k < nk; ++k) {
+        const int start = M->h_band_chunk.back();
+        if (M->h_band_off[k + 1] - M->h_band_off[start] > kBandChunkSlots) M->h_band_chunk.push_back(k);
     }
+    M->h_band_chunk.push_back(nk);
+    M->band_chunk_slots = 0;
+    for (size_t j = 0; j + 1 < M->h_band_chunk.size(); ++j)
+        M->band_chunk_slots = std::max(M->band_chunk_slots,
+                                       M->h_band_off[M->h_band_chunk[j + 1]] - M->h_band_off[M->h_band_chunk[j]]);
+    CT_CHECK(alloc_dev((void**)&M->band_chunk, M->h_band_chunk.size() * sizeof(int32_t)));
+    CT_CUDA(cudaMemcpy(M->band_chunk, M->h_band_chunk.data(), M->h_band_chunk.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice));
     M->h_band_angle.resize(M->band_total);
     for (int k = 0; k < nk; ++k)
         for (int c = M->h_band_off[k]; c < M->h_band_off[k + 1]; ++c) M->h_band_angle[c] = (uint16_t)k;

@@ -146,6 +146,7 @@ void ct_destroy_matrix(ct_matrix_t A)
     cudaFree(A->dirs);
     cudaFree(A->band_lo);
     cudaFree(A->band_off);
+    cudaFree(A->band_chunk);
     cudaFree(A->band_angle);
     if (prev >= 0 && prev != A->device) cudaSetDevice(prev);
     delete A;
@@ -251,6 +252,29 @@ int ct_split_bregman(ct_matrix_t A, const ct_sb_params* params, const float* f, 
     CT_CUDA(cudaMemcpyAsync(w.stage_b, f, ny * sizeof(float), cudaMemcpyHostToDevice, st));
     CT_CUDA(cudaMemcpyAsync(w.stage_a, u, nx * sizeof(float), cudaMemcpyHostToDevice, st));
     int rc = split_bregman(A, params, w.stage_b, w.stage_a, batch, stats, st);
+    if (rc != CT_OK && rc != CT_ERR_BREAKDOWN && rc != CT_ERR_NONFINITE) return rc;
+    CT_CUDA(cudaMemcpyAsync(u, w.stage_a, nx * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CT_CUDA(cudaStreamSynchronize(st));
+    return rc;
+}
+
+int ct_chambolle_pock(ct_matrix_t A, const ct_cp_params* params, const float* g, float* u, int32_t batch,
+                      ct_sb_stats* stats, void* cuda_stream)
+{
+    CT_CHECK(check_handle(A));
+    if (!params) return fail(CT_ERR_ARG, "NULL params");
+    if (batch < 1) return fail(CT_ERR_ARG, "batch must be >= 1");
+    int host = 0;
+    CT_CHECK(classify(g, u, &host));
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (!host) return chambolle_pock(A, params, g, u, batch, stats, st);
+    Workspace& w = A->ws;
+    const int64_t nx = A->cols * batch, ny = A->rows * batch;
+    CT_CHECK(ensure_stage(&w.stage_a, &w.stage_a_len, nx));
+    CT_CHECK(ensure_stage(&w.stage_b, &w.stage_b_len, ny));
+    CT_CUDA(cudaMemcpyAsync(w.stage_b, g, ny * sizeof(float), cudaMemcpyHostToDevice, st));
+    CT_CUDA(cudaMemcpyAsync(w.stage_a, u, nx * sizeof(float), cudaMemcpyHostToDevice, st));
+    int rc = chambolle_pock(A, params, w.stage_b, w.stage_a, batch, stats, st);
     if (rc != CT_OK && rc != CT_ERR_BREAKDOWN && rc != CT_ERR_NONFINITE) return rc;
     CT_CUDA(cudaMemcpyAsync(u, w.stage_a, nx * sizeof(float), cudaMemcpyDeviceToHost, st));
     CT_CUDA(cudaStreamSynchronize(st));

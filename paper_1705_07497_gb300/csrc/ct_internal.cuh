@@ -144,7 +144,9 @@ struct ct_matrix {
     int32_t* band_off = nullptr; // device [n_kept+1]: offset of each angle's slots in a band
     uint16_t* band_angle = nullptr;  // device [band_total]: kept angle of each band slot
     int band_total = 0;          // slots of one tile's band (sum of the angles' widths)
-    std::vector<int32_t> h_band_lo, h_band_off;
+    int32_t* band_chunk = nullptr;  // device [nchunks+1]: first kept angle of each staged band chunk
+    int band_chunk_slots = 0;       // slots of the largest chunk
+    std::vector<int32_t> h_band_lo, h_band_off, h_band_chunk;
     std::vector<uint16_t> h_band_angle;
     double* dirs = nullptr;  // device [n_kept][2]: cos, sin
     std::vector<double> h_cos, h_sin;
@@ -249,6 +251,8 @@ int sb1_prepare(ct_matrix* M, Workspace& w, const ct_sb_params* Sp, const float*
 int sb1_update(Sb1Run* r, cudaStream_t s);
 int sb1_finish(Sb1Run* r, float* u, ct_sb_stats* stats, cudaStream_t st);
 void sb1_free(Sb1Run* r);
+int chambolle_pock(ct_matrix* M, const ct_cp_params* Cp, const float* g, float* u, int32_t batch,
+                   ct_sb_stats* stats, cudaStream_t st);
 int split_bregman_ragged(int32_t count, ct_matrix* const* A, const float* const* f, float* const* u,
                          const ct_sb_params* Sp, ct_sb_stats* stats, cudaStream_t st);
 int split_bregman_batched(ct_matrix* M, const ct_sb_params* P, const float* f, float* u, int32_t B,

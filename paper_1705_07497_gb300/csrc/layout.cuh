@@ -24,6 +24,7 @@ namespace ct {
 constexpr int kTile = 16;        // pixels per tile side
 constexpr int kTilePix = 256;    // pixels per tile
 constexpr int kBandMax = 32;     // bound on the bins of one (tile, angle) band (<= 24 are used)
+constexpr int kBandChunkSlots = 3968;  // slots of a staged band chunk (31 KB in double-float)
 
 __host__ __device__ inline int tiles_per_side(int n) { return (n + kTile - 1) / kTile; }
 

@@ -8,6 +8,7 @@
 // array's name as a device address (on the host it names a stand-in object),
 // so the first call on each device asks the runtime for the device address
 // with cudaGetSymbolAddress, with that device current, and caches it.
+#include <algorithm>
 #include <mutex>
 
 #include "ct_internal.cuh"
@@ -48,7 +49,9 @@ Layout layout_for(const ct_matrix* M)
 {
     Layout L;
     const size_t n2 = (size_t)M->npad, rows = (size_t)M->rows;
-    const size_t nparts = (size_t)4 * (M->sm_count > 0 ? M->sm_count : 148) * 8;
+    // two partials per block of the widest reduction (the fused adjoint: one block per tile)
+    const size_t nparts = std::max((size_t)4 * (M->sm_count > 0 ? M->sm_count : 148) * 8,
+                                   (size_t)2 * M->tn * M->tn);
     L.vec = round256(n2 * sizeof(float2));
     L.y = round256(rows * sizeof(float2));
     L.partials = round256(nparts * sizeof(float2));

@@ -10,6 +10,7 @@
 // amplifies their rounding by orders of magnitude, see solver_ops.cu); each
 // reduction is finished by the last block of its kernel in a fixed order, so
 // results are bitwise reproducible run to run.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -18,6 +19,7 @@
 
 #include "ct_internal.cuh"
 #include "dfloat.cuh"
+#include "grad.cuh"
 #include "reduce.cuh"
 
 namespace ct {
@@ -103,6 +105,91 @@ __global__ void __launch_bounds__(256) sb_shrink_kernel(const float2* __restrict
             sb->stopped = 1;
         } else {
             sb_after_update(*sb, tot[0], tol);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Chambolle-Pock primal-dual steps around the resolvent of Eq. PD_resolve
+// (Sec. 2), for alpha/2 ||A u - g||^2 + ||grad u||_1: the dual ascent and
+// projection onto the box |p| <= 1, the resolvent's right-hand side, and the
+// extrapolation with the size of the update.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 clip_unit(float2 x)
+{
+    const float2 one = make_float2(1.0f, 0.0f), mone = make_float2(-1.0f, 0.0f);
+    if (df_gt(x, one)) return one;
+    if (df_gt(mone, x)) return mone;
+    return x;
+}
+
+// p = clip(p + sigma grad(ubar), -1, 1), per component.
+__global__ void __launch_bounds__(256) cp_dual_kernel(const float2* __restrict__ ubar, float2* __restrict__ px,
+                                                      float2* __restrict__ py, int n, int tn, float2 sigma,
+                                                      const SbSlice* sb)
+{
+    if (sb->stopped) return;
+    const int64_t npad = padded_pixels(n);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npad;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int i, j;
+        tiled_coords(p, tn, i, j);
+        if (i >= n || j >= n) continue;
+        const float2 c = ubar[p];
+        const float2 gx = (j < n - 1) ? df_sub(ubar[tiled_index(i, j + 1, tn)], c) : df_zero();
+        const float2 gy = (i < n - 1) ? df_sub(ubar[tiled_index(i + 1, j, tn)], c) : df_zero();
+        px[p] = clip_unit(df_add(px[p], df_mul(sigma, gx)));
+        py[p] = clip_unit(df_add(py[p], df_mul(sigma, gy)));
+    }
+}
+
+// rhs = u - tau grad^T p + tau alpha A^T g (Eq. PD_resolve with u~ = u - tau grad^T p);
+// u_old = u.
+__global__ void __launch_bounds__(256) cp_rhs_kernel(const float2* __restrict__ u, const float2* __restrict__ px,
+                                                     const float2* __restrict__ py, const float2* __restrict__ atf,
+                                                     float2* __restrict__ rhs, float2* __restrict__ u_old, int n,
+                                                     int tn, float2 ntau, const SbSlice* sb)
+{
+    if (sb->stopped) return;
+    const int64_t npad = padded_pixels(n);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npad;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int i, j;
+        tiled_coords(p, tn, i, j);
+        if (i >= n || j >= n) continue;
+        const float2 c = u[p];
+        rhs[p] = df_add(df_add(c, atf[p]), df_mul(ntau, grad_adj_df(px, py, p, i, j, n, tn)));
+        u_old[p] = c;
+    }
+}
+
+// ubar = u + theta (u - u_old); the L1 size of the update ends in the
+// slice's update bookkeeping (the last block).
+__global__ void __launch_bounds__(256) cp_extrap_kernel(const float2* __restrict__ u,
+                                                        const float2* __restrict__ u_old, float2* __restrict__ ubar,
+                                                        int n, int tn, float2 theta, SbSlice* sb, const CgSlice* cg,
+                                                        float2* partials, unsigned* counter)
+{
+    if (sb->stopped) return;
+    const int64_t npad = padded_pixels(n);
+    float s = 0.0f, cc = 0.0f;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npad;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int i, j;
+        tiled_coords(p, tn, i, j);
+        if (i >= n || j >= n) continue;
+        const float2 d = df_sub(u[p], u_old[p]);
+        ubar[p] = df_add(u[p], df_mul(theta, d));
+        acc_add(s, cc, df_abs(d));
+    }
+    float2 v[1] = {acc_value(s, cc)};
+    double tot[1];
+    if (grid_reduce_last<1>(v, partials, counter, tot)) {
+        if (cg->status != CT_OK) {
+            sb->status = cg->status;
+            sb->stopped = 1;
+        } else {
+            sb_after_update(*sb, tot[0], 0.0);
         }
     }
 }
@@ -224,6 +311,8 @@ int make_plan(ct_matrix* M, Workspace* ws, double c_id, double c_ata, double c_g
     }
     P.refresh = refresh;
     Workspace& w = *ws;
+    if (w.partials_len < (int64_t)2 * M->tn * M->tn)
+        return fail(CT_ERR_CUDA, "internal: reduction partials smaller than the fused adjoint's grid needs");
     OpEpilogue& b = P.base;
     std::memset(&b, 0, sizeof(b));
     b.c_id = df_from_double(c_id);
@@ -292,7 +381,11 @@ int ensure_workspace_in(ct_matrix* M, Workspace& w, int32_t batch)
     float2** vs[] = {&w.u, &w.r, &w.p, &w.q, &w.rhs, &w.atf, &w.u_old, &w.bx, &w.by, &w.vx, &w.vy};
     for (float2** v : vs) CT_CHECK(alloc_n(v, nv));
     CT_CHECK(alloc_n(&w.y, w.rows * batch));
-    w.partials_len = (int64_t)4 * (M->sm_count > 0 ? M->sm_count : 148) * 8 * batch;
+    // grid-wide reductions write NQ <= 2 partials per block: the batched
+    // kernels run at most 8 blocks per SM per 32-slice chunk, the fused
+    // adjoint one block per image tile
+    w.partials_len = std::max((int64_t)4 * (M->sm_count > 0 ? M->sm_count : 148) * 8 * batch,
+                              (int64_t)2 * M->tn * M->tn);
     CT_CHECK(alloc_n(&w.partials, w.partials_len));
     CT_CHECK(alloc_n(&w.counter, 16));
     CT_CUDA(cudaMemset(w.counter, 0, 16 * sizeof(unsigned)));
@@ -498,6 +591,61 @@ int split_bregman(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u
     CT_CHECK(run_updates({[r](cudaStream_t s) { return sb1_update(r, s); }}, {M->ws.cap_stream}, Sp->outer_iters,
                          st));
     return sb1_finish(r, u, stats, st);
+}
+
+int chambolle_pock(ct_matrix* M, const ct_cp_params* Cp, const float* g, float* u, int32_t batch,
+                   ct_sb_stats* stats, cudaStream_t st)
+{
+    if (!(Cp->tau > 0.0) || !(Cp->sigma > 0.0) || !(Cp->alpha >= 0.0) || !(Cp->theta >= 0.0 && Cp->theta <= 1.0) ||
+        Cp->outer_iters < 0 || Cp->inner_cg_iters < 0)
+        return fail(CT_ERR_ARG, "Chambolle-Pock needs tau, sigma > 0, alpha >= 0, theta in [0, 1] and "
+                                "non-negative iteration counts");
+    if (batch != 1) return fail(CT_ERR_UNSUPPORTED, "ct_chambolle_pock solves one slice per call (batch 1)");
+    CT_CHECK(ensure_workspace(M, 1, true));
+    Workspace& w = M->ws;
+    Plan P;
+    const double ta = Cp->tau * Cp->alpha;
+    CT_CHECK(make_plan(M, &w, 1.0, ta, 0.0, 0.0, 0, 0, 0, P));
+    P.base.gate = &w.sb->stopped;
+    const int64_t n2 = P.n2;
+    const int gv = grid_for(M, n2, 256, 8);
+    // tau alpha A^T g once; FP16 storage applies A^T as Q^T (s .* g)
+    CT_CHECK(launch_to_df(M, g, P.vk == ValKind::F16 ? M->row_scale : nullptr, w.y, M->rows, st));
+    CT_CHECK(launch_adjoint_df(M, P.vk, w.y, w.atf, ta, st));
+    widen_kernel<<<gv, 256, 0, st>>>(u, w.u, M->g.n, M->tn);
+    CT_CUDA(cudaGetLastError());
+    // ubar (vx) = u; dual (bx, by) = 0
+    CT_CUDA(cudaMemcpyAsync(w.vx, w.u, n2 * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    CT_CUDA(cudaMemsetAsync(w.bx, 0, n2 * sizeof(float2), st));
+    CT_CUDA(cudaMemsetAsync(w.by, 0, n2 * sizeof(float2), st));
+    CT_CUDA(cudaMemsetAsync(w.sb, 0, sizeof(SbSlice), st));
+    const float2 sigma = df_from_double(Cp->sigma), ntau = df_from_double(-Cp->tau),
+                 theta = df_from_double(Cp->theta);
+    const int n = M->g.n, tn = M->tn, inner = Cp->inner_cg_iters;
+    auto update = [&](cudaStream_t s) -> int {
+        cp_dual_kernel<<<gv, 256, 0, s>>>(w.vx, w.bx, w.by, n, tn, sigma, w.sb);
+        CT_CUDA(cudaGetLastError());
+        cp_rhs_kernel<<<gv, 256, 0, s>>>(w.u, w.bx, w.by, w.atf, w.rhs, w.u_old, n, tn, ntau, w.sb);
+        CT_CUDA(cudaGetLastError());
+        CT_CHECK(enqueue_cg(P, w.rhs, inner, s));
+        cp_extrap_kernel<<<gv, 256, 0, s>>>(w.u, w.u_old, w.vx, n, tn, theta, w.sb, w.cg, w.partials, w.counter);
+        CT_CUDA(cudaGetLastError());
+        return CT_OK;
+    };
+    CT_CHECK(run_updates({update}, {w.cap_stream}, Cp->outer_iters, st));
+    narrow_kernel<<<gv, 256, 0, st>>>(w.u, u, n, tn);
+    CT_CUDA(cudaGetLastError());
+    if (stats) {
+        SbSlice h;
+        CT_CUDA(cudaMemcpyAsync(&h, w.sb, sizeof(h), cudaMemcpyDeviceToHost, st));
+        CT_CUDA(cudaStreamSynchronize(st));
+        stats->outer_done = h.outer_done;
+        stats->first_update_l1 = h.first_upd;
+        stats->last_update_l1 = h.last_upd;
+        stats->status = h.status;
+        if (stats->status != CT_OK) return fail(stats->status, "Chambolle-Pock resolvent solve failed");
+    }
+    return CT_OK;
 }
 
 }  // namespace ct

@@ -32,6 +32,7 @@
 // on 152 SMs.
 #include "ct_internal.cuh"
 #include "dfloat.cuh"
+#include "grad.cuh"
 #include "layout.cuh"
 #include "reduce.cuh"
 #include "sparse_common.cuh"
@@ -53,6 +54,8 @@ struct BandView {
     const uint16_t* col16;
     const int32_t* band_lo;   // [tiles][nk] first bin of each band
     const int32_t* band_off;  // [nk+1] slot offsets of the angles
+    const int32_t* chunk_k;   // [nchunks+1] first kept angle of each staged band chunk
+    int nchunks;
     int slots;                // band_off[nk]
     int n, tn, nb, nk;
 };
@@ -153,18 +156,6 @@ __device__ __forceinline__ float2 lap_df(const float2* __restrict__ u, int64_t t
     return acc;
 }
 
-// (grad^T (vx, vy)) at pixel (i, j), the adjoint of the forward differences.
-__device__ __forceinline__ float2 grad_adj_df(const float2* __restrict__ vx, const float2* __restrict__ vy,
-                                              int64_t t, int i, int j, int n, int tn)
-{
-    float2 acc = df_zero();
-    if (j >= 1) acc = df_add(acc, vx[tiled_index(i, j - 1, tn)]);
-    if (j <= n - 2) acc = df_sub(acc, vx[t]);
-    if (i >= 1) acc = df_add(acc, vy[tiled_index(i - 1, j, tn)]);
-    if (i <= n - 2) acc = df_sub(acc, vy[t]);
-    return acc;
-}
-
 // Per-pixel epilogue.  MODE 1: q = Op(p), accumulate p.q.  MODE 2: r = rhs -
 // Op(u), p = r, accumulate r.r and rhs.rhs.  MODE 3: r = rhs - Op(u), r.r.
 template <int MODE>
@@ -261,9 +252,10 @@ __device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes, 
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Copies the tile's sinogram band into shared memory: every angle's W_k bins
-// (one warp per angle, one lane per bin), all copies in flight at once; bins
-// past the detector read as zero.  Ends with the block synchronised.
+// Copies the tile's whole sinogram band into shared memory: every angle's W_k
+// bins, one warp per angle and one lane per bin, all copies in flight at
+// once; bins past the detector read as zero.  Ends with the block
+// synchronised.
 template <typename YT>
 __device__ __forceinline__ void stage_band(const BandView& bv, int tile, const YT* __restrict__ y, YT* band)
 {
@@ -280,6 +272,70 @@ __device__ __forceinline__ void stage_band(const BandView& bv, int tile, const Y
     }
     cp_async_wait_all();
     __syncthreads();
+}
+
+// Copies angles [k0, k1) of the tile's sinogram band into shared memory
+// (slot off_k0 at band[0]): every angle's W_k bins, one warp per angle and one
+// lane per bin, all copies in flight at once; bins past the detector read as
+// zero.  Ends with the block synchronised.
+template <typename YT>
+__device__ __forceinline__ void stage_band_range(const BandView& bv, int tile, const YT* __restrict__ y, YT* band,
+                                                 int k0, int k1)
+{
+    const int32_t* blo = bv.band_lo + (int64_t)tile * bv.nk;
+    const int base = __ldg(bv.band_off + k0);
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int k = k0 + (threadIdx.x >> 5); k < k1; k += nwarps) {
+        const int off = __ldg(bv.band_off + k);
+        if (lane < __ldg(bv.band_off + k + 1) - off) {
+            const int b = __ldg(blo + k) + lane;
+            const bool in = b < bv.nb;
+            cp_async(band + (off - base) + lane, y + (in ? (int64_t)k * bv.nb + b : 0), (int)sizeof(YT),
+                     in ? (int)sizeof(YT) : 0);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+}
+
+// The lane's row of A^T against a band staged chunk by chunk (many angles):
+// for each angle chunk, stage it, then walk the row's 8-entry chunks from the
+// lane's position until one reaches past the chunk's slots; a chunk that
+// straddles two band chunks is walked in both, each time with the other's
+// entries masked.  Every lane of the CTA takes part in every staging.
+template <typename VT, typename YT>
+__device__ __forceinline__ float2 band_dot_chunked(const BandView& bv, const VT* __restrict__ val, int tile,
+                                                   const YT* __restrict__ y, YT* band, int64_t t)
+{
+    const int lane = threadIdx.x & 31;
+    const int len = bv.len[t];
+    const int nch = (len + kChunk - 1) / kChunk;
+    const int64_t base = bv.sp[t >> 5] + lane * kChunk;
+    float hs = 0.0f, hc = 0.0f;
+    int c = 0;
+    for (int j = 0; j < bv.nchunks; ++j) {
+        const int k0 = __ldg(bv.chunk_k + j), k1 = __ldg(bv.chunk_k + j + 1);
+        const int lo = __ldg(bv.band_off + k0), hi = __ldg(bv.band_off + k1);
+        stage_band_range(bv, tile, y, band, k0, k1);
+        while (c < nch) {
+            const int64_t p = base + (int64_t)c * kStep;
+            int cc[8];
+            float v[8];
+            load8_col(bv.col16, p, cc);
+            Vals<VT>::load8(val, p, v);
+            bool beyond = false;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const bool in = cc[u] >= lo && cc[u] < hi;
+                beyond |= cc[u] >= hi;
+                acc_fma(hs, hc, in ? v[u] : 0.0f, band_value(band, in ? cc[u] - lo : 0));
+            }
+            if (beyond) break;  // the rest of this chunk belongs to a later band chunk
+            ++c;
+        }
+        __syncthreads();  // every lane done with this band chunk before the next staging
+    }
+    return acc_value(hs, hc);
 }
 
 // Plain store of an A^T row total: OT = float2 writes the internal layout;
@@ -304,7 +360,7 @@ __device__ __forceinline__ float2 band_dot(const BandView& bv, const VT* __restr
     return acc_value(hs, hc);
 }
 
-template <typename VT, typename YT, typename OT>
+template <typename VT, typename YT, typename OT, bool CHUNKED>
 __global__ void __launch_bounds__(kAdjWarps * 32, kAdjMinBlocks)
     band_adj_kernel(BandView bv, const VT* __restrict__ val, const YT* __restrict__ y, OT* __restrict__ out,
                     float2 scale)
@@ -313,9 +369,15 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjMinBlocks)
     YT* band = reinterpret_cast<YT*>(smem);
     const int ntiles = bv.tn * bv.tn;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        stage_band(bv, tile, y, band);
         int64_t t;
-        const float2 d = band_dot<VT>(bv, val, tile, band, t);
+        float2 d;
+        if (CHUNKED) {
+            t = (int64_t)tile * kTilePix + threadIdx.x;
+            d = band_dot_chunked<VT>(bv, val, tile, y, band, t);
+        } else {
+            stage_band(bv, tile, y, band);
+            d = band_dot<VT>(bv, val, tile, band, t);
+        }
         int i, j;
         tiled_coords(t, bv.tn, i, j);
         if (i < bv.n && j < bv.n) store_pix(out, t, i, j, bv.n, df_mul(scale, d));
@@ -323,7 +385,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjMinBlocks)
     }
 }
 
-template <typename VT, int MODE>
+template <typename VT, int MODE, bool CHUNKED>
 __global__ void __launch_bounds__(kAdjWarps * 32, kAdjMinBlocks)
     band_op_kernel(BandView bv, const VT* __restrict__ val, const float2* __restrict__ y, OpEpilogue a)
 {
@@ -334,9 +396,15 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjMinBlocks)
     const int ntiles = bv.tn * bv.tn;
     float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        stage_band(bv, tile, y, band);
         int64_t t;
-        const float2 d = band_dot<VT>(bv, val, tile, band, t);
+        float2 d;
+        if (CHUNKED) {
+            t = (int64_t)tile * kTilePix + threadIdx.x;
+            d = band_dot_chunked<VT>(bv, val, tile, y, band, t);
+        } else {
+            stage_band(bv, tile, y, band);
+            d = band_dot<VT>(bv, val, tile, band, t);
+        }
         int i, j;
         tiled_coords(t, bv.tn, i, j);
         if (i < bv.n && j < bv.n) {
@@ -416,11 +484,13 @@ int launch_fwd(const ct_matrix* M, ValKind vk, const XT* x, YT* y, ProdArgs a, c
 
 BandView band_view(const ct_matrix* M)
 {
-    return BandView{M->At.slice_ptr, M->At.row_len, M->At.col16, M->band_lo, M->band_off, M->band_total,
-                    M->g.n, M->tn, M->g.n_bins, M->n_kept};
+    return BandView{M->At.slice_ptr, M->At.row_len, M->At.col16, M->band_lo, M->band_off, M->band_chunk,
+                    (int)M->h_band_chunk.size() - 1, M->band_total, M->g.n, M->tn, M->g.n_bins, M->n_kept};
 }
 
-size_t band_smem(const ct_matrix* M, size_t elem) { return band_bytes(M->band_total, elem); }
+size_t band_smem(const ct_matrix* M, size_t elem) { return band_bytes(M->band_chunk_slots, elem); }
+
+bool band_chunked(const ct_matrix* M) { return M->h_band_chunk.size() > 2; }
 
 int band_grid(const ct_matrix* M) { return M->tn * M->tn; }
 
@@ -432,12 +502,29 @@ int allow_smem(K kernel, size_t smem)
     return CT_OK;
 }
 
+template <typename VT, typename YT, typename OT, bool CHUNKED>
+int launch_band_adj_t(const ct_matrix* M, const VT* val, const YT* y, OT* out, float2 scale, cudaStream_t st)
+{
+    const size_t smem = band_smem(M, sizeof(YT));
+    CT_CHECK(allow_smem(band_adj_kernel<VT, YT, OT, CHUNKED>, smem));
+    band_adj_kernel<VT, YT, OT, CHUNKED><<<band_grid(M), kAdjWarps * 32, smem, st>>>(band_view(M), val, y, out, scale);
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
 template <typename VT, typename YT, typename OT>
 int launch_band_adj(const ct_matrix* M, const VT* val, const YT* y, OT* out, float2 scale, cudaStream_t st)
 {
-    const size_t smem = band_smem(M, sizeof(YT));
-    CT_CHECK(allow_smem(band_adj_kernel<VT, YT, OT>, smem));
-    band_adj_kernel<VT, YT, OT><<<band_grid(M), kAdjWarps * 32, smem, st>>>(band_view(M), val, y, out, scale);
+    if (band_chunked(M)) return launch_band_adj_t<VT, YT, OT, true>(M, val, y, out, scale, st);
+    return launch_band_adj_t<VT, YT, OT, false>(M, val, y, out, scale, st);
+}
+
+template <typename VT, int MODE, bool CHUNKED>
+int launch_band_op_t(const ct_matrix* M, const VT* val, const float2* y, const OpEpilogue& ep, cudaStream_t st)
+{
+    const size_t smem = band_smem(M, sizeof(float2));
+    CT_CHECK(allow_smem(band_op_kernel<VT, MODE, CHUNKED>, smem));
+    band_op_kernel<VT, MODE, CHUNKED><<<band_grid(M), kAdjWarps * 32, smem, st>>>(band_view(M), val, y, ep);
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -445,11 +532,8 @@ int launch_band_adj(const ct_matrix* M, const VT* val, const YT* y, OT* out, flo
 template <typename VT, int MODE>
 int launch_band_op(const ct_matrix* M, const VT* val, const float2* y, const OpEpilogue& ep, cudaStream_t st)
 {
-    const size_t smem = band_smem(M, sizeof(float2));
-    CT_CHECK(allow_smem(band_op_kernel<VT, MODE>, smem));
-    band_op_kernel<VT, MODE><<<band_grid(M), kAdjWarps * 32, smem, st>>>(band_view(M), val, y, ep);
-    CT_CUDA(cudaGetLastError());
-    return CT_OK;
+    if (band_chunked(M)) return launch_band_op_t<VT, MODE, true>(M, val, y, ep, st);
+    return launch_band_op_t<VT, MODE, false>(M, val, y, ep, st);
 }
 
 }  // namespace

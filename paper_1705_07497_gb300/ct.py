@@ -44,6 +44,7 @@ SYMBOLS = (
     "ct_cg_solve_noalloc",
     "ct_split_bregman",
     "ct_split_bregman_ragged",
+    "ct_chambolle_pock",
     "ct_set_spmm_unroll",
     "ct_get_spmm_unroll",
     "ct_matrix_export",
@@ -97,6 +98,17 @@ class SbParams(ctypes.Structure):
     ]
 
 
+class CpParams(ctypes.Structure):
+    _fields_ = [
+        ("alpha", ctypes.c_double),
+        ("tau", ctypes.c_double),
+        ("sigma", ctypes.c_double),
+        ("theta", ctypes.c_double),
+        ("outer_iters", ctypes.c_int32),
+        ("inner_cg_iters", ctypes.c_int32),
+    ]
+
+
 class SbStats(ctypes.Structure):
     _fields_ = [
         ("outer_done", ctypes.c_int32),
@@ -138,6 +150,7 @@ def lib():
         L.ct_cg_solve_noalloc.argtypes = [vp, P(CgParams), vp, vp, P(CgStats), vp]
         L.ct_split_bregman.argtypes = [vp, P(SbParams), vp, vp, i32, P(SbStats), vp]
         L.ct_split_bregman_ragged.argtypes = [i32, vp, vp, vp, P(SbParams), vp, vp]
+        L.ct_chambolle_pock.argtypes = [vp, P(CpParams), vp, vp, i32, P(SbStats), vp]
         L.ct_set_spmm_unroll.argtypes = [vp, i32, i32]
         L.ct_get_spmm_unroll.argtypes = [vp, i32, P(i32)]
         L.ct_matrix_export.argtypes = [vp, i32, vp, vp, vp]
@@ -247,6 +260,13 @@ def ct_split_bregman(h, params, f, u, batch, stats=None, stream=None):
     pu, _ = _vec(u)
     sp = ctypes.byref(stats) if stats is not None else None
     return _check(lib().ct_split_bregman(h, ctypes.byref(params), pf, pu, batch, sp, sf if stream is None else stream))
+
+
+def ct_chambolle_pock(h, params, g, u, batch, stats=None, stream=None):
+    pg, sg = _vec(g)
+    pu, _ = _vec(u)
+    sp = ctypes.byref(stats) if stats is not None else None
+    return _check(lib().ct_chambolle_pock(h, ctypes.byref(params), pg, pu, batch, sp, sg if stream is None else stream))
 
 
 def ct_split_bregman_ragged(handles, params, fs, us, stats=None, stream=None):
@@ -359,6 +379,16 @@ class Matrix:
         p = SbParams(alpha, lam, outer, inner, stop_rel_update, surrogate_r, refresh_every, int(square))
         st = SbStats() if stats else None
         ct_split_bregman(self.handle, p, f, u, self._batch(u, self.cols), st)
+        if st is None:
+            return None
+        return {"outer_done": st.outer_done, "first_update_l1": st.first_update_l1,
+                "last_update_l1": st.last_update_l1, "status": st.status}
+
+    def chambolle_pock(self, g, u, alpha, tau, sigma, outer, inner, theta=1.0, stats=True):
+        """Primal-dual TV reconstruction (one slice): u in = initial guess, out = result."""
+        p = CpParams(alpha, tau, sigma, theta, outer, inner)
+        st = SbStats() if stats else None
+        ct_chambolle_pock(self.handle, p, g, u, self._batch(u, self.cols), st)
         if st is None:
             return None
         return {"outer_done": st.outer_done, "first_update_l1": st.first_update_l1,

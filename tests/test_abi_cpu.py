@@ -90,3 +90,8 @@ def test_spmm_unroll_argument_errors(lib):
     v = ctypes.c_int32()
     assert lib.ct_set_spmm_unroll(None, 4, 4) == ct.CT_ERR_ARG
     assert lib.ct_get_spmm_unroll(None, 4, ctypes.byref(v)) == ct.CT_ERR_ARG
+
+
+def test_chambolle_pock_argument_errors(lib):
+    p = ct.CpParams(1.0, 0.3, 0.3, 1.0, 3, 3)
+    assert lib.ct_chambolle_pock(None, ctypes.byref(p), None, None, 1, None, None) == ct.CT_ERR_ARG

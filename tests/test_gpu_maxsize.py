@@ -1,7 +1,8 @@
 """The largest geometry the ragged workload draws: a 1024 x 1024 image, 900
 angles (all kept), 1449 bins, about 1.2e9 entries per matrix.  The oracle
 cannot build it whole, so sampled rows come from its per-ray tracer; the
-adjoint is checked through the adjoint identity, which holds at any size."""
+adjoint is checked through the adjoint identity, which holds at any size, and
+the solvers through an invariant of the first CG step."""
 
 import numpy as np
 import pytest
@@ -30,6 +31,24 @@ def sampled_rows():
     return rows, radon.siddon_rows(*GEOM, rows)
 
 
+def _solvers_run(M, dev, seed):
+    """The solvers at this size: one CG step from zero gives u = c rhs with
+    c = (r.r) / (r.Op r) > 0, and one split-Bregman update completes."""
+    rhs = torch.tensor(inputs.random_vector(M.cols, seed), dtype=torch.float32, device=dev)
+    u = torch.zeros(M.cols, device=dev)
+    st = M.cg_solve(rhs, u, 0.0, 1.0, 1.0, 1)
+    assert st["status"] == 0 and st["iters"] == 1
+    ud, rd = u.double(), rhs.double()
+    cos = float((ud * rd).sum() / (ud.norm() * rd.norm()))
+    assert cos >= 1.0 - 1e-6
+    y = torch.empty(M.rows, device=dev)
+    M.forward(torch.tensor(inputs.ellipse_phantom(M.n, seed + 1).ravel(), dtype=torch.float32, device=dev), y)
+    u.zero_()
+    sb = M.split_bregman(y, u, 1.0, 1.0, 1, 3)
+    assert sb["status"] == 0 and sb["outer_done"] == 1 and sb["first_update_l1"] > 0
+    assert torch.isfinite(u).all()
+
+
 def _rel_max(got, want):
     return float(np.abs(got - want).max() / np.abs(want).max())
 
@@ -53,6 +72,7 @@ def test_largest_geometry_fp32(dev, sampled_rows):
         lhs = float((Ax.double() * v.double()).sum())
         rhs = float((xr.double() * Atv.double()).sum())
         assert abs(lhs - rhs) <= 1e-6 * float((Ax.double().abs() * v.double().abs()).sum())
+        _solvers_run(M, dev, 53)
     finally:
         M.close()
 
@@ -67,5 +87,6 @@ def test_largest_geometry_fp16(dev, sampled_rows):
         y = torch.empty(M.rows, device=dev)
         M.forward(torch.tensor(x, dtype=torch.float32, device=dev), y)
         assert _rel_max(y.cpu().numpy()[rows], R16 @ x) <= 1e-5
+        _solvers_run(M, dev, 55)
     finally:
         M.close()

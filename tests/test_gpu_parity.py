@@ -375,3 +375,70 @@ def test_surrogate_warm_start_then_exact(dev):
     M.split_bregman(ft, u, 1.0, 0.1, 6, 10)
     got = u.cpu().double().numpy()
     assert np.linalg.norm(got - want) <= 1e-3 * np.linalg.norm(want)
+
+
+def test_many_angles_stage_the_band_in_chunks(dev):
+    """400 kept angles: a tile's band (about 8,800 slots) is staged in three
+    angle chunks by the adjoint kernels.  Products, CG and split Bregman
+    against the oracle."""
+    geom = (64, 400, 1, 91)
+    ref = oracle_A(*geom)
+    M = gpu_A(*geom)
+    x = inputs.random_vector(ref.shape[1], 61)
+    y = inputs.random_vector(ref.shape[0], 62)
+    yg = torch.empty(ref.shape[0], device=dev)
+    xg = torch.empty(ref.shape[1], device=dev)
+    M.forward(t32(x, dev), yg)
+    M.adjoint(t32(y, dev), xg)
+    assert rel(yg.cpu().numpy(), ref @ x) <= SPMV_TOL
+    assert rel(xg.cpu().numpy(), ref.T @ y) <= SPMV_TOL
+    op = tv.make_operator(ref, (64, 64), 0.0, 1.0, 0.5)
+    rhs = inputs.random_vector(ref.shape[1], 63)
+    u = torch.zeros(ref.shape[1], device=dev)
+    M.cg_solve(t32(rhs, dev), u, 0.0, 1.0, 0.5, 10)
+    want, _ = tv.cg(op, rhs, np.zeros(ref.shape[1]), 10)
+    assert rel(u.cpu().numpy(), want) <= 1e-4
+    f = ref @ inputs.ellipse_phantom(64, 64).ravel()
+    u = torch.zeros(ref.shape[1], device=dev)
+    M.split_bregman(t32(f, dev), u, 1.0, 0.5, 8, 10)
+    want = tv.split_bregman(ref, f, (64, 64), 1.0, 0.5, 8, 10)["u"].ravel()
+    assert rel(u.cpu().numpy(), want) <= 1e-3
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_chambolle_pock_matches_oracle(dev, host):
+    """Chambolle-Pock with the resolvent of Eq. PD_resolve solved by 10 CG
+    steps per update, 20 updates, against the oracle; device and host pointers."""
+    geom = (64, 90, 3, 91)
+    A = oracle_A(*geom)
+    M = gpu_A(*geom)
+    f = inputs.gaussian_noisy(A @ inputs.ellipse_phantom(64, 31).ravel(), 0.01, 32)
+    step = 0.99 / np.sqrt(8.0)
+    want = tv.chambolle_pock(A, f, (64, 64), 1.0, step, step, 20, 10)
+    if host:
+        u = np.zeros(64 * 64, dtype=np.float32)
+        st = M.chambolle_pock(f.astype(np.float32), u, 1.0, step, step, 20, 10)
+        got = u.astype(np.float64)
+    else:
+        u = torch.zeros(64 * 64, dtype=torch.float32, device=dev)
+        st = M.chambolle_pock(t32(f, dev), u, 1.0, step, step, 20, 10)
+        got = u.cpu().double().numpy()
+    assert st["status"] == 0 and st["outer_done"] == 20
+    assert rel(got, want["u"].ravel()) <= 1e-4
+    assert abs(st["first_update_l1"] - want["updates"][0]) <= 1e-4 * want["updates"][0]
+
+
+def test_chambolle_pock_warm_start_and_batch_limit(dev):
+    geom = (64, 90, 3, 91)
+    A = oracle_A(*geom)
+    M = gpu_A(*geom)
+    f = A @ inputs.ellipse_phantom(64, 33).ravel()
+    u0 = inputs.ellipse_phantom(64, 34).ravel()
+    want = tv.chambolle_pock(A, f, (64, 64), 0.5, 0.3, 0.3, 6, 8, theta=0.5, u0=u0)
+    u = t32(u0, dev)
+    M.chambolle_pock(t32(f, dev), u, 0.5, 0.3, 0.3, 6, 8, theta=0.5)
+    assert rel(u.cpu().numpy(), want["u"].ravel()) <= 1e-4
+    with pytest.raises(ct.CtError) as e:
+        M.chambolle_pock(torch.zeros((M.rows, 2), device=dev), torch.zeros((M.cols, 2), device=dev),
+                         1.0, 0.3, 0.3, 3, 3)
+    assert e.value.code == ct.CT_ERR_UNSUPPORTED

@@ -268,3 +268,39 @@ def test_complex_step_of_linear_solve_is_exact():
     u_c, _ = tv.cg(op, rhs + 1j * 1e-30 * d, np.zeros(n * n), 400, rel_tol=1e-14)
     want, _ = tv.cg(op, d, np.zeros(n * n), 400, rel_tol=1e-14)
     np.testing.assert_allclose(np.imag(u_c) / 1e-30, want, rtol=0, atol=1e-8 * np.abs(want).max())
+
+
+def test_chambolle_pock_reaches_the_split_bregman_minimiser_with_a_kkt_certificate():
+    """Chambolle-Pock (dual projection, resolvent of Eq. PD_resolve, theta = 1)
+    and split Bregman are different algorithms for the same objective
+    alpha/2 ||A u - f||^2 + ||grad u||_1: both limits must coincide, and CP's
+    dual p must certify optimality (|p| <= 1, p = sign(grad u) where
+    grad u != 0, alpha A^T (A u - f) + grad^T p = 0)."""
+    n, alpha, lam = 8, 0.3, 2.0
+    A = radon.siddon_matrix(n, 12, 1, inputs.n_bins_for(n))
+    truth = inputs.ellipse_phantom(n, 3)
+    f = A @ truth.ravel() + 0.3 * inputs.standard_normal(A.shape[0], 4)
+    sb = tv.split_bregman(A, f, (n, n), alpha, lam, outer=1500, inner=300, cg_tol=1e-14)
+    step = 0.99 / np.sqrt(8.0)
+    cp = tv.chambolle_pock(A, f, (n, n), alpha, step, step, outer=2000, inner=100)
+    u = cp["u"]
+    assert np.linalg.norm(u - sb["u"]) <= 1e-8 * np.linalg.norm(sb["u"])
+    px, py = cp["px"], cp["py"]
+    assert max(np.abs(px).max(), np.abs(py).max()) <= 1.0
+    gx, gy = tv.grad(u)
+    for g, p in ((gx, px), (gy, py)):
+        nz = np.abs(g) > 1e-7
+        assert nz.any()
+        np.testing.assert_allclose(p[nz], np.sign(g[nz]), atol=1e-6)
+    stat = alpha * (A.T @ (A @ u.ravel() - f)) + tv.grad_adj(px, py).ravel()
+    assert np.abs(stat).max() <= 1e-7
+
+
+def test_chambolle_pock_constant_image_is_a_fixed_point():
+    n = 16
+    A = _small_problem(n)
+    u_true = np.full((n, n), 0.7)
+    f = A @ u_true.ravel()
+    res = tv.chambolle_pock(A, f, (n, n), 1.0, 0.3, 0.3, outer=5, inner=10, u0=u_true)
+    np.testing.assert_allclose(res["u"], u_true, atol=1e-13)
+    assert np.abs(res["px"]).max() == 0.0 and np.abs(res["py"]).max() == 0.0
