@@ -43,6 +43,7 @@ namespace {
 constexpr int kFwdWarps = 8;   // warps per block (= per slice of rays) of y = A x
 constexpr int kAdjWarps = kTilePix / kSliceRows;  // warps per CTA of x = A^T y (one per pixel slice)
 constexpr int kAdjMinBlocks = 7;                    // CTAs per SM the register budget allows
+constexpr int kAdjMinBlocksChunked = 5;             // the same when the band is staged in angle chunks
 constexpr int64_t kStep = kSliceRows * kChunk;      // entries between a lane's consecutive chunks
 
 // Bytes of a staged band of `slots` values.
@@ -317,20 +318,35 @@ __device__ __forceinline__ float2 band_dot_chunked(const BandView& bv, const VT*
         const int k0 = __ldg(bv.chunk_k + j), k1 = __ldg(bv.chunk_k + j + 1);
         const int lo = __ldg(bv.band_off + k0), hi = __ldg(bv.band_off + k1);
         stage_band_range(bv, tile, y, band, k0, k1);
+        // two 8-entry chunks per step, both loads issued first
         while (c < nch) {
             const int64_t p = base + (int64_t)c * kStep;
-            int cc[8];
-            float v[8];
-            load8_col(bv.col16, p, cc);
-            Vals<VT>::load8(val, p, v);
+            const bool two = c + 1 < nch;
+            int c0[8], c1[8];
+            float v0[8], v1[8];
+            load8_col(bv.col16, p, c0);
+            Vals<VT>::load8(val, p, v0);
+            if (two) {
+                load8_col(bv.col16, p + kStep, c1);
+                Vals<VT>::load8(val, p + kStep, v1);
+            }
             bool beyond = false;
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const bool in = cc[u] >= lo && cc[u] < hi;
-                beyond |= cc[u] >= hi;
-                acc_fma(hs, hc, in ? v[u] : 0.0f, band_value(band, in ? cc[u] - lo : 0));
+                const bool in = c0[u] >= lo && c0[u] < hi;
+                beyond |= c0[u] >= hi;
+                acc_fma(hs, hc, in ? v0[u] : 0.0f, band_value(band, in ? c0[u] - lo : 0));
             }
-            if (beyond) break;  // the rest of this chunk belongs to a later band chunk
+            if (beyond) break;  // the rest of chunk c belongs to a later band chunk
+            ++c;
+            if (!two) break;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const bool in = c1[u] >= lo && c1[u] < hi;
+                beyond |= c1[u] >= hi;
+                acc_fma(hs, hc, in ? v1[u] : 0.0f, band_value(band, in ? c1[u] - lo : 0));
+            }
+            if (beyond) break;
             ++c;
         }
         __syncthreads();  // every lane done with this band chunk before the next staging
@@ -361,7 +377,7 @@ __device__ __forceinline__ float2 band_dot(const BandView& bv, const VT* __restr
 }
 
 template <typename VT, typename YT, typename OT, bool CHUNKED>
-__global__ void __launch_bounds__(kAdjWarps * 32, kAdjMinBlocks)
+__global__ void __launch_bounds__(kAdjWarps * 32, CHUNKED ? kAdjMinBlocksChunked : kAdjMinBlocks)
     band_adj_kernel(BandView bv, const VT* __restrict__ val, const YT* __restrict__ y, OT* __restrict__ out,
                     float2 scale)
 {
@@ -386,7 +402,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjMinBlocks)
 }
 
 template <typename VT, int MODE, bool CHUNKED>
-__global__ void __launch_bounds__(kAdjWarps * 32, kAdjMinBlocks)
+__global__ void __launch_bounds__(kAdjWarps * 32, CHUNKED ? kAdjMinBlocksChunked : kAdjMinBlocks)
     band_op_kernel(BandView bv, const VT* __restrict__ val, const float2* __restrict__ y, OpEpilogue a)
 {
     if (a.gate && *a.gate) return;
