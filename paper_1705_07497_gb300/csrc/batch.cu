@@ -34,7 +34,8 @@ __device__ __forceinline__ void st_y(float2* y, int64_t i, float2 v) { y[i] = v;
 
 struct Grid2 {
     int rb;      // row blocks per slice chunk
-    int chunks;  // ceil(B / 32)
+    int chunks;  // ceil(B / (32 * spl))
+    int spl;     // slices per lane in the sparse products (1, or 2 for batches >= 64)
 };
 
 // Block (rb, chunk) of a 1-D grid of rb * chunks blocks, chunk-major: the
@@ -76,6 +77,23 @@ __device__ __forceinline__ LaneMap lane_map(int B, int chunk, int lane)
     return m;
 }
 
+// Slices per lane of the sparse products: two adjacent slices (one 16-byte
+// gather of their double-float values) once a batch fills two warps' lanes.
+__host__ __device__ inline int slices_per_lane(int B) { return (B >= 64 && B % 2 == 0) ? 2 : 1; }
+
+// Lane map of the sparse products: SPL slices per lane, chunks of 32 * SPL.
+template <int SPL>
+__device__ __forceinline__ LaneMap lane_map_spl(int B, int chunk, int lane)
+{
+    if (SPL == 1) return lane_map(B, chunk, lane);
+    LaneMap m;
+    m.W = 32;
+    m.g = 0;
+    m.b = chunk * 32 * SPL + SPL * lane;
+    m.rpw = 1;
+    return m;
+}
+
 // First row of the warp (its sub-group 0) and the stride between a warp's rows.
 __device__ __forceinline__ int64_t warp_row0(int rb, int w, const LaneMap& m)
 {
@@ -91,35 +109,41 @@ __device__ __forceinline__ bool slice_live(int b, int B, const CgSlice* cg, cons
     return true;
 }
 
-// Sum over the block's warps of each lane's value (fixed order), written as
-// the block's partial for slice chunk*32 + lane:  partials[(q*B + b)*G + rb].
-// With sub-groups (W < 32) the lanes of one slice are first combined by a
-// fixed butterfly, and lanes b < B write.
-template <int NQ>
-__device__ __forceinline__ void block_partials(float2 (&v)[NQ], float2* partials, int B, int G, int rb, int chunk,
-                                               int W)
+// Sum over the block's warps of each lane's values (fixed order), written as
+// the block's partials for slices chunk * 32 * SPL + SPL * lane + s:
+// partials[(q*B + b)*G + rb].  With sub-groups (W < 32) the lanes of one
+// slice are first combined by a fixed butterfly, and lanes b < B write.
+template <int NQ, int SPL = 1>
+__device__ __forceinline__ void block_partials(float2 (&v)[NQ][SPL], float2* partials, int B, int G, int rb,
+                                               int chunk, int W)
 {
-    __shared__ float2 red[NQ][kWarps][32];
+    __shared__ float2 red[NQ][kWarps][32 * SPL];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int o = W; o < 32; o <<= 1) {
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            float2 t;
-            t.x = __shfl_xor_sync(0xffffffffu, v[q].x, o);
-            t.y = __shfl_xor_sync(0xffffffffu, v[q].y, o);
-            v[q] = df_add(v[q], t);
-        }
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int e = 0; e < SPL; ++e) {
+                float2 t;
+                t.x = __shfl_xor_sync(0xffffffffu, v[q][e].x, o);
+                t.y = __shfl_xor_sync(0xffffffffu, v[q][e].y, o);
+                v[q][e] = df_add(v[q][e], t);
+            }
     }
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) red[q][w][lane] = v[q];
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int e = 0; e < SPL; ++e) red[q][w][SPL * lane + e] = v[q][e];
     __syncthreads();
-    if (w == 0) {
-        const int b = chunk * 32 + lane;
-        if (b < B && lane < W) {
+    if (w == 0 && lane < W) {
+#pragma unroll
+        for (int e = 0; e < SPL; ++e) {
+            const int b = chunk * 32 * SPL + SPL * lane + e;
+            if (b >= B) continue;
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                float2 s = red[q][0][lane];
-                for (int k = 1; k < kWarps; ++k) s = df_add(s, red[q][k][lane]);
+                float2 s = red[q][0][SPL * lane + e];
+                for (int k = 1; k < kWarps; ++k) s = df_add(s, red[q][k][SPL * lane + e]);
                 partials[((size_t)q * B + b) * G + rb] = s;
             }
         }
@@ -174,28 +198,60 @@ __device__ __forceinline__ void stage_entries(const ColMap& cm, const VT* __rest
     *stage = e;
 }
 
-// acc += sum over the cnt staged entries of val * X[col][b], U entries per
-// step (U gathers in flight); every U gives the same bits.
-template <typename XT, int U>
+// Loads of SPL adjacent slices' values of one vector element: double-float
+// (16 bytes for two slices) or FP32 (8 bytes for two), as double-float pairs.
+template <int SPL>
+__device__ __forceinline__ void ld_xs(const float2* x, int64_t i, float2 (&o)[SPL])
+{
+    if (SPL == 1) {
+        o[0] = __ldg(x + i);
+    } else {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(x + i));
+        o[0] = make_float2(v.x, v.y);
+        o[SPL - 1] = make_float2(v.z, v.w);
+    }
+}
+template <int SPL>
+__device__ __forceinline__ void ld_xs(const float* x, int64_t i, float2 (&o)[SPL])
+{
+    if (SPL == 1) {
+        o[0] = make_float2(__ldg(x + i), 0.0f);
+    } else {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(x + i));
+        o[0] = make_float2(v.x, 0.0f);
+        o[SPL - 1] = make_float2(v.y, 0.0f);
+    }
+}
+
+// acc[e] += sum over the cnt staged entries of val * X[col][b + e], U entries
+// per step (U gathers in flight); every U gives the same bits.
+template <typename XT, int U, int SPL>
 __device__ __forceinline__ void staged_dot(const int2* st, int cnt, const XT* __restrict__ x, int B, int b,
-                                           float& hs, float& hc)
+                                           float (&hs)[SPL], float (&hc)[SPL])
 {
     int t = 0;
     for (; t + U <= cnt; t += U) {
         int2 e[U];
-        float2 xv[U];
+        float2 xv[U][SPL];
 #pragma unroll
         for (int u = 0; u < U; ++u) e[u] = st[t + u];
 #pragma unroll
-        for (int u = 0; u < U; ++u) xv[u] = ld_x(x, (int64_t)e[u].x * B + b);
+        for (int u = 0; u < U; ++u) ld_xs<SPL>(x, (int64_t)e[u].x * B + b, xv[u]);
 #pragma unroll
-        for (int u = 0; u < U; ++u) acc_fma(hs, hc, __int_as_float(e[u].y), xv[u]);
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int k = 0; k < SPL; ++k) acc_fma(hs[k], hc[k], __int_as_float(e[u].y), xv[u][k]);
     }
-    for (; t < cnt; ++t) acc_fma(hs, hc, __int_as_float(st[t].y), ld_x(x, (int64_t)st[t].x * B + b));
+    for (; t < cnt; ++t) {
+        float2 xv[SPL];
+        ld_xs<SPL>(x, (int64_t)st[t].x * B + b, xv);
+#pragma unroll
+        for (int k = 0; k < SPL; ++k) acc_fma(hs[k], hc[k], __int_as_float(st[t].y), xv[k]);
+    }
 }
 
-// Y[row][b] = scale * sum_k val_k X[col_k][b].
-template <typename VT, typename XT, typename YT, int U>
+// Y[row][b] = scale * sum_k val_k X[col_k][b]; SPL slices per lane.
+template <typename VT, typename XT, typename YT, int U, int SPL>
 __global__ void __launch_bounds__(256) spmm_df_kernel(SellView m, ColMap cm, const VT* __restrict__ val,
                                                       const XT* __restrict__ x, YT* __restrict__ y, int B,
                                                       BProd a, OutMap om)
@@ -203,42 +259,50 @@ __global__ void __launch_bounds__(256) spmm_df_kernel(SellView m, ColMap cm, con
     __shared__ int2 stage[kWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int rb, chunk;
-    const int chunks = (B + 31) / 32;
+    const int chunks = (B + 32 * SPL - 1) / (32 * SPL);
     block_coords(chunks, rb, chunk);
     const int G = (int)gridDim.x / chunks;
-    const LaneMap lm = lane_map(B, chunk, lane);
+    const LaneMap lm = lane_map_spl<SPL>(B, chunk, lane);
     const int b = lm.b, t_in = lane % lm.W;
-    const bool live = slice_live(b, B, a.cg, a.sb);
+    bool live[SPL];
+#pragma unroll
+    for (int k = 0; k < SPL; ++k) live[k] = slice_live(b + k, B, a.cg, a.sb);
+    const bool any = SPL == 1 ? live[0] : (live[0] || live[SPL - 1]);
     for (int64_t r0 = warp_row0(rb, w, lm); r0 < m.rows; r0 += row_stride(G, lm)) {
         const int64_t row = r0 + lm.g;
         const bool rv = row < m.rows;
         const int len = rv ? m.len[row] : 0;
         const int64_t base = rv ? row_base(m, row) : 0;
         const int maxlen = __reduce_max_sync(0xffffffffu, len);
-        float hs = 0.0f, hc = 0.0f;
+        float hs[SPL], hc[SPL];
+#pragma unroll
+        for (int k = 0; k < SPL; ++k) hs[k] = hc[k] = 0.0f;
         for (int j0 = 0; j0 < maxlen; j0 += lm.W) {
             stage_entries<VT>(cm, val, row, base, len, j0, t_in, &stage[w][lane]);
             __syncwarp();
             const int cnt = min(lm.W, len - j0);
-            if (live && cnt > 0) staged_dot<XT, U>(&stage[w][lm.g * lm.W], cnt, x, B, b, hs, hc);
+            if (any && cnt > 0) staged_dot<XT, U, SPL>(&stage[w][lm.g * lm.W], cnt, x, B, b, hs, hc);
             __syncwarp();
         }
-        if (live && rv) {
-            float2 v = acc_value(hs, hc);
+        if (!rv) continue;
+        int64_t pos = row;
+        bool keep = true;
+        if (om.user) {
+            int i, j;
+            tiled_coords(row, om.tn, i, j);
+            keep = i < om.n && j < om.n;
+            pos = (int64_t)i * om.n + j;
+        }
+#pragma unroll
+        for (int k = 0; k < SPL; ++k) {
+            if (!live[k] || !keep) continue;
+            float2 v = acc_value(hs[k], hc[k]);
             if (a.row_scale) {
-                const float s = a.row_scale[row];
-                v = df_mul_f(v, s);
-                if (a.rpow == 2) v = df_mul_f(v, s);
+                const float sc = a.row_scale[row];
+                v = df_mul_f(v, sc);
+                if (a.rpow == 2) v = df_mul_f(v, sc);
             }
-            int64_t pos = row;
-            bool keep = true;
-            if (om.user) {
-                int i, j;
-                tiled_coords(row, om.tn, i, j);
-                keep = i < om.n && j < om.n;
-                pos = (int64_t)i * om.n + j;
-            }
-            if (keep) st_y(y, pos * B + b, df_mul(a.scale, v));
+            st_y(y, pos * B + b + k, df_mul(a.scale, v));
         }
     }
 }
@@ -305,48 +369,64 @@ __device__ __forceinline__ void bop_epilogue(const BOp& a, int64_t t, int i, int
     }
 }
 
-// A^T y for every slice fused with the operator epilogue (rows = pixels).
-template <typename VT, int MODE, int U>
+// A^T y for every slice fused with the operator epilogue (rows = pixels);
+// SPL slices per lane.
+template <typename VT, int MODE, int U, int SPL>
 __global__ void __launch_bounds__(256) spmm_op_kernel(SellView m, ColMap cm, const VT* __restrict__ val,
                                                       const float2* __restrict__ y, int B, BOp a)
 {
     __shared__ int2 stage[kWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int rb, chunk;
-    const int chunks = (B + 31) / 32;
+    const int chunks = (B + 32 * SPL - 1) / (32 * SPL);
     block_coords(chunks, rb, chunk);
     const int G = (int)gridDim.x / chunks;
-    const LaneMap lm = lane_map(B, chunk, lane);
+    const LaneMap lm = lane_map_spl<SPL>(B, chunk, lane);
     const int b = lm.b, t_in = lane % lm.W;
-    const bool live = slice_live(b, B, MODE == 2 ? nullptr : a.cg, a.sb);
-    float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
+    bool live[SPL];
+#pragma unroll
+    for (int k = 0; k < SPL; ++k) live[k] = slice_live(b + k, B, MODE == 2 ? nullptr : a.cg, a.sb);
+    const bool any = SPL == 1 ? live[0] : (live[0] || live[SPL - 1]);
+    float s0[SPL], c0[SPL], s1[SPL], c1[SPL];
+#pragma unroll
+    for (int k = 0; k < SPL; ++k) s0[k] = c0[k] = s1[k] = c1[k] = 0.0f;
     for (int64_t r0 = warp_row0(rb, w, lm); r0 < m.rows; r0 += row_stride(G, lm)) {
         const int64_t row = r0 + lm.g;
         const bool rv = row < m.rows;
         const int len = rv ? m.len[row] : 0;
         const int64_t base = rv ? row_base(m, row) : 0;
         const int maxlen = __reduce_max_sync(0xffffffffu, len);
-        float hs = 0.0f, hc = 0.0f;
+        float hs[SPL], hc[SPL];
+#pragma unroll
+        for (int k = 0; k < SPL; ++k) hs[k] = hc[k] = 0.0f;
         for (int j0 = 0; j0 < maxlen; j0 += lm.W) {
             stage_entries<VT>(cm, val, row, base, len, j0, t_in, &stage[w][lane]);
             __syncwarp();
             const int cnt = min(lm.W, len - j0);
-            if (live && cnt > 0) staged_dot<float2, U>(&stage[w][lm.g * lm.W], cnt, y, B, b, hs, hc);
+            if (any && cnt > 0) staged_dot<float2, U, SPL>(&stage[w][lm.g * lm.W], cnt, y, B, b, hs, hc);
             __syncwarp();
         }
-        if (live && rv) {
-            int i, j;
-            tiled_coords(row, a.tn, i, j);
+        if (!rv) continue;
+        int i, j;
+        tiled_coords(row, a.tn, i, j);
+#pragma unroll
+        for (int k = 0; k < SPL; ++k) {
+            if (!live[k]) continue;
             if (i < a.n && j < a.n) {
-                bop_epilogue<MODE>(a, row, i, j, B, b, acc_value(hs, hc), s0, c0, s1, c1);
+                bop_epilogue<MODE>(a, row, i, j, B, b + k, acc_value(hs[k], hc[k]), s0[k], c0[k], s1[k], c1[k]);
             } else {
-                a.out[row * B + b] = df_zero();  // padding stays zero
-                if (MODE == 2) a.p_out[row * B + b] = df_zero();
+                a.out[row * B + b + k] = df_zero();  // padding stays zero
+                if (MODE == 2) a.p_out[row * B + b + k] = df_zero();
             }
         }
     }
-    float2 v[2] = {acc_value(s0, c0), acc_value(s1, c1)};
-    block_partials<2>(v, a.partials, B, G, rb, chunk, lm.W);
+    float2 v[2][SPL];
+#pragma unroll
+    for (int k = 0; k < SPL; ++k) {
+        v[0][k] = acc_value(s0[k], c0[k]);
+        v[1][k] = acc_value(s1[k], c1[k]);
+    }
+    block_partials<2, SPL>(v, a.partials, B, G, rb, chunk, lm.W);
 }
 
 // Surrogate stencil T (Sec. 3.2) for every slice fused with the epilogue.
@@ -392,7 +472,7 @@ __global__ void __launch_bounds__(256) stencil_b_kernel(int B, BOp a, const int3
             bop_epilogue<MODE>(a, p, i, j, B, b, acc_value(hs, hc), s0, c0, s1, c1);
         }
     }
-    float2 v[2] = {acc_value(s0, c0), acc_value(s1, c1)};
+    float2 v[2][1] = {{acc_value(s0, c0)}, {acc_value(s1, c1)}};
     block_partials<2>(v, a.partials, B, G, rb, chunk, lm.W);
 }
 
@@ -422,7 +502,7 @@ __global__ void __launch_bounds__(256) bcg_update_kernel(float2* __restrict__ u,
             acc_add(s, c, df_mul(rn, rn));
         }
     }
-    float2 v[1] = {acc_value(s, c)};
+    float2 v[1][1] = {{acc_value(s, c)}};
     block_partials<1>(v, partials, B, G, rb, chunk, lm.W);
 }
 
@@ -488,7 +568,7 @@ __global__ void __launch_bounds__(256) bsb_shrink_kernel(const float2* __restric
             u_old[e] = c;
         }
     }
-    float2 v[1] = {acc_value(s, cc)};
+    float2 v[1][1] = {{acc_value(s, cc)}};
     block_partials<1>(v, partials, B, G, rb, chunk, lm.W);
 }
 
@@ -623,10 +703,11 @@ struct BPlan {
     const SbSlice* sb;                 // gate (SB) or null
 };
 
-Grid2 make_grid(const ct_matrix* M, int64_t rows, int B)
+Grid2 make_grid(const ct_matrix* M, int64_t rows, int B, int spl = 1)
 {
     Grid2 g;
-    g.chunks = (B + 31) / 32;
+    g.spl = spl;
+    g.chunks = (B + 32 * spl - 1) / (32 * spl);
     const int64_t rows_per_block = (int64_t)kWarps * (32 / lanes_per_row(B));
     const int64_t cap = (int64_t)(M->sm_count > 0 ? M->sm_count : 148) * 8;
     int64_t rb = (rows + rows_per_block - 1) / rows_per_block;
@@ -679,16 +760,27 @@ int launch_spmm(const ct_matrix* M, int which, ValKind vk, const XT* x, YT* y, i
     const SellView m{C.slice_ptr, C.row_len, C.rows};
     const ColMap cm = colmap_of(M, which);
     const OutMap om{user_out ? 1 : 0, M->g.n, M->tn};
-    const Grid2 g = make_grid(M, C.rows, B);
+    // paired slices load two adjacent values at once: only from an input
+    // aligned for that (a caller's array may be an offset view)
+    const int spl = (slices_per_lane(B) == 2 && reinterpret_cast<uintptr_t>(x) % (2 * sizeof(XT)) == 0) ? 2 : 1;
+    const Grid2 g = make_grid(M, C.rows, B, spl);
     const int blocks = g.rb * g.chunks;
     const bool u4 = (unroll ? unroll : spmm_unroll(M, B)) == 4;
+#define CT_DF(VT, VAL, U, SPL) spmm_df_kernel<VT, XT, YT, U, SPL><<<blocks, 256, 0, st>>>(m, cm, VAL, x, y, B, a, om)
     if (vk == ValKind::F16) {
-        if (u4) spmm_df_kernel<__half, XT, YT, 4><<<blocks, 256, 0, st>>>(m, cm, C.qval, x, y, B, a, om);
-        else spmm_df_kernel<__half, XT, YT, 8><<<blocks, 256, 0, st>>>(m, cm, C.qval, x, y, B, a, om);
+        if (spl == 2) {
+            if (u4) CT_DF(__half, C.qval, 4, 2); else CT_DF(__half, C.qval, 8, 2);
+        } else {
+            if (u4) CT_DF(__half, C.qval, 4, 1); else CT_DF(__half, C.qval, 8, 1);
+        }
     } else {
-        if (u4) spmm_df_kernel<float, XT, YT, 4><<<blocks, 256, 0, st>>>(m, cm, C.val, x, y, B, a, om);
-        else spmm_df_kernel<float, XT, YT, 8><<<blocks, 256, 0, st>>>(m, cm, C.val, x, y, B, a, om);
+        if (spl == 2) {
+            if (u4) CT_DF(float, C.val, 4, 2); else CT_DF(float, C.val, 8, 2);
+        } else {
+            if (u4) CT_DF(float, C.val, 4, 1); else CT_DF(float, C.val, 8, 1);
+        }
     }
+#undef CT_DF
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -751,24 +843,25 @@ int bapply(const BPlan& P, BOp ep, const float2* in, cudaStream_t st, Grid2& g_u
         const ColMap cm = colmap_of(P.M, 1);
         g_used = P.g_rows_t;
         const int blocks = g_used.rb * g_used.chunks;
-#define CT_BOP(VT, VAL, U)                                                                  \
-    switch (ep.mode) {                                                                      \
-    case 1: spmm_op_kernel<VT, 1, U><<<blocks, 256, 0, st>>>(m, cm, VAL, w.y, P.B, ep); break; \
-    case 2: spmm_op_kernel<VT, 2, U><<<blocks, 256, 0, st>>>(m, cm, VAL, w.y, P.B, ep); break; \
-    default: spmm_op_kernel<VT, 3, U><<<blocks, 256, 0, st>>>(m, cm, VAL, w.y, P.B, ep); break; \
+#define CT_BOP(VT, VAL, U, SPL)                                                                       \
+    switch (ep.mode) {                                                                                \
+    case 1: spmm_op_kernel<VT, 1, U, SPL><<<blocks, 256, 0, st>>>(m, cm, VAL, w.y, P.B, ep); break;  \
+    case 2: spmm_op_kernel<VT, 2, U, SPL><<<blocks, 256, 0, st>>>(m, cm, VAL, w.y, P.B, ep); break;  \
+    default: spmm_op_kernel<VT, 3, U, SPL><<<blocks, 256, 0, st>>>(m, cm, VAL, w.y, P.B, ep); break; \
     }
         const bool u4 = spmm_unroll(P.M, P.B) == 4;
+        const bool pair = g_used.spl == 2;
         if (vk == ValKind::F16) {
-            if (u4) {
-                CT_BOP(__half, C.qval, 4)
+            if (pair) {
+                if (u4) { CT_BOP(__half, C.qval, 4, 2) } else { CT_BOP(__half, C.qval, 8, 2) }
             } else {
-                CT_BOP(__half, C.qval, 8)
+                if (u4) { CT_BOP(__half, C.qval, 4, 1) } else { CT_BOP(__half, C.qval, 8, 1) }
             }
         } else {
-            if (u4) {
-                CT_BOP(float, C.val, 4)
+            if (pair) {
+                if (u4) { CT_BOP(float, C.val, 4, 2) } else { CT_BOP(float, C.val, 8, 2) }
             } else {
-                CT_BOP(float, C.val, 8)
+                if (u4) { CT_BOP(float, C.val, 4, 1) } else { CT_BOP(float, C.val, 8, 1) }
             }
         }
 #undef CT_BOP
@@ -848,8 +941,8 @@ int bmake_plan(ct_matrix* M, int B, double c_id, double c_ata, double c_grad, do
     P.refresh = refresh;
     P.tol = tol;
     P.sb = nullptr;
-    P.g_rows_a = make_grid(M, M->rows, B);
-    P.g_rows_t = make_grid(M, M->At.rows, B);
+    P.g_rows_a = make_grid(M, M->rows, B, slices_per_lane(B));
+    P.g_rows_t = make_grid(M, M->At.rows, B, slices_per_lane(B));
     P.g_pix = make_grid(M, P.n2, B);
     BOp& b = P.base;
     std::memset(&b, 0, sizeof(b));

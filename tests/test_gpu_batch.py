@@ -288,3 +288,19 @@ def test_spmm_unroll_variants_are_bit_identical_and_tuned(dev):
     assert M.spmm_unroll(5) in (4, 8)
     assert torch.equal(u.cpu(), outs[0])
     M.close()
+
+
+def test_batched_split_bregman_66_slices(dev):
+    """66 slices: the sparse products run two slices per lane (chunks of 64
+    slices, the last one partial)."""
+    ref = oracle_A(*GEOM64)
+    M = gpu_A(GEOM64)
+    seeds = list(range(100, 166))
+    truths, F = _data(GEOM64, seeds, ref)
+    u = torch.zeros((M.cols, len(seeds)), device=dev)
+    st = M.split_bregman(t32(F, dev), u, 1.0, 0.1, 8, 10)
+    assert st["status"] == 0 and st["outer_done"] == 8
+    got = u.cpu().numpy()
+    for b in (0, 1, 33, 63, 64, 65):
+        want = tv.split_bregman(ref, F[:, b], (64, 64), 1.0, 0.1, 8, 10)["u"].ravel()
+        assert rel(got[:, b], want) <= 1e-3, b

@@ -102,7 +102,7 @@ def test_matrix_entries_full_size_sampled(dev):
 
 
 @pytest.mark.parametrize("geom", GEOMS[:4] + [(256, 360, 2, 363)])
-@pytest.mark.parametrize("batch", [1, 3, 40])
+@pytest.mark.parametrize("batch", [1, 3, 40, 64, 65])
 def test_forward_adjoint_parity(dev, geom, batch):
     ref = oracle_A(*geom)
     M = gpu_A(*geom)
@@ -442,3 +442,19 @@ def test_chambolle_pock_warm_start_and_batch_limit(dev):
         M.chambolle_pock(torch.zeros((M.rows, 2), device=dev), torch.zeros((M.cols, 2), device=dev),
                          1.0, 0.3, 0.3, 3, 3)
     assert e.value.code == ct.CT_ERR_UNSUPPORTED
+
+
+def test_batched_products_from_an_offset_view(dev):
+    """A batch of 64 from an array that starts 4 bytes into its allocation: the
+    products must not assume the alignment paired-slice loads need."""
+    geom = (64, 90, 3, 91)
+    ref = oracle_A(*geom)
+    M = gpu_A(*geom)
+    B = 64
+    y = inputs.random_vector(ref.shape[0] * B, 64).reshape(ref.shape[0], B)
+    big = torch.empty(ref.shape[0] * B + 1, dtype=torch.float32, device=dev)
+    yv = big[1:].view(ref.shape[0], B)
+    yv.copy_(t32(y, dev))
+    xg = torch.empty((ref.shape[1], B), dtype=torch.float32, device=dev)
+    M.adjoint(yv, xg)
+    assert rel(xg.cpu().numpy(), ref.T @ y) <= SPMV_TOL
