@@ -827,7 +827,8 @@ def bench_kernel(args):
     """Small committed case for ncu: W + K launches of one product on the
     slice workload's geometry (A and A^T resident, 0.98 GB > L2).
     forward/adjoint: ct_forward / ct_adjoint (batch 1); solver: ct_cg_solve
-    with the split-Bregman operator and K CG steps."""
+    with the split-Bregman operator and K CG steps; spmm: the same solve on
+    the FP16 matrices for 256 slices at once (the batched products)."""
     import torch
 
     from paper_1705_07497_gb300 import ct
@@ -836,11 +837,18 @@ def bench_kernel(args):
     torch.cuda.set_device(dev)
     wl = inputs.WORKLOADS[args.workload]
     n = wl["n"]
+    if args.kernel == "spmm":
+        bl = inputs.WORKLOADS["batch_512x256"]
+        M = ct.Matrix(bl["n"], bl["n_angles_total"], bl["keep_every"], bl["n_bins"], ct.CT_VAL_FP16_ROWSCALE)
+        B = bl["batch"]
+        rhs = torch.tensor(inputs.random_vector(M.cols * B, 1).reshape(M.cols, B), dtype=torch.float32, device=dev)
+        u = torch.zeros((M.cols, B), dtype=torch.float32, device=dev)
+        fn = lambda: M.cg_solve(rhs, u, 0.0, bl["alpha"], bl["lam"], args.steps)  # noqa: E731
+        return _time_kernel_fn(args, M, fn, dev, 1)
     M = ct.Matrix(n, wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
     x = torch.tensor(inputs.ellipse_phantom(n, wl["seed"]).ravel(), dtype=torch.float32, device=dev)
     y = torch.empty(M.rows, dtype=torch.float32, device=dev)
     M.forward(x, y)
-    stream = torch.cuda.current_stream(dev)
     if args.kernel == "forward":
         fn = lambda: M.forward(x, y)  # noqa: E731
     elif args.kernel == "adjoint":
@@ -850,10 +858,16 @@ def bench_kernel(args):
         M.adjoint(y, rhs)
         u = torch.zeros(M.cols, dtype=torch.float32, device=dev)
         fn = lambda: M.cg_solve(rhs, u, 0.0, wl["alpha"], wl["lam"], args.steps)  # noqa: E731
+    return _time_kernel_fn(args, M, fn, dev, 1 if args.kernel == "solver" else args.steps)
+
+
+def _time_kernel_fn(args, M, fn, dev, reps):
+    import torch
+
+    stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
         fn()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 1 if args.kernel == "solver" else args.steps
     a.record(stream)
     for _ in range(reps):
         fn()
@@ -924,7 +938,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(inputs.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default=None, choices=["forward", "adjoint", "solver"],
+    ap.add_argument("--kernel", default=None, choices=["forward", "adjoint", "solver", "spmm"],
                     help="time one product kernel in isolation (small case for profilers)")
     ap.add_argument("--_oracle-in", dest="oracle_in", default=None)
     ap.add_argument("--_oracle-out", dest="oracle_out", default=None)

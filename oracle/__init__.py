@@ -14,9 +14,12 @@ Contents
              anisotropic-TV split Bregman (Sec. 2, Eq. SB_solve; Sec. 4), the
              Chambolle-Pock resolvent (Sec. 2, Eq. PD_resolve), and the sparse
              surrogate T (Sec. 3.2, Eq. def_sparse_surr / surr_SBupd).
+  fourier    the Fourier-domain data term (Sec. 2, Eq. four_obj): the exact
+             nonuniform DFT on polar samples, the data's 1-D DFTs, Gaussian
+             gridding and the fused matrix B* B (Sec. 3.1, Eq. fusedop).
 
 Every floating-point result is FP64.  Readings of the paper where it is
 silent or garbled are stated in the docstring of the function that takes them.
 """
 
-from . import radon, tv  # noqa: F401
+from . import fourier, radon, tv  # noqa: F401
