@@ -81,18 +81,30 @@ __device__ __forceinline__ LaneMap lane_map(int B, int chunk, int lane)
 // gather of their double-float values) once a batch fills two warps' lanes.
 __host__ __device__ inline int slices_per_lane(int B) { return (B >= 64 && B % 2 == 0) ? 2 : 1; }
 
-// Lane map of the sparse products: SPL slices per lane, chunks of 32 * SPL.
-template <int SPL>
+// Lane map of the sparse products: SPL slices per lane, chunks of 32 * SPL
+// slices; HALF (SPL = 2): half-warps of 16 lanes take one row each for a
+// chunk of 32 slices, so that a chunk's gathered vectors (N^2 x 32 slices)
+// stay within L2 while the matrix streams past them once per chunk.
+template <int SPL, bool HALF = false>
 __device__ __forceinline__ LaneMap lane_map_spl(int B, int chunk, int lane)
 {
     if (SPL == 1) return lane_map(B, chunk, lane);
     LaneMap m;
+    if (HALF) {
+        m.W = 16;
+        m.g = lane >> 4;
+        m.b = chunk * 32 + SPL * (lane & 15);
+        m.rpw = 2;
+        return m;
+    }
     m.W = 32;
     m.g = 0;
     m.b = chunk * 32 * SPL + SPL * lane;
     m.rpw = 1;
     return m;
 }
+
+__host__ __device__ inline int chunk_slices(int spl, bool half) { return half ? 32 : 32 * spl; }
 
 // First row of the warp (its sub-group 0) and the stride between a warp's rows.
 __device__ __forceinline__ int64_t warp_row0(int rb, int w, const LaneMap& m)
@@ -250,8 +262,9 @@ __device__ __forceinline__ void staged_dot(const int2* st, int cnt, const XT* __
     }
 }
 
-// Y[row][b] = scale * sum_k val_k X[col_k][b]; SPL slices per lane.
-template <typename VT, typename XT, typename YT, int U, int SPL>
+// Y[row][b] = scale * sum_k val_k X[col_k][b]; SPL slices per lane (HALF:
+// 16 lanes per row, see lane_map_spl).
+template <typename VT, typename XT, typename YT, int U, int SPL, bool HALF>
 __global__ void __launch_bounds__(256) spmm_df_kernel(SellView m, ColMap cm, const VT* __restrict__ val,
                                                       const XT* __restrict__ x, YT* __restrict__ y, int B,
                                                       BProd a, OutMap om)
@@ -259,10 +272,11 @@ __global__ void __launch_bounds__(256) spmm_df_kernel(SellView m, ColMap cm, con
     __shared__ int2 stage[kWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int rb, chunk;
-    const int chunks = (B + 32 * SPL - 1) / (32 * SPL);
+    const int cs = chunk_slices(SPL, HALF);
+    const int chunks = (B + cs - 1) / cs;
     block_coords(chunks, rb, chunk);
     const int G = (int)gridDim.x / chunks;
-    const LaneMap lm = lane_map_spl<SPL>(B, chunk, lane);
+    const LaneMap lm = lane_map_spl<SPL, HALF>(B, chunk, lane);
     const int b = lm.b, t_in = lane % lm.W;
     bool live[SPL];
 #pragma unroll
@@ -703,12 +717,13 @@ struct BPlan {
     const SbSlice* sb;                 // gate (SB) or null
 };
 
-Grid2 make_grid(const ct_matrix* M, int64_t rows, int B, int spl = 1)
+Grid2 make_grid(const ct_matrix* M, int64_t rows, int B, int spl = 1, bool half = false)
 {
     Grid2 g;
     g.spl = spl;
-    g.chunks = (B + 32 * spl - 1) / (32 * spl);
-    const int64_t rows_per_block = (int64_t)kWarps * (32 / lanes_per_row(B));
+    const int cs = chunk_slices(spl, half);
+    g.chunks = (B + cs - 1) / cs;
+    const int64_t rows_per_block = (int64_t)kWarps * (half ? 2 : 32 / lanes_per_row(B));
     const int64_t cap = (int64_t)(M->sm_count > 0 ? M->sm_count : 148) * 8;
     int64_t rb = (rows + rows_per_block - 1) / rows_per_block;
     if (rb > cap) rb = cap;
@@ -763,21 +778,29 @@ int launch_spmm(const ct_matrix* M, int which, ValKind vk, const XT* x, YT* y, i
     // paired slices load two adjacent values at once: only from an input
     // aligned for that (a caller's array may be an offset view)
     const int spl = (slices_per_lane(B) == 2 && reinterpret_cast<uintptr_t>(x) % (2 * sizeof(XT)) == 0) ? 2 : 1;
-    const Grid2 g = make_grid(M, C.rows, B, spl);
+    // y = A x gathers image vectors from all over the image: 32-slice chunks
+    // keep them L2-resident (the A^T products gather within a tile's band)
+    const bool half = spl == 2 && which == 0;
+    const Grid2 g = make_grid(M, C.rows, B, spl, half);
     const int blocks = g.rb * g.chunks;
     const bool u4 = (unroll ? unroll : spmm_unroll(M, B)) == 4;
-#define CT_DF(VT, VAL, U, SPL) spmm_df_kernel<VT, XT, YT, U, SPL><<<blocks, 256, 0, st>>>(m, cm, VAL, x, y, B, a, om)
+#define CT_DF(VT, VAL, U, SPL, H) \
+    spmm_df_kernel<VT, XT, YT, U, SPL, H><<<blocks, 256, 0, st>>>(m, cm, VAL, x, y, B, a, om)
     if (vk == ValKind::F16) {
-        if (spl == 2) {
-            if (u4) CT_DF(__half, C.qval, 4, 2); else CT_DF(__half, C.qval, 8, 2);
+        if (half) {
+            if (u4) CT_DF(__half, C.qval, 4, 2, true); else CT_DF(__half, C.qval, 8, 2, true);
+        } else if (spl == 2) {
+            if (u4) CT_DF(__half, C.qval, 4, 2, false); else CT_DF(__half, C.qval, 8, 2, false);
         } else {
-            if (u4) CT_DF(__half, C.qval, 4, 1); else CT_DF(__half, C.qval, 8, 1);
+            if (u4) CT_DF(__half, C.qval, 4, 1, false); else CT_DF(__half, C.qval, 8, 1, false);
         }
     } else {
-        if (spl == 2) {
-            if (u4) CT_DF(float, C.val, 4, 2); else CT_DF(float, C.val, 8, 2);
+        if (half) {
+            if (u4) CT_DF(float, C.val, 4, 2, true); else CT_DF(float, C.val, 8, 2, true);
+        } else if (spl == 2) {
+            if (u4) CT_DF(float, C.val, 4, 2, false); else CT_DF(float, C.val, 8, 2, false);
         } else {
-            if (u4) CT_DF(float, C.val, 4, 1); else CT_DF(float, C.val, 8, 1);
+            if (u4) CT_DF(float, C.val, 4, 1, false); else CT_DF(float, C.val, 8, 1, false);
         }
     }
 #undef CT_DF
