@@ -61,7 +61,7 @@ def measured_peak():
 def kernel_source_hash():
     h = hashlib.sha256()
     for name in ("solver_ops.cu", "sparse_common.cuh", "dfloat.cuh", "reduce.cuh", "ct_internal.cuh",
-                 "layout.cuh"):
+                 "layout.cuh", "op_epilogue.cuh"):
         with open(os.path.join(ROOT, "paper_1705_07497_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -721,6 +721,168 @@ def bench_cp(args):
     M.close()
 
 
+def bench_fourier(args):
+    """Fourier-domain workload: one step = one split-Bregman reconstruction of
+    the slice with the data term Re(F^H F) of Eq. SBFFT, evaluated by Gaussian
+    gridding and the fused matrix of Eq. fusedop (C, the samples and the data
+    resident); the sinogram is measured through the Siddon operator."""
+    import torch
+
+    from paper_1705_07497_gb300 import ct
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = inputs.WORKLOADS[args.workload]
+    n, na, ke, nb = wl["n"], wl["n_angles_total"], wl["keep_every"], wl["n_bins"]
+    A = ct.Matrix(n, na, ke, nb)
+    truth, f_host = make_data(wl, A, dev, wl["seed"])
+    x_probe = torch.tensor(truth.ravel(), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def op_ms(fn, reps=20):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    # one normal-operator product per data term (Sec. 4's table compares these)
+    out_img = torch.empty(n * n, dtype=torch.float32, device=dev)
+    y_tmp = torch.empty(A.rows, dtype=torch.float32, device=dev)
+    per_apply = {"siddon_A_then_AT": round(op_ms(lambda: (A.forward(x_probe, y_tmp), A.adjoint(y_tmp, out_img))), 4)}
+    for mode, name in ((ct.CT_FOURIER_FUSED, "fused"), (ct.CT_FOURIER_GRIDDING, "gridding")):
+        for m_sp in (2, 6, 12):
+            t0 = time.perf_counter()
+            Fm = ct.FourierMatrix(n, na, ke, nb, m_sp=m_sp, mode=mode)
+            torch.cuda.synchronize()
+            bs = time.perf_counter() - t0
+            per_apply["%s_msp%d" % (name, m_sp)] = {"ms": round(op_ms(lambda: Fm.normal(x_probe, out_img)), 4),
+                                                   "build_s": round(bs, 3), "stored_weights": Fm.nnz}
+            Fm.close()
+    A.close()
+
+    F = ct.FourierMatrix(n, na, ke, nb, m_sp=wl["m_sp"], mode=wl["fourier_mode"])
+    f = torch.tensor(f_host, dtype=torch.float32, device=dev)
+    u = torch.zeros(n * n, dtype=torch.float32, device=dev)
+    prm = (wl["alpha"], wl["lam"], wl["outer"], wl["inner"])
+
+    def step():
+        u.zero_()
+        F.split_bregman(f, u, *prm, stats=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed_steps")
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    secs = e0.elapsed_time(e1) / 1e3
+    normal_ms = op_ms(lambda: F.normal(x_probe, out_img))
+    f_pin = torch.tensor(f_host, dtype=torch.float32).pin_memory()
+    u_pin = torch.zeros(n * n, dtype=torch.float32).pin_memory()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u_pin.zero_()
+        F.split_bregman(f_pin, u_pin, *prm, stats=False)
+    e2e_secs = time.perf_counter() - t0
+    mr = 2 * n
+    nd = 4 * wl["m_sp"] + 1
+    # bytes of one fused normal-operator product: C once; the 2N x 2N complex
+    # double-float grid written by the padding, read and written by four FFT
+    # passes and the fused product, read by the crop; image in and out
+    grid = mr * mr * 16
+    alg = nd * nd * mr * mr * 4 + grid * (1 + 8 + 2 + 1) + 2 * n * n * 4
+    peak, peak_kind = measured_peak()
+    out = {
+        "metric": METRIC,
+        "value": round(args.steps / secs, 4),
+        "unit": "slices/s",
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1e3 * secs / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic: seeded random-ellipse phantom, projected by the Siddon A, 1% Gaussian noise",
+        "config": {
+            "workload": args.workload + ": %dx%d slice, %d of %d angles, %d bins, split Bregman %d x %d CG on the "
+                        "Fourier-domain data term (gridding m_sp = %d, %s)"
+                        % (n, n, F.rows // nb, na, nb, wl["outer"], wl["inner"], wl["m_sp"],
+                           "fused matrix" if wl["fourier_mode"] == 0 else "interpolate and spread"),
+            "l2": "inputs larger than L2: the fused matrix streams %.2f GB per product" % (nd * nd * mr * mr * 4 / 1e9),
+        },
+        "roofline": {
+            "kernel": "ct_fourier_normal: pad, 2-D FFT, fused-matrix product (dia_kernel), inverse 2-D FFT, crop",
+            "bound": "hbm",
+            "achieved": round(alg / (normal_ms * 1e-3) / 1e9, 1),
+            "peak": peak,
+            "peak_kind": peak_kind,
+            "unit": "GB/s",
+            "frac": round(alg / (normal_ms * 1e-3) / 1e9 / peak, 4),
+            "traffic": None,
+            "algorithmic_bytes": int(alg),
+            "launch_ms": round(normal_ms, 4),
+        },
+        "per_apply_ms": per_apply,
+        "e2e": {"value": round(args.steps / e2e_secs, 4), "unit": "slices/s",
+                "h2d_bytes_per_step": int(f_pin.numel() * 4 + u_pin.numel() * 4),
+                "d2h_bytes_per_step": int(u_pin.numel() * 4)},
+        "gpu_launches": None,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        # the oracle (unfused gridding, FP64) on the first update, and the GPU against it
+        from oracle import fourier as fo
+        from oracle import radon, tv
+
+        t0 = time.perf_counter()
+        g = fo.Gridding(n, na, ke, nb, wl["m_sp"])
+        S = fo.FourierSystem(n, na, ke, nb, gridding=g)
+        fhat = fo.sinogram_dft(f_host, radon.num_kept(na, ke), nb)
+        ref = tv.split_bregman(S, fhat, (n, n), wl["alpha"], wl["lam"], 1, wl["inner"], normal=g.normal)
+        secs_cpu = time.perf_counter() - t0
+        # the oracle with the weights and E rounded to FP32 as the library stores them
+        g32 = fo.Gridding(n, na, ke, nb, wl["m_sp"])
+        g32.G.data = g32.G.data.astype(np.float32).astype(np.float64)
+        g32.E = g32.E.astype(np.float32).astype(np.float64)
+        S32 = fo.FourierSystem(n, na, ke, nb, gridding=g32)
+        ref32 = tv.split_bregman(S32, fhat, (n, n), wl["alpha"], wl["lam"], 1, wl["inner"], normal=g32.normal)
+
+        def rel_to_ref(v):
+            return float(np.linalg.norm(v - ref["u"].ravel()) / np.linalg.norm(ref["u"].ravel()))
+
+        par = {"oracle_fp32_tables_vs_oracle": rel_to_ref(ref32["u"].ravel())}
+        for mode, key in ((wl["fourier_mode"], "after_1_update"), (1 - wl["fourier_mode"], "other_mode_after_1_update")):
+            Fm = F if mode == wl["fourier_mode"] else ct.FourierMatrix(n, na, ke, nb, m_sp=wl["m_sp"], mode=mode)
+            u1 = torch.zeros(n * n, dtype=torch.float32, device=dev)
+            Fm.split_bregman(f, u1, wl["alpha"], wl["lam"], 1, wl["inner"])
+            par[key] = rel_to_ref(u1.cpu().double().numpy())
+            if Fm is not F:
+                Fm.close()
+        out["parity"] = par
+        out["cpu_baseline"] = {"value": round(1 / wl["outer"] / secs_cpu, 6), "unit": "slices/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": "1 of %d updates, FP64 numpy/scipy gridding (FFT, sparse G and G^T), "
+                                         "single-threaded; %.1f s" % (wl["outer"], secs_cpu)}
+    print(json.dumps(out))
+    F.close()
+
+
 def bench_ragged(args):
     """Ragged workload: one step = every problem reconstructed by one
     ct_split_bregman_ragged call (matrices resident, one per geometry)."""
@@ -828,7 +990,8 @@ def bench_kernel(args):
     slice workload's geometry (A and A^T resident, 0.98 GB > L2).
     forward/adjoint: ct_forward / ct_adjoint (batch 1); solver: ct_cg_solve
     with the split-Bregman operator and K CG steps; spmm: the same solve on
-    the FP16 matrices for 256 slices at once (the batched products)."""
+    the FP16 matrices for 256 slices at once (the batched products);
+    fourier: ct_fourier_normal, the fused Fourier-domain normal operator."""
     import torch
 
     from paper_1705_07497_gb300 import ct
@@ -837,6 +1000,14 @@ def bench_kernel(args):
     torch.cuda.set_device(dev)
     wl = inputs.WORKLOADS[args.workload]
     n = wl["n"]
+    if args.kernel == "fourier":
+        fl = inputs.WORKLOADS["fourier_512"]
+        F = ct.FourierMatrix(fl["n"], fl["n_angles_total"], fl["keep_every"], fl["n_bins"], m_sp=args.m_sp,
+                             mode=fl["fourier_mode"])
+        x = torch.tensor(inputs.ellipse_phantom(fl["n"], fl["seed"]).ravel(), dtype=torch.float32, device=dev)
+        out = torch.empty_like(x)
+        fn = lambda: F.normal(x, out)  # noqa: E731
+        return _time_kernel_fn(args, F, fn, dev, args.steps)
     if args.kernel == "spmm":
         bl = inputs.WORKLOADS["batch_512x256"]
         M = ct.Matrix(bl["n"], bl["n_angles_total"], bl["keep_every"], bl["n_bins"], ct.CT_VAL_FP16_ROWSCALE)
@@ -938,8 +1109,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(inputs.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default=None, choices=["forward", "adjoint", "solver", "spmm"],
+    ap.add_argument("--kernel", default=None, choices=["forward", "adjoint", "solver", "spmm", "fourier"],
                     help="time one product kernel in isolation (small case for profilers)")
+    ap.add_argument("--m-sp", dest="m_sp", type=int, default=6,
+                    help="--kernel fourier: gridding window half-width")
     ap.add_argument("--_oracle-in", dest="oracle_in", default=None)
     ap.add_argument("--_oracle-out", dest="oracle_out", default=None)
     ap.add_argument("--_oracle-updates", dest="oracle_updates", type=int, default=ORACLE_UPDATES)
@@ -957,6 +1130,8 @@ def main():
         bench_ragged(args)
     elif args.workload.startswith("grad_"):
         bench_grad(args)
+    elif args.workload.startswith("fourier_"):
+        bench_fourier(args)
     elif wl.get("solver") == "cp":
         bench_cp(args)
     elif wl.get("batch", 1) > 1:

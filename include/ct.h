@@ -277,6 +277,77 @@ int ct_matrix_export_fp16(ct_matrix_t A, uint16_t *q_bits, float *scale);
 int ct_surrogate_stencil(ct_matrix_t A, int32_t r, int32_t square, int32_t capacity,
                          int32_t *di, int32_t *dj, double *val, int32_t *count);
 
+/* ---------------------------------------------------------------------------
+ * Fourier-domain data term (Sec. 2, Eqs. four_obj, SBFFT) evaluated by Gaussian
+ * gridding (Sec. 3.1) with the fused matrix B* B (Eq. fusedop).
+ *
+ * By the Fourier slice theorem the 1-D DFT of the projection at angle theta_k
+ * samples the image's 2-D transform on the line rho (cos theta_k, sin theta_k).
+ *   samples   J = n_kept * n_bins, sample j = k'*n_bins + m at
+ *             omega_j = rho_m (cos theta_k, sin theta_k),
+ *             rho_m = 2 pi (m - floor(n_bins/2)) / n_bins.
+ *   F         (F x)_j = n_bins^{-1/2} sum_p x_p exp(-i omega_j . c_p), c_p the
+ *             centre of pixel p: (j - N/2 + 1/2, i - N/2 + 1/2).
+ *   data      fhat_j = n_bins^{-1/2} sum_b f_{k',b} exp(-i rho_m s_b), the DFT
+ *             of each measured projection; the scaling makes ||F x - fhat||
+ *             the sinogram residual of point-sampled pixels, so alpha and
+ *             lambda keep their meaning.
+ *   normal    Re(F^H F) (real images); right-hand side Re(F^H fhat).
+ * F is evaluated as Greengard and Lee's gridding: deconvolution by
+ * E(k) = sqrt(pi/tau) exp(k^2 tau) per dimension, zero padding to a 2N x 2N
+ * grid, FFT, and Gaussian weights exp(-(w - 2 pi m / 2N)^2 / (4 tau)) over the
+ * 2 m_sp + 1 grid points per dimension nearest each sample (|m - m_j| <= m_sp,
+ * m_j = floor(w 2N / 2 pi), periodic).  With G those weights (J x 4N^2),
+ * Re(F^H F) = E Z^T FFT^H (G^T G) FFT Z E / (16 N^4 n_bins); convolution
+ * fusing stores C = G^T G, whose nonzeros lie on the (4 m_sp + 1)^2 periodic
+ * offsets |d| <= 2 m_sp, so that one normal-operator product is two FFTs,
+ * one product with C and two diagonal scalings.  Accuracy about 2, 6 and 12
+ * digits at m_sp = 2, 6, 12 with tau = m_sp / N^2.  The grid and sample
+ * vectors are carried in double-float; the FP32 tables (weights, twiddles,
+ * C) perturb the operator by about 1e-7 relative, amplified towards the
+ * corners of the frequency square by the deconvolution (about exp(m_sp)).
+ *
+ * The handle returned by ct_build_fourier works with ct_matrix_info
+ * (rows = J, cols = N*N, nnz = stored weights: C's (4 m_sp + 1)^2 * 4N^2
+ * diagonal entries, or J (2 m_sp + 1)^2 for CT_FOURIER_GRIDDING),
+ * ct_destroy_matrix, ct_surrogate_stencil (the stencil of the Fourier normal
+ * operator, whose point response is translation invariant: s(d) =
+ * n_bins^{-1} sum_j cos(omega_j . d), FP64), and with ct_cg_solve,
+ * ct_split_bregman and ct_chambolle_pock at batch 1, where c_ata multiplies
+ * Re(F^H F) and the data vectors f, g stay real sinograms [n_kept][n_bins]
+ * (transformed to fhat inside the call).  Every other call returns
+ * CT_ERR_UNSUPPORTED for it.  N must be a power of two in [16, 2048]. */
+enum {
+    CT_FOURIER_FUSED = 0,    /* precomputed C = G^T G (convolution fusing, Eq. fusedop) */
+    CT_FOURIER_GRIDDING = 1  /* interpolate with G, then spread with G^T, each product */
+};
+
+typedef struct {
+    int32_t m_sp;  /* window half-width, 1 .. 12 (2 m_sp + 1 <= 2N)                 */
+    double tau;    /* Gaussian parameter; 0 selects m_sp / N^2                       */
+    int32_t mode;  /* CT_FOURIER_FUSED or CT_FOURIER_GRIDDING                        */
+} ct_fourier_params;
+
+/* Builds the samples, weights and (fused mode) C on the current device.
+ * Errors: CT_ERR_ARG for bad sizes or parameters, CT_ERR_UNSUPPORTED for N not
+ * a power of two in [16, 2048], CT_ERR_OOM, CT_ERR_CUDA. */
+int ct_build_fourier(const ct_geometry *g, const ct_fourier_params *params, ct_matrix_t *out);
+
+/* y = F x: x[N*N] real image (row-major), y[2*J] complex samples (re, im
+ * interleaved).  Device pointers only (CT_ERR_ARG otherwise); asynchronous. */
+int ct_fourier_forward(ct_matrix_t F, const float *x, float *y, void *cuda_stream);
+
+/* x = Re(F^H y): y[2*J] complex, x[N*N] real.  Device pointers; asynchronous. */
+int ct_fourier_adjoint(ct_matrix_t F, const float *y, float *x, void *cuda_stream);
+
+/* out = Re(F^H F x) through the handle's mode (fused C or gridding pair).
+ * Device pointers; asynchronous. */
+int ct_fourier_normal(ct_matrix_t F, const float *x, float *out, void *cuda_stream);
+
+/* fhat = the DFTs of the projections: f[n_kept*n_bins] real sinogram,
+ * fhat[2*J] complex.  Device pointers; asynchronous. */
+int ct_fourier_data(ct_matrix_t F, const float *f, float *fhat, void *cuda_stream);
+
 /* Short description of a status code. */
 const char *ct_status_string(int status);
 

@@ -126,6 +126,7 @@ class Gridding:
         self.E = deconvolution(n, self.tau)
         self.phase = np.exp(-0.5j * (self.wx + self.wy))  # half-pixel centre offset
         self.G = self._interp_matrix()
+        self._C = None
 
     def _interp_matrix(self):
         """G[j, my * M_r + mx] = gx_j(mx) gy_j(my) over the window (indices wrapped)."""
@@ -171,8 +172,10 @@ class Gridding:
         return np.real(self.scale() * self.crop(P)).ravel()
 
     def fused_matrix(self):
-        """C = G^T G (Eq. fusedop's B* B), M_r^2 x M_r^2."""
-        return (self.G.T @ self.G).tocsr()
+        """C = G^T G (Eq. fusedop's B* B), M_r^2 x M_r^2 (formed once)."""
+        if self._C is None:
+            self._C = (self.G.T @ self.G).tocsr()
+        return self._C
 
     def normal_fused(self, mu, C=None):
         """Re(F^H F mu) evaluated as E Z^T FFT^H C FFT Z E mu (2 FFTs, one

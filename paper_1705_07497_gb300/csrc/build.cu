@@ -363,6 +363,11 @@ std::vector<AngleRow> angle_table(const ct_geometry& g, std::vector<double>& hc,
 
 }  // namespace
 
+void angle_directions(const ct_geometry& g, std::vector<double>& c, std::vector<double>& s)
+{
+    (void)angle_table(g, c, s);
+}
+
 void free_sell(Sell& c)
 {
     cudaFree(c.slice_ptr);
@@ -499,14 +504,18 @@ int make_stencil(ct_matrix* M, int r, int square, Stencil** out)
     }
     if (r <= 0 || r > 16) return fail(CT_ERR_ARG, "surrogate radius must be in [1, 16]");
     const int w = 2 * r + 1;
-    double* d_h = nullptr;
-    CT_CHECK(alloc_dev((void**)&d_h, (size_t)w * w * sizeof(double)));
-    point_response_kernel<<<w * w, 256>>>(M->g.n, M->g.n_bins, M->n_kept, (const AngleRow*)M->dirs, r, d_h);
-    CT_CUDA(cudaGetLastError());
     std::vector<double> h((size_t)w * w);
-    cudaError_t e = cudaMemcpy(h.data(), d_h, h.size() * sizeof(double), cudaMemcpyDeviceToHost);
-    cudaFree(d_h);
-    CT_CUDA(e);
+    if (M->fourier) {
+        fourier_point_response(M, r, h);
+    } else {
+        double* d_h = nullptr;
+        CT_CHECK(alloc_dev((void**)&d_h, (size_t)w * w * sizeof(double)));
+        point_response_kernel<<<w * w, 256>>>(M->g.n, M->g.n_bins, M->n_kept, (const AngleRow*)M->dirs, r, d_h);
+        CT_CUDA(cudaGetLastError());
+        cudaError_t e = cudaMemcpy(h.data(), d_h, h.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        cudaFree(d_h);
+        CT_CUDA(e);
+    }
     Stencil S;
     S.r = r;
     std::vector<float> wf;

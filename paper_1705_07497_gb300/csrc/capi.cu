@@ -1,4 +1,5 @@
 // extern "C" entry points of libct (declared and documented in include/ct.h).
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -49,6 +50,14 @@ int check_handle(ct_matrix_t A)
     if (dev != A->device)
         return fail(CT_ERR_ARG, "matrix lives on device " + std::to_string(A->device) +
                                     " but device " + std::to_string(dev) + " is current");
+    return CT_OK;
+}
+
+// Calls that need the Siddon matrices reject ct_build_fourier handles.
+int no_fourier(ct_matrix_t A, const char* what)
+{
+    if (A->fourier)
+        return fail(CT_ERR_UNSUPPORTED, std::string(what) + " is not available for a Fourier-operator handle");
     return CT_OK;
 }
 
@@ -121,12 +130,41 @@ int ct_build_matrix(const ct_geometry* g, uint32_t flags, ct_matrix_t* out)
     return CT_OK;
 }
 
+int ct_build_fourier(const ct_geometry* g, const ct_fourier_params* params, ct_matrix_t* out)
+{
+    if (!out) return fail(CT_ERR_ARG, "NULL output handle pointer");
+    *out = nullptr;
+    if (!g || !params) return fail(CT_ERR_ARG, "NULL geometry or params");
+    if (g->n <= 0 || g->n_angles_total <= 0 || g->keep_every <= 0 || g->n_bins <= 0)
+        return fail(CT_ERR_ARG, "geometry sizes must be positive");
+    const int64_t n_kept = (g->n_angles_total + g->keep_every - 1) / g->keep_every;
+    if (n_kept * g->n_bins >= ((int64_t)1 << 31)) return fail(CT_ERR_ARG, "kept angles * bins must be below 2^31");
+    CT_CHECK(check_fourier_params(*g, *params));
+    ct_matrix* M = new (std::nothrow) ct_matrix();
+    if (!M) return fail(CT_ERR_OOM, "host allocation failed");
+    M->g = *g;
+    M->flags = 0;
+    cudaError_t e = cudaGetDevice(&M->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&M->sm_count, cudaDevAttrMultiProcessorCount, M->device);
+    if (e != cudaSuccess) {
+        delete M;
+        return cuda_fail(e, "cudaGetDevice", __FILE__, __LINE__);
+    }
+    int rc = build_fourier(M, params);
+    if (rc != CT_OK) {
+        ct_destroy_matrix(M);
+        return rc;
+    }
+    *out = M;
+    return CT_OK;
+}
+
 int ct_matrix_info(ct_matrix_t A, int64_t* rows, int64_t* cols, int64_t* nnz)
 {
     if (!A) return fail(CT_ERR_ARG, "NULL matrix handle");
     if (rows) *rows = A->rows;
     if (cols) *cols = A->cols;
-    if (nnz) *nnz = A->A.nnz;
+    if (nnz) *nnz = A->fourier ? fourier_stored_weights(A) : A->A.nnz;
     return CT_OK;
 }
 
@@ -140,6 +178,7 @@ void ct_destroy_matrix(ct_matrix_t A)
     free_workspace(A->ws);
     for (auto& w : A->ws_pool) free_workspace(*w);
     for (auto& kv : A->stencils) free_stencil(kv.second);
+    free_fourier(A);
     free_sell(A->A);
     free_sell(A->At);
     cudaFree(A->row_scale);
@@ -155,6 +194,7 @@ void ct_destroy_matrix(ct_matrix_t A)
 int ct_forward(ct_matrix_t A, const float* x, float* y, int32_t batch, void* cuda_stream)
 {
     CT_CHECK(check_handle(A));
+    CT_CHECK(no_fourier(A, "ct_forward"));
     if (batch < 1) return fail(CT_ERR_ARG, "batch must be >= 1");
     int host = 0;
     CT_CHECK(classify(x, y, &host));
@@ -175,6 +215,7 @@ int ct_forward(ct_matrix_t A, const float* x, float* y, int32_t batch, void* cud
 int ct_adjoint(ct_matrix_t A, const float* y, float* x, int32_t batch, void* cuda_stream)
 {
     CT_CHECK(check_handle(A));
+    CT_CHECK(no_fourier(A, "ct_adjoint"));
     if (batch < 1) return fail(CT_ERR_ARG, "batch must be >= 1");
     int host = 0;
     CT_CHECK(classify(y, x, &host));
@@ -195,6 +236,7 @@ int ct_adjoint(ct_matrix_t A, const float* y, float* x, int32_t batch, void* cud
 int ct_forward_f64(ct_matrix_t A, const double* x, double* y, int32_t batch, void* cuda_stream)
 {
     CT_CHECK(check_handle(A));
+    CT_CHECK(no_fourier(A, "ct_forward_f64"));
     if (batch < 1) return fail(CT_ERR_ARG, "batch must be >= 1");
     int host = 0;
     CT_CHECK(classify(x, y, &host));
@@ -205,6 +247,7 @@ int ct_forward_f64(ct_matrix_t A, const double* x, double* y, int32_t batch, voi
 int ct_adjoint_f64(ct_matrix_t A, const double* y, double* x, int32_t batch, void* cuda_stream)
 {
     CT_CHECK(check_handle(A));
+    CT_CHECK(no_fourier(A, "ct_adjoint_f64"));
     if (batch < 1) return fail(CT_ERR_ARG, "batch must be >= 1");
     int host = 0;
     CT_CHECK(classify(y, x, &host));
@@ -291,6 +334,7 @@ int ct_split_bregman_ragged(int32_t count, const ct_matrix_t* A, const float* co
         return fail(CT_ERR_ARG, "split Bregman needs lambda > 0 and non-negative iteration counts");
     for (int32_t i = 0; i < count; ++i) {
         CT_CHECK(check_handle(A[i]));
+        CT_CHECK(no_fourier(A[i], "ct_split_bregman_ragged"));
         if (!f[i] || !u[i]) return fail(CT_ERR_ARG, "NULL vector pointer for problem " + std::to_string(i));
         if (!is_device_ptr(f[i]) || !is_device_ptr(u[i]))
             return fail(CT_ERR_ARG, "ct_split_bregman_ragged needs device pointers (problem " + std::to_string(i) + ")");
@@ -301,6 +345,7 @@ int ct_split_bregman_ragged(int32_t count, const ct_matrix_t* A, const float* co
 int ct_set_spmm_unroll(ct_matrix_t A, int32_t batch, int32_t unroll)
 {
     CT_CHECK(check_handle(A));
+    CT_CHECK(no_fourier(A, "ct_set_spmm_unroll"));
     if (batch < 2) return fail(CT_ERR_ARG, "batch must be >= 2 (batch 1 does not use the batched products)");
     if (unroll != 0 && unroll != 4 && unroll != 8) return fail(CT_ERR_ARG, "unroll must be 0, 4 or 8");
     if (unroll == 0)
@@ -322,6 +367,7 @@ int ct_get_spmm_unroll(ct_matrix_t A, int32_t batch, int32_t* unroll)
 int ct_matrix_export(ct_matrix_t A, int32_t which, int64_t* row_ptr, int32_t* cols, float* vals)
 {
     CT_CHECK(check_handle(A));
+    CT_CHECK(no_fourier(A, "ct_matrix_export"));
     if (which != 0 && which != 1) return fail(CT_ERR_ARG, "which must be 0 (A) or 1 (A^T)");
     if (!row_ptr || !cols || !vals) return fail(CT_ERR_ARG, "NULL output array");
     const Sell& C = which == 0 ? A->A : A->At;
@@ -398,6 +444,7 @@ int ct_matrix_export(ct_matrix_t A, int32_t which, int64_t* row_ptr, int32_t* co
 int ct_matrix_export_fp16(ct_matrix_t A, uint16_t* q_bits, float* scale)
 {
     CT_CHECK(check_handle(A));
+    CT_CHECK(no_fourier(A, "ct_matrix_export_fp16"));
     if (!(A->flags & CT_VAL_FP16_ROWSCALE)) return fail(CT_ERR_UNSUPPORTED, "matrix has no FP16 storage");
     if (!q_bits || !scale) return fail(CT_ERR_ARG, "NULL output array");
     const Sell& C = A->A;
@@ -430,6 +477,43 @@ int ct_surrogate_stencil(ct_matrix_t A, int32_t r, int32_t square, int32_t capac
         val[t] = S->h_w[t];
     }
     return CT_OK;
+}
+
+// Fourier-operator products: device pointers only, complex samples
+// interleaved (8-byte aligned).
+static int fourier_args(ct_matrix_t F, const void* a, const void* b, const void* complex_arg)
+{
+    CT_CHECK(check_handle(F));
+    if (!F->fourier) return fail(CT_ERR_UNSUPPORTED, "not a Fourier-operator handle (ct_build_fourier)");
+    if (!a || !b) return fail(CT_ERR_ARG, "NULL vector pointer");
+    if (!is_device_ptr(a) || !is_device_ptr(b)) return fail(CT_ERR_ARG, "the Fourier products need device pointers");
+    if (complex_arg && reinterpret_cast<uintptr_t>(complex_arg) % 8 != 0)
+        return fail(CT_ERR_ARG, "complex sample arrays must be 8-byte aligned");
+    return CT_OK;
+}
+
+int ct_fourier_forward(ct_matrix_t F, const float* x, float* y, void* cuda_stream)
+{
+    CT_CHECK(fourier_args(F, x, y, y));
+    return fourier_forward(F, x, y, (cudaStream_t)cuda_stream);
+}
+
+int ct_fourier_adjoint(ct_matrix_t F, const float* y, float* x, void* cuda_stream)
+{
+    CT_CHECK(fourier_args(F, y, x, y));
+    return fourier_adjoint(F, y, x, (cudaStream_t)cuda_stream);
+}
+
+int ct_fourier_normal(ct_matrix_t F, const float* x, float* out, void* cuda_stream)
+{
+    CT_CHECK(fourier_args(F, x, out, nullptr));
+    return fourier_normal(F, x, out, (cudaStream_t)cuda_stream);
+}
+
+int ct_fourier_data(ct_matrix_t F, const float* f, float* fhat, void* cuda_stream)
+{
+    CT_CHECK(fourier_args(F, f, fhat, fhat));
+    return fourier_data(F, f, fhat, (cudaStream_t)cuda_stream);
 }
 
 const char* ct_status_string(int status)

@@ -129,6 +129,8 @@ struct Workspace {
     int32_t ragged_cap = 0;
 };
 
+struct FourierOp;  // fourier.cu: the Fourier-domain data term of a ct_build_fourier handle
+
 }  // namespace ct
 
 struct ct_matrix {
@@ -158,12 +160,16 @@ struct ct_matrix {
     // extra single-slice workspaces: ct_split_bregman_ragged runs the
     // problems of a small group on one handle side by side
     std::vector<std::unique_ptr<ct::Workspace>> ws_pool;
+    // ct_build_fourier handles: the data term is Re(F^H F) (no Siddon matrices)
+    ct::FourierOp* fourier = nullptr;
 };
 
 namespace ct {
 
 // build.cu
 int build_matrices(ct_matrix* M);
+// cos, sin of the kept angles (theta exactly 0 or pi/2 snapped), FP64
+void angle_directions(const ct_geometry& g, std::vector<double>& c, std::vector<double>& s);
 void free_sell(Sell& c);
 int make_stencil(ct_matrix* M, int r, int square, Stencil** out);
 void free_stencil(Stencil& s);
@@ -257,5 +263,22 @@ int split_bregman_ragged(int32_t count, ct_matrix* const* A, const float* const*
                          const ct_sb_params* Sp, ct_sb_stats* stats, cudaStream_t st);
 int split_bregman_batched(ct_matrix* M, const ct_sb_params* P, const float* f, float* u, int32_t B,
                           ct_sb_stats* stats, cudaStream_t st);
+
+// fourier.cu: the Fourier-domain data term (Eqs. four_obj, fusedop)
+int check_fourier_params(const ct_geometry& g, const ct_fourier_params& P);
+int build_fourier(ct_matrix* M, const ct_fourier_params* P);
+void free_fourier(ct_matrix* M);
+int64_t fourier_stored_weights(const ct_matrix* M);
+// Re(F^H F) in (double-float, tiled) fused with the CG operator epilogue
+int launch_fourier_op_df(const ct_matrix* M, const OpEpilogue& ep, cudaStream_t st);
+// out (double-float, tiled) = scale Re(F^H fhat), fhat the DFTs of the real sinogram f
+int fourier_backproject_df(const ct_matrix* M, const float* f, float2* out, double scale, cudaStream_t st);
+// point response s(d) = Re(F^H F e_c)[c + d] for |di|, |dj| <= r, FP64 [(2r+1)^2]
+void fourier_point_response(const ct_matrix* M, int r, std::vector<double>& h);
+// public products (FP32, row-major image, interleaved complex samples)
+int fourier_forward(const ct_matrix* M, const float* x, float* y, cudaStream_t st);
+int fourier_adjoint(const ct_matrix* M, const float* y, float* x, cudaStream_t st);
+int fourier_normal(const ct_matrix* M, const float* x, float* out, cudaStream_t st);
+int fourier_data(const ct_matrix* M, const float* f, float* fhat, cudaStream_t st);
 
 }  // namespace ct

@@ -245,7 +245,9 @@ int apply_op(const Plan& P, OpEpilogue ep, const float2* in, cudaStream_t st, bo
 {
     Workspace& w = *P.w;
     ep.in = in;
-    if (P.sparse) {
+    if (P.sparse && P.M->fourier) {
+        CT_CHECK(launch_fourier_op_df(P.M, ep, st));
+    } else if (P.sparse) {
         const ValKind vk = fp32_refresh ? ValKind::F32 : P.vk;
         CT_CHECK(launch_forward_df(P.M, vk, in, w.y, vk == ValKind::F16 ? 2 : 0,
                                    ep.mode == 2 ? nullptr : ep.cg, ep.gate, st));
@@ -323,6 +325,15 @@ int make_plan(ct_matrix* M, Workspace* ws, double c_id, double c_ata, double c_g
     b.counter = w.counter;
     b.tol = tol;
     return CT_OK;
+}
+
+// w.atf = scale A^T f for a real sinogram f (double-float, tiled): the
+// Siddon adjoint, or Re(F^H fhat) of the data's DFTs on a Fourier handle.
+int backproject_data(ct_matrix* M, ValKind vk, const float* f, Workspace& w, double scale, cudaStream_t st)
+{
+    if (M->fourier) return fourier_backproject_df(M, f, w.atf, scale, st);
+    CT_CHECK(launch_to_df(M, f, vk == ValKind::F16 ? M->row_scale : nullptr, w.y, M->rows, st));
+    return launch_adjoint_df(M, vk, w.y, w.atf, scale, st);
 }
 
 }  // namespace
@@ -428,6 +439,7 @@ int cg_solve(ct_matrix* M, const ct_cg_params* Pp, const float* rhs, float* u, i
              ct_cg_stats* stats, cudaStream_t st)
 {
     if (Pp->max_iters < 0) return fail(CT_ERR_ARG, "max_iters < 0");
+    if (batch != 1 && M->fourier) return fail(CT_ERR_UNSUPPORTED, "the Fourier operator solves one slice per call");
     if (batch != 1) return cg_solve_batched(M, Pp, rhs, u, batch, stats, st);
     CT_CHECK(ensure_workspace(M, batch, true));
     return cg_solve_in(M, M->ws, Pp, rhs, u, stats, st);
@@ -481,9 +493,8 @@ int sb1_prepare(ct_matrix* M, Workspace& w, const ct_sb_params* Sp, const float*
     const int gv = grid_for(M, n2, 256, 8);
     // alpha A^T f, once (the right-hand side keeps the exact back-projection
     // also with the surrogate, Eq. surr_SBupd); FP16 storage applies A^T as
-    // Q^T (s .* f)
-    CT_CHECK(launch_to_df(M, f, P.vk == ValKind::F16 ? M->row_scale : nullptr, w.y, M->rows, st));
-    CT_CHECK(launch_adjoint_df(M, P.vk, w.y, w.atf, Sp->alpha, st));
+    // Q^T (s .* f); the Fourier data term back-projects the data's DFTs
+    CT_CHECK(backproject_data(M, P.vk, f, w, Sp->alpha, st));
     widen_kernel<<<gv, 256, 0, st>>>(u, w.u, M->g.n, M->tn);
     CT_CUDA(cudaGetLastError());
     CT_CUDA(cudaMemsetAsync(w.bx, 0, n2 * sizeof(float2), st));
@@ -584,6 +595,7 @@ int split_bregman(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u
 {
     if (!(Sp->lambda > 0.0) || Sp->outer_iters < 0 || Sp->inner_cg_iters < 0)
         return fail(CT_ERR_ARG, "split Bregman needs lambda > 0 and non-negative iteration counts");
+    if (batch != 1 && M->fourier) return fail(CT_ERR_UNSUPPORTED, "the Fourier operator solves one slice per call");
     if (batch != 1) return split_bregman_batched(M, Sp, f, u, batch, stats, st);
     Sb1Run* r = nullptr;
     CT_CHECK(sb1_prepare(M, M->ws, Sp, f, u, &r, st));
@@ -610,8 +622,7 @@ int chambolle_pock(ct_matrix* M, const ct_cp_params* Cp, const float* g, float* 
     const int64_t n2 = P.n2;
     const int gv = grid_for(M, n2, 256, 8);
     // tau alpha A^T g once; FP16 storage applies A^T as Q^T (s .* g)
-    CT_CHECK(launch_to_df(M, g, P.vk == ValKind::F16 ? M->row_scale : nullptr, w.y, M->rows, st));
-    CT_CHECK(launch_adjoint_df(M, P.vk, w.y, w.atf, ta, st));
+    CT_CHECK(backproject_data(M, P.vk, g, w, ta, st));
     widen_kernel<<<gv, 256, 0, st>>>(u, w.u, M->g.n, M->tn);
     CT_CUDA(cudaGetLastError());
     // ubar (vx) = u; dual (bx, by) = 0

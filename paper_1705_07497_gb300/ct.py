@@ -32,6 +32,9 @@ CT_VAL_FP32 = 0
 CT_VAL_FP16_ROWSCALE = 1
 CT_KEEP_FP32_COPY = 4
 
+CT_FOURIER_FUSED = 0
+CT_FOURIER_GRIDDING = 1
+
 SYMBOLS = (
     "ct_build_matrix",
     "ct_matrix_info",
@@ -50,6 +53,11 @@ SYMBOLS = (
     "ct_matrix_export",
     "ct_matrix_export_fp16",
     "ct_surrogate_stencil",
+    "ct_build_fourier",
+    "ct_fourier_forward",
+    "ct_fourier_adjoint",
+    "ct_fourier_normal",
+    "ct_fourier_data",
     "ct_status_string",
     "ct_last_error",
 )
@@ -109,6 +117,14 @@ class CpParams(ctypes.Structure):
     ]
 
 
+class FourierParams(ctypes.Structure):
+    _fields_ = [
+        ("m_sp", ctypes.c_int32),
+        ("tau", ctypes.c_double),
+        ("mode", ctypes.c_int32),
+    ]
+
+
 class SbStats(ctypes.Structure):
     _fields_ = [
         ("outer_done", ctypes.c_int32),
@@ -156,6 +172,11 @@ def lib():
         L.ct_matrix_export.argtypes = [vp, i32, vp, vp, vp]
         L.ct_matrix_export_fp16.argtypes = [vp, vp, vp]
         L.ct_surrogate_stencil.argtypes = [vp, i32, i32, i32, vp, vp, vp, P(i32)]
+        L.ct_build_fourier.argtypes = [P(Geometry), P(FourierParams), P(vp)]
+        L.ct_fourier_forward.argtypes = [vp, vp, vp, vp]
+        L.ct_fourier_adjoint.argtypes = [vp, vp, vp, vp]
+        L.ct_fourier_normal.argtypes = [vp, vp, vp, vp]
+        L.ct_fourier_data.argtypes = [vp, vp, vp, vp]
         L.ct_status_string.argtypes = [ctypes.c_int]
         L.ct_status_string.restype = ctypes.c_char_p
         L.ct_last_error.argtypes = []
@@ -320,6 +341,40 @@ def ct_surrogate_stencil(h, r, square=False):
     return {(int(a), int(b)): float(v) for a, b, v in zip(di, dj, w)}
 
 
+def ct_build_fourier(geometry, params):
+    h = ctypes.c_void_p()
+    _check(lib().ct_build_fourier(ctypes.byref(geometry), ctypes.byref(params), ctypes.byref(h)))
+    return h
+
+
+def ct_fourier_forward(h, x, y, stream=None):
+    """y (2J floats, complex interleaved) = F x."""
+    px, sx = _vec(x)
+    py, _ = _vec(y)
+    return _check(lib().ct_fourier_forward(h, px, py, sx if stream is None else stream))
+
+
+def ct_fourier_adjoint(h, y, x, stream=None):
+    """x = Re(F^H y)."""
+    py, sy = _vec(y)
+    px, _ = _vec(x)
+    return _check(lib().ct_fourier_adjoint(h, py, px, sy if stream is None else stream))
+
+
+def ct_fourier_normal(h, x, out, stream=None):
+    """out = Re(F^H F x)."""
+    px, sx = _vec(x)
+    po, _ = _vec(out)
+    return _check(lib().ct_fourier_normal(h, px, po, sx if stream is None else stream))
+
+
+def ct_fourier_data(h, f, fhat, stream=None):
+    """fhat (2J floats, complex interleaved) = DFTs of the sinogram's projections."""
+    pf, sf = _vec(f)
+    ph, _ = _vec(fhat)
+    return _check(lib().ct_fourier_data(h, pf, ph, sf if stream is None else stream))
+
+
 def _is_f64(x):
     dt = getattr(x, "dtype", None)
     return str(dt) in ("torch.float64", "float64")
@@ -412,6 +467,42 @@ class Matrix:
 
     def surrogate_stencil(self, r, square=False):
         return ct_surrogate_stencil(self.handle, r, square)
+
+
+class FourierMatrix(Matrix):
+    """The Fourier-domain data term of one geometry (Sec. 2, Eq. four_obj),
+    gridded with window half-width m_sp (Sec. 3.1) and, in fused mode, the
+    precomputed matrix of Eq. fusedop.  cg_solve, split_bregman,
+    chambolle_pock and surrogate_stencil work as on a Matrix (one slice);
+    forward/adjoint are the complex F and Re(F^H)."""
+
+    def __init__(self, n, n_angles_total, keep_every, n_bins, m_sp=6, tau=0.0, mode=CT_FOURIER_FUSED):
+        self.geometry = Geometry(n, n_angles_total, keep_every, n_bins)
+        self.flags = 0
+        self.params = FourierParams(m_sp, tau, mode)
+        self.handle = ct_build_fourier(self.geometry, self.params)
+        self.rows, self.cols, self.nnz = ct_matrix_info(self.handle)
+        self.n = n
+
+    def forward(self, x, y):
+        """y (2 * rows floats: complex samples, interleaved) = F x."""
+        ct_fourier_forward(self.handle, x, y)
+        return y
+
+    def adjoint(self, y, x):
+        """x = Re(F^H y)."""
+        ct_fourier_adjoint(self.handle, y, x)
+        return x
+
+    def normal(self, x, out):
+        """out = Re(F^H F x)."""
+        ct_fourier_normal(self.handle, x, out)
+        return out
+
+    def data(self, f, fhat):
+        """fhat (2 * rows floats) = the DFTs of the sinogram f's projections."""
+        ct_fourier_data(self.handle, f, fhat)
+        return fhat
 
 
 def split_bregman_ragged(matrices, fs, us, alpha, lam, outer, inner, stop_rel_update=0.0, surrogate_r=0,

@@ -50,6 +50,11 @@ WORKLOADS = {
     "ragged_64": dict(count=64, sizes=(128, 256, 512, 1024), angle_counts=(60, 120, 360, 900),
                       outer=50, inner=20, alpha=1.0, lam=1.0, noise="gauss", sigma_rel=0.01,
                       seed=4000, fp16=True),
+    # the 512x512 slice through the Fourier-domain data term: Gaussian gridding
+    # with window half-width 6 (six digits) and the fused matrix
+    "fourier_512": dict(n=512, n_angles_total=720, keep_every=4, n_bins=725, outer=50, inner=20,
+                        alpha=1.0, lam=1.0, noise="gauss", sigma_rel=0.01, seed=1000, m_sp=6,
+                        fourier_mode=0),
     # 16 slices of 256x256, 360 angles keeping every 2nd, 363 bins, 10 unrolled updates
     "grad_256x16": dict(n=256, n_angles_total=360, keep_every=2, n_bins=363, batch=16,
                         outer=10, inner=10, alpha=1.0, lam=1.0, noise="gauss", sigma_rel=0.01,

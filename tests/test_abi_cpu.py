@@ -95,3 +95,26 @@ def test_spmm_unroll_argument_errors(lib):
 def test_chambolle_pock_argument_errors(lib):
     p = ct.CpParams(1.0, 0.3, 0.3, 1.0, 3, 3)
     assert lib.ct_chambolle_pock(None, ctypes.byref(p), None, None, 1, None, None) == ct.CT_ERR_ARG
+
+
+@pytest.mark.parametrize(
+    "geom,params,code",
+    [
+        ((48, 40, 1, 68), (6, 0.0, 0), ct.CT_ERR_UNSUPPORTED),  # N not a power of two
+        ((8, 40, 1, 12), (2, 0.0, 0), ct.CT_ERR_UNSUPPORTED),   # N below 16
+        ((32, 40, 1, 46), (0, 0.0, 0), ct.CT_ERR_ARG),          # m_sp below 1
+        ((32, 40, 1, 46), (13, 0.0, 0), ct.CT_ERR_ARG),         # m_sp above 12
+        ((32, 40, 1, 46), (6, -1.0, 0), ct.CT_ERR_ARG),         # negative tau
+        ((32, 40, 1, 46), (6, 0.0, 7), ct.CT_ERR_ARG),          # unknown mode
+        ((32, 0, 1, 46), (6, 0.0, 0), ct.CT_ERR_ARG),           # bad geometry
+    ],
+)
+def test_fourier_argument_errors_without_a_gpu(lib, geom, params, code):
+    """ct_build_fourier validates sizes and parameters before any CUDA call."""
+    g = ct.Geometry(*geom)
+    p = ct.FourierParams(*params)
+    h = ctypes.c_void_p()
+    assert lib.ct_build_fourier(ctypes.byref(g), ctypes.byref(p), ctypes.byref(h)) == code
+    assert h.value is None
+    assert lib.ct_build_fourier(ctypes.byref(g), None, ctypes.byref(h)) == ct.CT_ERR_ARG
+    assert lib.ct_fourier_forward(None, None, None, None) == ct.CT_ERR_ARG
