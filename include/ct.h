@@ -303,9 +303,8 @@ int ct_surrogate_stencil(ct_matrix_t A, int32_t r, int32_t square, int32_t capac
  * offsets |d| <= 2 m_sp, so that one normal-operator product is two FFTs,
  * one product with C and two diagonal scalings.  Accuracy about 2, 6 and 12
  * digits at m_sp = 2, 6, 12 with tau = m_sp / N^2.  The grid and sample
- * vectors are carried in double-float; the FP32 tables (weights, twiddles,
- * C) perturb the operator by about 1e-7 relative, amplified towards the
- * corners of the frequency square by the deconvolution (about exp(m_sp)).
+ * vectors, the FFT twiddles and the pixel scaling are double-float; the
+ * weights and C are FP32 (a symmetric perturbation of about 1e-7 relative).
  *
  * The handle returned by ct_build_fourier works with ct_matrix_info
  * (rows = J, cols = N*N, nnz = stored weights: C's (4 m_sp + 1)^2 * 4N^2

@@ -21,8 +21,11 @@
 // weights.  The spread is a gather over the samples binned by cell (host
 // counting sort), so every sum has a fixed order and results are bitwise
 // reproducible.  The FFTs are radix-2 passes in shared memory, two
-// transforms per block, rows and then columns.  Tables (weights, phases,
-// twiddles, E) are computed on the host in FP64 and rounded once.
+// transforms per block, rows and then columns.  Tables are computed on the
+// host in FP64 and rounded once: the weights, the phases and C to FP32,
+// the FFT twiddles and the pixel scaling sqrt(c) E to double-float (a
+// fixed-count CG tolerates a symmetric FP32 perturbation of the weights,
+// but not a non-unitary FFT or a pixel scaling that is not separable).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -44,9 +47,9 @@ struct FourierOp {
     double tau = 0.0;
     int n_bins = 0, n_kept = 0;
     int64_t J = 0;
-    float c = 0.0f;               // 1 / (M_r^2 sqrt(n_bins))
+    double c = 0.0;               // 1 / (M_r^2 sqrt(n_bins))
     std::vector<double> h_wx, h_wy;  // sample frequencies (host, FP64)
-    float* E = nullptr;           // [n] E(i - n/2)
+    float2* sE = nullptr;         // [n] sqrt(c) E(i - n/2), double-float
     int2* base = nullptr;         // [J] floor point of each sample's window, per dimension
     float* wgt = nullptr;         // [J][2][win] 1-D weights along x, then y
     float2* phase = nullptr;      // [J] exp(-i (w_x + w_y) / 2)
@@ -130,11 +133,14 @@ __device__ __forceinline__ bool gated(const Gate& g)
     return g.need_active && g.cg && !g.cg->active;
 }
 
-// Image -> grid: X[k mod M_r] = (c E(k_y) E(k_x)) x(k), zero elsewhere.  DF
-// selects the solver's double-float tiled input, else a row-major FP32 image.
+// Image -> grid: X[k mod M_r] = sE(k_y) sE(k_x) x(k), zero elsewhere (sE =
+// sqrt(c) E in double-float: the pixel scaling must be separable to full
+// precision; per-pixel FP32 products sE_i sE_j perturb the operator enough
+// for a 20-step CG to drift by 6e-3).  DF selects the solver's double-float
+// tiled input, else a row-major FP32 image.
 template <bool DF>
 __global__ void __launch_bounds__(256) pad_kernel(const void* __restrict__ in, float4* __restrict__ X, int n,
-                                                  int tn, int mr, const float* __restrict__ E, float c, Gate g)
+                                                  int tn, int mr, const float2* __restrict__ sE, Gate g)
 {
     if (gated(g)) return;
     const int64_t len = (int64_t)mr * mr;
@@ -145,11 +151,9 @@ __global__ void __launch_bounds__(256) pad_kernel(const void* __restrict__ in, f
         float2 v = df_zero();
         if (ky >= -h && kx >= -h) {
             const int i = ky + h, j = kx + h;
-            const float s = c * E[i] * E[j];
-            if (DF)
-                v = df_mul_f(static_cast<const float2*>(in)[tiled_index(i, j, tn)], s);
-            else
-                v = two_prod(static_cast<const float*>(in)[(int64_t)i * n + j], s);
+            const float2 x = DF ? static_cast<const float2*>(in)[tiled_index(i, j, tn)]
+                                : make_float2(static_cast<const float*>(in)[(int64_t)i * n + j], 0.0f);
+            v = df_mul(df_mul(x, sE[i]), sE[j]);
         }
         X[m] = cdf(v, df_zero());
     }
@@ -398,7 +402,7 @@ __global__ void __launch_bounds__(256) sym_fused_kernel(float* __restrict__ C, i
 // the CG operator epilogue of `MODE`.
 template <int MODE>
 __global__ void __launch_bounds__(256) crop_op_kernel(OpEpilogue a, const float4* __restrict__ Y, int n, int tn,
-                                                      int64_t npad, int mr, const float* __restrict__ E, float c)
+                                                      int64_t npad, int mr, const float2* __restrict__ sE)
 {
     if (a.gate && *a.gate) return;
     if (MODE != 2 && !a.cg->active) return;
@@ -413,16 +417,16 @@ __global__ void __launch_bounds__(256) crop_op_kernel(OpEpilogue a, const float4
             continue;
         }
         const int my = (i - h + mr) % mr, mx = (j - h + mr) % mr;
-        const float2 v = df_mul_f(re_of(Y[(int64_t)my * mr + mx]), c * E[i] * E[j]);
+        const float2 v = df_mul(df_mul(re_of(Y[(int64_t)my * mr + mx]), sE[i]), sE[j]);
         op_epilogue<MODE>(a, n, tn, p, i, j, v, s0, c0, s1, c1);
     }
     op_finish<MODE>(a, s0, c0, s1, c1);
 }
 
-// Grid -> image: out = (cs E E) Re(Y), row-major FP32 or tiled double-float.
+// Grid -> image: out = scale sE sE Re(Y), row-major FP32 or tiled double-float.
 template <bool DF>
 __global__ void __launch_bounds__(256) crop_kernel(const float4* __restrict__ Y, void* __restrict__ out, int n,
-                                                   int tn, int mr, const float* __restrict__ E, float cs)
+                                                   int tn, int mr, const float2* __restrict__ sE, float2 scale)
 {
     const int h = n / 2;
     const int64_t len = DF ? padded_pixels(n) : (int64_t)n * n;
@@ -439,7 +443,7 @@ __global__ void __launch_bounds__(256) crop_kernel(const float4* __restrict__ Y,
             j = (int)(p - (int64_t)i * n);
         }
         const int my = (i - h + mr) % mr, mx = (j - h + mr) % mr;
-        const float2 v = df_mul_f(re_of(Y[(int64_t)my * mr + mx]), cs * E[i] * E[j]);
+        const float2 v = df_mul(df_mul(df_mul(re_of(Y[(int64_t)my * mr + mx]), sE[i]), sE[j]), scale);
         if (DF)
             static_cast<float2*>(out)[p] = v;
         else
@@ -584,7 +588,7 @@ void free_fourier(ct_matrix* M)
 {
     FourierOp* F = M->fourier;
     if (!F) return;
-    void* ps[] = {F->E, F->base, F->wgt, F->phase, F->cell_start, F->cell_idx, F->C, F->tw, F->sino_tw,
+    void* ps[] = {F->sE, F->base, F->wgt, F->phase, F->cell_start, F->cell_idx, F->C, F->tw, F->sino_tw,
                   F->X, F->Y, F->S};
     for (void* p : ps) cudaFree(p);
     delete F;
@@ -633,7 +637,7 @@ int build_fourier(ct_matrix* M, const ct_fourier_params* P)
     M->npad = padded_pixels(n);
     const int mr = F->mr, msp = F->msp, win = F->win, nb = g.n_bins;
     const int64_t J = F->J;
-    F->c = (float)(1.0 / ((double)mr * mr * std::sqrt((double)nb)));
+    F->c = 1.0 / ((double)mr * mr * std::sqrt((double)nb));
 
     // samples, windows and weights (FP64, rounded once)
     F->h_wx.resize(J);
@@ -675,10 +679,10 @@ int build_fourier(ct_matrix* M, const ct_fourier_params* P)
             cell_idx[fill[cell]++] = (int32_t)j;
         }
     }
-    std::vector<float> E(n);
+    std::vector<float2> sE(n);
     for (int i = 0; i < n; ++i) {
         const double k = (double)(i - n / 2);
-        E[i] = (float)(std::sqrt(kPi / F->tau) * std::exp(k * k * F->tau));
+        sE[i] = df_from_double(std::sqrt(F->c) * std::sqrt(kPi / F->tau) * std::exp(k * k * F->tau));
     }
     std::vector<float4> tw(mr / 2);
     std::vector<float2> stw(2 * nb);
@@ -691,7 +695,7 @@ int build_fourier(ct_matrix* M, const ct_fourier_params* P)
         const double a = kPi * q / nb;
         stw[q] = make_float2((float)std::cos(a), (float)-std::sin(a));
     }
-    CT_CHECK(upload(&F->E, E));
+    CT_CHECK(upload(&F->sE, sE));
     CT_CHECK(upload(&F->base, base));
     CT_CHECK(upload(&F->wgt, wgt));
     CT_CHECK(upload(&F->phase, phase));
@@ -733,16 +737,16 @@ int launch_fourier_op_df(const ct_matrix* M, const OpEpilogue& ep, cudaStream_t 
     const FourierOp& F = *M->fourier;
     const Gate g{ep.gate, ep.cg, ep.mode != 2};
     const int64_t len = (int64_t)F.mr * F.mr;
-    pad_kernel<true><<<grid_blocks(M, len), 256, 0, st>>>(ep.in, F.X, F.n, M->tn, F.mr, F.E, F.c, g);
+    pad_kernel<true><<<grid_blocks(M, len), 256, 0, st>>>(ep.in, F.X, F.n, M->tn, F.mr, F.sE, g);
     CT_CUDA(cudaGetLastError());
     CT_CHECK(fft2(F, F.X, false, g, st));
     CT_CHECK(grid_normal(M, F, g, st));
     CT_CHECK(fft2(F, F.Y, true, g, st));
     const int grid = grid_for(M, M->npad, 256, 8);
     switch (ep.mode) {
-    case 1: crop_op_kernel<1><<<grid, 256, 0, st>>>(ep, F.Y, F.n, M->tn, M->npad, F.mr, F.E, F.c); break;
-    case 2: crop_op_kernel<2><<<grid, 256, 0, st>>>(ep, F.Y, F.n, M->tn, M->npad, F.mr, F.E, F.c); break;
-    default: crop_op_kernel<3><<<grid, 256, 0, st>>>(ep, F.Y, F.n, M->tn, M->npad, F.mr, F.E, F.c); break;
+    case 1: crop_op_kernel<1><<<grid, 256, 0, st>>>(ep, F.Y, F.n, M->tn, M->npad, F.mr, F.sE); break;
+    case 2: crop_op_kernel<2><<<grid, 256, 0, st>>>(ep, F.Y, F.n, M->tn, M->npad, F.mr, F.sE); break;
+    default: crop_op_kernel<3><<<grid, 256, 0, st>>>(ep, F.Y, F.n, M->tn, M->npad, F.mr, F.sE); break;
     }
     CT_CUDA(cudaGetLastError());
     return CT_OK;
@@ -756,8 +760,8 @@ int fourier_backproject_df(const ct_matrix* M, const float* f, float2* out, doub
                                                                      F.phase);
     CT_CUDA(cudaGetLastError());
     CT_CHECK(spread_inverse(M, F, st));
-    crop_kernel<true><<<grid_for(M, M->npad, 256, 8), 256, 0, st>>>(F.Y, out, F.n, M->tn, F.mr, F.E,
-                                                                    (float)(scale * F.c));
+    crop_kernel<true><<<grid_for(M, M->npad, 256, 8), 256, 0, st>>>(F.Y, out, F.n, M->tn, F.mr, F.sE,
+                                                                    df_from_double(scale));
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -781,7 +785,7 @@ int fourier_forward(const ct_matrix* M, const float* x, float* y, cudaStream_t s
     const FourierOp& F = *M->fourier;
     const Gate none{nullptr, nullptr, 0};
     const int64_t len = (int64_t)F.mr * F.mr;
-    pad_kernel<false><<<grid_blocks(M, len), 256, 0, st>>>(x, F.X, F.n, M->tn, F.mr, F.E, F.c, none);
+    pad_kernel<false><<<grid_blocks(M, len), 256, 0, st>>>(x, F.X, F.n, M->tn, F.mr, F.sE, none);
     CT_CUDA(cudaGetLastError());
     CT_CHECK(fft2(F, F.X, false, none, st));
     interp_kernel<true><<<grid_blocks(M, F.J), 256, 0, st>>>(F.X, y, F.J, F.mr, F.msp, F.base,
@@ -796,7 +800,7 @@ int fourier_adjoint(const ct_matrix* M, const float* y, float* x, cudaStream_t s
     conj_phase_kernel<<<grid_blocks(M, F.J), 256, 0, st>>>(reinterpret_cast<const float2*>(y), F.S, F.phase, F.J);
     CT_CUDA(cudaGetLastError());
     CT_CHECK(spread_inverse(M, F, st));
-    crop_kernel<false><<<grid_blocks(M, M->cols), 256, 0, st>>>(F.Y, x, F.n, M->tn, F.mr, F.E, F.c);
+    crop_kernel<false><<<grid_blocks(M, M->cols), 256, 0, st>>>(F.Y, x, F.n, M->tn, F.mr, F.sE, df_from_double(1.0));
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -806,12 +810,12 @@ int fourier_normal(const ct_matrix* M, const float* x, float* out, cudaStream_t 
     const FourierOp& F = *M->fourier;
     const Gate none{nullptr, nullptr, 0};
     const int64_t len = (int64_t)F.mr * F.mr;
-    pad_kernel<false><<<grid_blocks(M, len), 256, 0, st>>>(x, F.X, F.n, M->tn, F.mr, F.E, F.c, none);
+    pad_kernel<false><<<grid_blocks(M, len), 256, 0, st>>>(x, F.X, F.n, M->tn, F.mr, F.sE, none);
     CT_CUDA(cudaGetLastError());
     CT_CHECK(fft2(F, F.X, false, none, st));
     CT_CHECK(grid_normal(M, F, none, st));
     CT_CHECK(fft2(F, F.Y, true, none, st));
-    crop_kernel<false><<<grid_blocks(M, M->cols), 256, 0, st>>>(F.Y, out, F.n, M->tn, F.mr, F.E, F.c);
+    crop_kernel<false><<<grid_blocks(M, M->cols), 256, 0, st>>>(F.Y, out, F.n, M->tn, F.mr, F.sE, df_from_double(1.0));
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
