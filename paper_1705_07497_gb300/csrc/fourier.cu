@@ -11,10 +11,11 @@
 // padding of the N x N image into the M_r = 2N grid (frequency k stored at
 // k mod M_r), FFT the unnormalised 2-D DFT and FFT^H its conjugate.
 //
-// GB300 layout: C is stored by diagonal, one plane of M_r^2 FP32 entries per
-// offset d in [-2 m_sp, 2 m_sp]^2 of the periodic grid, so a product with C
-// reads every plane once, coalesced, with the input tile and its halo staged
-// in shared memory; no column indices are stored.  Grid and sample vectors
+// GB300 layout: C is stored by diagonal, one FP32 entry per grid point and
+// offset d in [-2 m_sp, 2 m_sp]^2 of the periodic grid, no column indices,
+// ordered tile by tile (16 x 16 grid points, all offsets of a tile in one
+// contiguous run), so a block of the product streams one contiguous run
+// with its input tile and halo staged in shared memory.  Grid and sample vectors
 // are complex double-float (float4), accumulated with error-free
 // transformations; the FP32 tables are a fixed perturbation of the operator.  The gridding weights are
 // separable: a sample keeps its window's first point and 2 (2 m_sp + 1) FP32
@@ -55,7 +56,8 @@ struct FourierOp {
     float2* phase = nullptr;      // [J] exp(-i (w_x + w_y) / 2)
     int32_t* cell_start = nullptr;  // [M_r^2 + 1] samples binned by floor cell
     int32_t* cell_idx = nullptr;    // [J]
-    float* C = nullptr;           // [nd^2][M_r^2] fused matrix by diagonal
+    float* C = nullptr;           // fused matrix by diagonal, tile-major (see c_index)
+    uint8_t* tile_nz = nullptr;   // [(M_r/16)^2] 1 if a 16 x 16 tile has any nonzero of C
     float4* tw = nullptr;         // [M_r / 2] exp(-2 pi i k / M_r), double-float
     float2* sino_tw = nullptr;    // [2 n_bins] exp(-pi i q / n_bins)
     float4 *X = nullptr, *Y = nullptr, *S = nullptr;  // grid, grid, samples (complex double-float)
@@ -66,7 +68,7 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kFftThreads = 256;
-constexpr int kTile = 16;  // fused product: 16 x 16 grid points per block
+constexpr int kDiaTile = 16;  // fused product: 16 x 16 grid points per block
 // dynamic shared memory bounds: FFT 2 x (4096 + 1) complex double-float
 // points, fused product (16 + 48)^2 points, fused build 96 KB of accumulators
 constexpr int kFftSmemMax = 2 * 4097 * 16;
@@ -119,6 +121,16 @@ __device__ __forceinline__ float4 cacc_value(const CAcc& a)
     return cdf(acc_value(a.rs, a.rc), acc_value(a.is, a.ic));
 }
 
+// Position of the fused matrix's entry (m, m + d) for plane d (0 <= d < nd^2)
+// and grid point m = (my, mx): the 4N^2 grid in 16 x 16 tiles, and per tile
+// its nd^2 planes of 256 entries, so that a block of the product streams its
+// tile's coefficients as one contiguous run.
+__host__ __device__ __forceinline__ int64_t c_index(int64_t d, int my, int mx, int mr, int nd2)
+{
+    const int64_t tile = (int64_t)(my >> 4) * (mr >> 4) + (mx >> 4);
+    return ((tile * nd2 + d) << 8) + ((my & 15) << 4) + (mx & 15);
+}
+
 // Work of a solver product is skipped once the split-Bregman run has stopped
 // or (CG modes 1, 3) the slice has converged; the epilogue applies the same rule.
 struct Gate {
@@ -166,16 +178,20 @@ __global__ void __launch_bounds__(256) pad_kernel(const void* __restrict__ in, f
 // The twiddles are double-float: FP32 twiddles make the transform slightly
 // non-unitary, and the fixed-count CG of a later Bregman update amplifies
 // that perturbation by orders of magnitude.
+// keep > 0: only the transforms r < keep and r >= M_r - keep (the rows that
+// hold the zero-padded image, or the rows the crop reads) are computed; block
+// b takes the compact indices b T .. b T + T - 1.
 template <bool INV>
 __global__ void __launch_bounds__(kFftThreads) fft_kernel(float4* __restrict__ data, int lg, int T,
                                                           int64_t estride, int64_t rstride,
-                                                          const float4* __restrict__ tw, Gate g)
+                                                          const float4* __restrict__ tw, int keep, Gate g)
 {
     if (gated(g)) return;
     extern __shared__ float4 sbuf[];
     const int L = 1 << lg;
     const int pitch = L + 1;
-    const int64_t r0 = (int64_t)blockIdx.x * T;
+    int64_t r0 = (int64_t)blockIdx.x * T;
+    if (keep > 0 && r0 >= keep) r0 += L - 2 * keep;  // T divides keep: a block never straddles the gap
     const int total = T * L;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         int r, t;
@@ -223,19 +239,26 @@ __global__ void __launch_bounds__(kFftThreads) fft_kernel(float4* __restrict__ d
 
 // Y = C X with C by diagonal: Y[m] = sum_d C[d][m] X[(m + d) mod M_r].  A
 // block takes a 16 x 16 tile of grid points; the tile of X with its halo of
-// 2 m_sp on every side is staged in shared memory; every plane of C is read
-// once, coalesced (16 consecutive entries per row of the tile), in a fixed
-// order.
-__global__ void __launch_bounds__(256) dia_kernel(const float* __restrict__ C, const float4* __restrict__ X,
-                                                  float4* __restrict__ Y, int mr, int msp, Gate g)
+// 2 m_sp on every side is staged in shared memory; the tile's coefficients
+// are one contiguous run, read once in a fixed order.
+// Tiles whose rows of C are all zero (no sample within reach: the corners
+// of the frequency square outside the sampled disc) write zeros and read
+// nothing.
+__global__ void __launch_bounds__(256, 6) dia_kernel(const float* __restrict__ C, const float4* __restrict__ X,
+                                                  float4* __restrict__ Y, int mr, int msp,
+                                                  const uint8_t* __restrict__ tile_nz, Gate g)
 {
     if (gated(g)) return;
     extern __shared__ float4 xs[];
     const int nd = 4 * msp + 1, h = 2 * msp;
-    const int P = kTile + nd - 1;
-    const int64_t plane = (int64_t)mr * mr;
-    const int tiles = mr / kTile;
-    const int y0 = (blockIdx.x / tiles) * kTile, x0 = (blockIdx.x % tiles) * kTile;
+    const int P = kDiaTile + nd - 1;
+    const int tiles = mr / kDiaTile;
+    const int y0 = (blockIdx.x / tiles) * kDiaTile, x0 = (blockIdx.x % tiles) * kDiaTile;
+    if (!tile_nz[blockIdx.x]) {
+        const int64_t m = (int64_t)(y0 + threadIdx.x / kDiaTile) * mr + x0 + threadIdx.x % kDiaTile;
+        Y[m] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        return;
+    }
     for (int idx = threadIdx.x; idx < P * P; idx += blockDim.x) {
         const int ry = idx / P, cx = idx - ry * P;
         const int yy = (y0 - h + ry + 2 * mr) % mr;
@@ -243,14 +266,24 @@ __global__ void __launch_bounds__(256) dia_kernel(const float* __restrict__ C, c
         xs[idx] = X[(int64_t)yy * mr + xx];
     }
     __syncthreads();
-    const int ty = threadIdx.x / kTile, tx = threadIdx.x % kTile;
+    const int ty = threadIdx.x / kDiaTile, tx = threadIdx.x % kDiaTile;
     const int64_t m = (int64_t)(y0 + ty) * mr + x0 + tx;
+    // eight plane loads issued before their arithmetic, so that enough bytes
+    // are in flight to cover the memory latency
     CAcc acc;
+    const float* Ct = C + (((int64_t)blockIdx.x * nd * nd) << 8) + threadIdx.x;  // this tile's run
     for (int dy = 0; dy < nd; ++dy) {
-        const float* Cp = C + (int64_t)dy * nd * plane + m;
+        const float* Cp = Ct + (((int64_t)dy * nd) << 8);
         const float4* xr = xs + (ty + dy) * P + tx;
-#pragma unroll 4
-        for (int dx = 0; dx < nd; ++dx) cacc_fma(acc, __ldcs(Cp + (int64_t)dx * plane), xr[dx]);
+        int dx = 0;
+        for (; dx + 8 <= nd; dx += 8) {
+            float cv[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) cv[k] = __ldcs(Cp + ((dx + k) << 8));
+#pragma unroll
+            for (int k = 0; k < 8; ++k) cacc_fma(acc, cv[k], xr[dx + k]);
+        }
+        for (; dx < nd; ++dx) cacc_fma(acc, __ldcs(Cp + (dx << 8)), xr[dx]);
     }
     Y[m] = cacc_value(acc);
 }
@@ -337,7 +370,6 @@ __global__ void __launch_bounds__(256) build_fused_kernel(float* __restrict__ C,
 {
     extern __shared__ float2 acc[];
     const int win = 2 * msp + 1, nd = 4 * msp + 1, nd2 = nd * nd;
-    const int64_t plane = (int64_t)mr * mr;
     const int64_t m0 = (int64_t)blockIdx.x * G;
     for (int i = threadIdx.x; i < G * nd2; i += blockDim.x) acc[i] = make_float2(0.0f, 0.0f);
     __syncthreads();
@@ -371,8 +403,21 @@ __global__ void __launch_bounds__(256) build_fused_kernel(float* __restrict__ C,
     for (int i = threadIdx.x; i < G * nd2; i += blockDim.x) {
         const int d = i / G, gp = i - d * G;
         const float2 v = acc[gp * nd2 + d];
-        C[(int64_t)d * plane + m0 + gp] = acc_value(v.x, v.y).x;
+        const int64_t m = m0 + gp;
+        const int my = (int)(m / mr), mx = (int)(m - (int64_t)my * mr);
+        C[c_index(d, my, mx, mr, nd2)] = acc_value(v.x, v.y).x;
     }
+}
+
+// tile_nz[t] = 1 if any plane of C has a nonzero entry in 16 x 16 tile t.
+__global__ void __launch_bounds__(256) tile_nonzero_kernel(const float* __restrict__ C, int mr, int nd2,
+                                                           uint8_t* __restrict__ tile_nz)
+{
+    const float* Ct = C + (((int64_t)blockIdx.x * nd2) << 8) + threadIdx.x;
+    int nz = 0;
+    for (int d = 0; d < nd2 && !nz; ++d) nz = Ct[(int64_t)d << 8] != 0.0f;
+    nz = __syncthreads_or(nz);
+    if (threadIdx.x == 0) tile_nz[blockIdx.x] = (uint8_t)(nz != 0);
 }
 
 // Makes the fused matrix exactly symmetric: the entry (m, m + d) of plane d
@@ -391,10 +436,11 @@ __global__ void __launch_bounds__(256) sym_fused_kernel(float* __restrict__ C, i
         const int dy = (int)(dp / nd) - h, dx = (int)(dp % nd) - h;
         const int64_t dn = (int64_t)(-dy + h) * nd + (-dx + h);  // mirror plane
         const int my = (int)(m / mr), mx = (int)(m % mr);
-        const int64_t m2 = (int64_t)((my + dy + 2 * mr) % mr) * mr + (mx + dx + 2 * mr) % mr;
-        const float v = 0.5f * (C[dp * plane + m] + C[dn * plane + m2]);
-        C[dp * plane + m] = v;
-        C[dn * plane + m2] = v;
+        const int my2 = (my + dy + 2 * mr) % mr, mx2 = (mx + dx + 2 * mr) % mr;
+        const int64_t a = c_index(dp, my, mx, mr, nd * nd), b = c_index(dn, my2, mx2, mr, nd * nd);
+        const float v = 0.5f * (C[a] + C[b]);
+        C[a] = v;
+        C[b] = v;
     }
 }
 
@@ -526,21 +572,24 @@ size_t fft_smem(const FourierOp& F) { return (size_t)F.fft_T * (F.mr + 1) * size
 
 size_t dia_smem(const FourierOp& F)
 {
-    const size_t P = kTile + F.nd - 1;
+    const size_t P = kDiaTile + F.nd - 1;
     return P * P * sizeof(float4);
 }
 
 // 2-D FFT of a grid buffer in place (rows, then columns).
+// 2-D FFT of a grid buffer in place.  Forward: rows, then columns; only the
+// N rows that hold the zero-padded image need a row transform.  Inverse: the
+// mirror order, columns then rows, and only the N rows the crop reads.
 int fft2(const FourierOp& F, float4* data, bool inv, const Gate& g, cudaStream_t st)
 {
-    const int blocks = F.mr / F.fft_T;
+    const int all = F.mr / F.fft_T, half = F.n / F.fft_T, keep = F.n / 2;
     const size_t sm = fft_smem(F);
     if (inv) {
-        fft_kernel<true><<<blocks, kFftThreads, sm, st>>>(data, F.lg, F.fft_T, 1, F.mr, F.tw, g);
-        fft_kernel<true><<<blocks, kFftThreads, sm, st>>>(data, F.lg, F.fft_T, F.mr, 1, F.tw, g);
+        fft_kernel<true><<<all, kFftThreads, sm, st>>>(data, F.lg, F.fft_T, F.mr, 1, F.tw, 0, g);
+        fft_kernel<true><<<half, kFftThreads, sm, st>>>(data, F.lg, F.fft_T, 1, F.mr, F.tw, keep, g);
     } else {
-        fft_kernel<false><<<blocks, kFftThreads, sm, st>>>(data, F.lg, F.fft_T, 1, F.mr, F.tw, g);
-        fft_kernel<false><<<blocks, kFftThreads, sm, st>>>(data, F.lg, F.fft_T, F.mr, 1, F.tw, g);
+        fft_kernel<false><<<half, kFftThreads, sm, st>>>(data, F.lg, F.fft_T, 1, F.mr, F.tw, keep, g);
+        fft_kernel<false><<<all, kFftThreads, sm, st>>>(data, F.lg, F.fft_T, F.mr, 1, F.tw, 0, g);
     }
     CT_CUDA(cudaGetLastError());
     return CT_OK;
@@ -550,8 +599,8 @@ int fft2(const FourierOp& F, float4* data, bool inv, const Gate& g, cudaStream_t
 int grid_normal(const ct_matrix* M, const FourierOp& F, const Gate& g, cudaStream_t st)
 {
     if (F.mode == CT_FOURIER_FUSED) {
-        const int tiles = F.mr / kTile;
-        dia_kernel<<<tiles * tiles, kTile * kTile, dia_smem(F), st>>>(F.C, F.X, F.Y, F.mr, F.msp, g);
+        const int tiles = F.mr / kDiaTile;
+        dia_kernel<<<tiles * tiles, kDiaTile * kDiaTile, dia_smem(F), st>>>(F.C, F.X, F.Y, F.mr, F.msp, F.tile_nz, g);
     } else {
         interp_kernel<false><<<grid_blocks(M, F.J), 256, 0, st>>>(F.X, F.S, F.J, F.mr, F.msp, F.base, F.wgt,
                                                                   nullptr, g);
@@ -588,7 +637,7 @@ void free_fourier(ct_matrix* M)
 {
     FourierOp* F = M->fourier;
     if (!F) return;
-    void* ps[] = {F->sE, F->base, F->wgt, F->phase, F->cell_start, F->cell_idx, F->C, F->tw, F->sino_tw,
+    void* ps[] = {F->sE, F->base, F->wgt, F->phase, F->cell_start, F->cell_idx, F->C, F->tile_nz, F->tw, F->sino_tw,
                   F->X, F->Y, F->S};
     for (void* p : ps) cudaFree(p);
     delete F;
@@ -726,6 +775,10 @@ int build_fourier(ct_matrix* M, const ct_fourier_params* P)
         build_fused_kernel<<<(unsigned)blocks, 256, sm>>>(F->C, mr, msp, G, F->cell_start, F->cell_idx, F->wgt);
         CT_CUDA(cudaGetLastError());
         sym_fused_kernel<<<grid_blocks(M, (int64_t)mr * mr * ((F->nd * F->nd - 1) / 2)), 256>>>(F->C, mr, msp);
+        CT_CUDA(cudaGetLastError());
+        const int tiles = mr / kDiaTile;
+        CT_CHECK(alloc_bytes((void**)&F->tile_nz, (size_t)tiles * tiles));
+        tile_nonzero_kernel<<<tiles * tiles, kDiaTile * kDiaTile>>>(F->C, mr, F->nd * F->nd, F->tile_nz);
         CT_CUDA(cudaGetLastError());
     }
     CT_CUDA(cudaDeviceSynchronize());

@@ -161,3 +161,30 @@ def test_fourier_split_bregman_runs_on_the_system():
     b = tv.split_bregman(grid, fhat, (n, n), 1.0, 1.0, 2, 5, normal=grid.normal)
     assert _rel(b["u"], a["u"]) <= 1e-9
     assert a["updates"][0] > 0
+
+
+def _stencil_symbol_min(h, r, rr, square):
+    """min over frequencies of the symmetrised truncated stencil plus the
+    grad^T grad symbol (alpha = lambda = 1): the surrogate system's symbol."""
+    w = np.linspace(-math.pi, math.pi, 257)
+    WX, WY = np.meshgrid(w, w)
+    sym = 4.0 - 2.0 * np.cos(WX) - 2.0 * np.cos(WY)
+    for di in range(-rr, rr + 1):
+        for dj in range(-rr, rr + 1):
+            if square or di * di + dj * dj <= rr * rr:
+                sym = sym + 0.5 * (h[r + di, r + dj] + h[r - di, r - dj]) * np.cos(WX * dj + WY * di)
+    return float(sym.min())
+
+
+def test_truncated_fourier_point_response_definiteness():
+    """The Fourier normal operator's point response decays like 1/|d| (the
+    polar samples crowd the origin), so truncating it can make the surrogate
+    system indefinite: at N = 128 with N pi / 4 angles the disc of radius 1
+    and the windows of radius 3 are indefinite, the 3 x 3 square and the disc
+    of radius 2 are positive (the windows the experiment replay uses)."""
+    h = fo.point_response(128, 101, 1, 182, 3)
+    assert _stencil_symbol_min(h, 3, 1, False) < 0
+    assert _stencil_symbol_min(h, 3, 3, False) < 0
+    assert _stencil_symbol_min(h, 3, 3, True) < 0
+    assert _stencil_symbol_min(h, 3, 1, True) > 0
+    assert _stencil_symbol_min(h, 3, 2, False) > 0
