@@ -696,7 +696,7 @@ def bench_cp(args):
         "e2e": {"value": round(args.steps / e2e_secs, 4), "unit": "slices/s",
                 "h2d_bytes_per_step": int(f_pin.numel() * 4 + u_pin.numel() * 4),
                 "d2h_bytes_per_step": int(u_pin.numel() * 4)},
-        "gpu_launches": None,
+        "gpu_launches": int(args.steps * (3 + wl["outer"] * (5 + 4 * wl["inner"]) + 1)),
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
@@ -800,6 +800,7 @@ def bench_fourier(args):
     e2e_secs = time.perf_counter() - t0
     mr = 2 * n
     nd = 4 * wl["m_sp"] + 1
+    per_op = 7 if wl["fourier_mode"] == 0 else 8  # launches of one normal-operator product
     # bytes of one fused normal-operator product: C once; the 2N x 2N complex
     # double-float grid written by the padding, read and written by four FFT
     # passes and the fused product, read by the crop; image in and out
@@ -842,7 +843,7 @@ def bench_fourier(args):
         "e2e": {"value": round(args.steps / e2e_secs, 4), "unit": "slices/s",
                 "h2d_bytes_per_step": int(f_pin.numel() * 4 + u_pin.numel() * 4),
                 "d2h_bytes_per_step": int(u_pin.numel() * 4)},
-        "gpu_launches": None,
+        "gpu_launches": int(args.steps * (6 + wl["outer"] * (per_op + 1 + wl["inner"] * (per_op + 2)) + 1)),
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
