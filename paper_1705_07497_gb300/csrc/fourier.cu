@@ -15,18 +15,18 @@
 // offset d in [-2 m_sp, 2 m_sp]^2 of the periodic grid, no column indices,
 // ordered tile by tile (16 x 16 grid points, all offsets of a tile in one
 // contiguous run), so a block of the product streams one contiguous run
-// with its input tile and halo staged in shared memory.  Grid and sample vectors
-// are complex double-float (float4), accumulated with error-free
-// transformations; the FP32 tables are a fixed perturbation of the operator.  The gridding weights are
-// separable: a sample keeps its window's first point and 2 (2 m_sp + 1) FP32
-// weights.  The spread is a gather over the samples binned by cell (host
-// counting sort), so every sum has a fixed order and results are bitwise
-// reproducible.  The FFTs are radix-2 passes in shared memory, two
-// transforms per block, rows and then columns.  Tables are computed on the
-// host in FP64 and rounded once: the weights, the phases and C to FP32,
-// the FFT twiddles and the pixel scaling sqrt(c) E to double-float (a
-// fixed-count CG tolerates a symmetric FP32 perturbation of the weights,
-// but not a non-unitary FFT or a pixel scaling that is not separable).
+// with its input tile and halo staged in shared memory.  Grid and sample
+// vectors are complex double-float (float4), accumulated with error-free
+// transformations.  The gridding weights are separable: a sample keeps its
+// window's floor point and 2 (2 m_sp + 1) FP32 weights.  The spread is a
+// gather over the samples binned by cell (host counting sort), so every sum
+// has a fixed order and results are bitwise reproducible.  The FFTs are
+// radix-2 passes in shared memory, two transforms per block.  Tables are
+// computed on the host in FP64 and rounded once: the weights, the phases
+// and C to FP32, the FFT twiddles and the pixel scaling sqrt(c) E to
+// double-float (a fixed-count CG tolerates a symmetric FP32 perturbation of
+// the weights, but not a non-unitary FFT or a pixel scaling that is not
+// separable).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -78,8 +78,8 @@ constexpr int kBuildSmemMax = 96 * 1024;
 // ---- complex double-float values: float4 (re.hi, re.lo, im.hi, im.lo) ------
 // The grid and sample vectors of the solver's products are carried in
 // double-float: a fixed number of CG steps amplifies rounding that changes
-// from one product to the next, while the FP32 tables (weights, twiddles,
-// E, C) are a fixed perturbation of the operator.
+// from one product to the next, while the FP32 tables (weights, C) are a
+// fixed, symmetric perturbation of the operator.
 __device__ __forceinline__ float2 re_of(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 im_of(float4 v) { return make_float2(v.z, v.w); }
 __device__ __forceinline__ float4 cdf(float2 re, float2 im) { return make_float4(re.x, re.y, im.x, im.y); }
