@@ -20,7 +20,6 @@ import os
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 if "--_oracle-in" in sys.argv or "reference" in sys.argv:
