@@ -720,6 +720,122 @@ def bench_cp(args):
     M.close()
 
 
+def bench_kkt(args):
+    """p = 2 workload (Eq. KKT): one step = one solve of (alpha A^T A +
+    grad^T grad) u = alpha A^T f by a fixed number of CG steps from zero
+    through ct_cg_solve (A, A^T and the right-hand side resident)."""
+    import torch
+
+    from paper_1705_07497_gb300 import ct
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = inputs.WORKLOADS[args.workload]
+    n, iters, alpha = wl["n"], wl["cg_iters"], wl["alpha"]
+    M = ct.Matrix(n, wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
+    truth, f_host = make_data(wl, M, dev, wl["seed"])
+    f = torch.tensor(f_host, dtype=torch.float32, device=dev)
+    rhs = torch.empty(n * n, dtype=torch.float32, device=dev)
+    M.adjoint(f, rhs)
+    rhs *= alpha
+    u = torch.zeros(n * n, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        u.zero_()
+        return M.cg_solve(rhs, u, 0.0, alpha, 1.0, iters)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed_steps")
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    secs = e0.elapsed_time(e1) / 1e3
+    st = step()
+    rhs_pin = rhs.cpu().pin_memory()
+    u_pin = torch.zeros(n * n, dtype=torch.float32).pin_memory()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u_pin.zero_()
+        M.cg_solve(rhs_pin, u_pin, 0.0, alpha, 1.0, iters)
+    e2e_secs = time.perf_counter() - t0
+    # matrix bytes of one CG step (A p and the fused A^T product): SELL entries
+    # and row data of both matrices
+    step_bytes = M.nnz * (8 + 6) + (M.rows // 32 + 1) * 8 + M.rows * 4 + (n * n // 32 + 1) * 8 + n * n * 4
+    ms_cg = 1e3 * secs / args.steps / (iters + 1)
+    peak, peak_kind = measured_peak()
+    out = {
+        "metric": METRIC,
+        "value": round(args.steps / secs, 4),
+        "unit": "solves/s",
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1e3 * secs / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic: seeded random-ellipse phantom, projected by A, 1% Gaussian noise",
+        "config": {
+            "workload": args.workload + ": %dx%d slice, %d of %d angles, %d bins, p = 2 normal equations (alpha = %g, "
+                        "K = grad), %d CG steps from zero" % (n, n, M.rows // wl["n_bins"], wl["n_angles_total"],
+                                                             wl["n_bins"], alpha, iters),
+            "l2": "inputs larger than L2",
+        },
+        "roofline": {
+            "kernel": "one CG step (A p, A^T with the fused operator epilogue and p.q, two vector updates); matrix "
+                      "bytes only in the numerator",
+            "bound": "hbm",
+            "achieved": round(step_bytes / (ms_cg * 1e-3) / 1e9, 1),
+            "peak": peak,
+            "peak_kind": peak_kind,
+            "unit": "GB/s",
+            "frac": round(step_bytes / (ms_cg * 1e-3) / 1e9 / peak, 4),
+            "traffic": None,
+            "algorithmic_bytes": int(step_bytes),
+            "launch_ms": round(ms_cg, 4),
+        },
+        "final_rel_res": st["final_rel_res"],
+        "e2e": {"value": round(args.steps / e2e_secs, 4), "unit": "solves/s",
+                "h2d_bytes_per_step": int(rhs_pin.numel() * 4 + u_pin.numel() * 4),
+                "d2h_bytes_per_step": int(u_pin.numel() * 4)},
+        "gpu_launches": int(args.steps * (2 + 2 + 4 * iters + 1)),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        # the oracle on the first 10 CG steps of the same solve, timed, and the GPU against it
+        from oracle import radon, tv
+
+        A = radon.siddon_matrix(n, wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
+        k = 10
+        rhs64 = rhs.cpu().double().numpy()
+        op = tv.make_operator(A, (n, n), 0.0, alpha, 1.0)
+        t0 = time.perf_counter()
+        ref, _ = tv.cg(op, rhs64, np.zeros(n * n), k)
+        secs_cpu = time.perf_counter() - t0
+        u.zero_()
+        M.cg_solve(rhs, u, 0.0, alpha, 1.0, k)
+        got = u.cpu().double().numpy()
+        out["parity"] = {"after_%d_cg_steps" % k: float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+        out["cpu_baseline"] = {"value": round(k / iters / secs_cpu, 6), "unit": "solves/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": "%d of %d CG steps, FP64 numpy/scipy CSR, single-threaded; %.1f s"
+                                         % (k, iters, secs_cpu)}
+    print(json.dumps(out))
+    M.close()
+
+
 def bench_fourier(args):
     """Fourier-domain workload: one step = one split-Bregman reconstruction of
     the slice with the data term Re(F^H F) of Eq. SBFFT, evaluated by Gaussian
@@ -1132,6 +1248,8 @@ def main():
         bench_grad(args)
     elif args.workload.startswith("fourier_"):
         bench_fourier(args)
+    elif wl.get("solver") == "kkt":
+        bench_kkt(args)
     elif wl.get("solver") == "cp":
         bench_cp(args)
     elif wl.get("batch", 1) > 1:

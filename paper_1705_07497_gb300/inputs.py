@@ -38,6 +38,10 @@ WORKLOADS = {
     "cp_512": dict(n=512, n_angles_total=720, keep_every=4, n_bins=725, batch=1, solver="cp",
                    outer=50, inner=20, alpha=1.0, tau=0.35, sigma=0.35, theta=1.0, noise="gauss",
                    sigma_rel=0.01, seed=1000),
+    # the p = 2 normal equations (Eq. KKT) on the same slice: (alpha A^T A +
+    # grad^T grad) u = alpha A^T f by a fixed number of CG steps from zero
+    "kkt_512": dict(n=512, n_angles_total=720, keep_every=4, n_bins=725, batch=1, solver="kkt",
+                    cg_iters=200, alpha=1.0, noise="gauss", sigma_rel=0.01, seed=1000),
     # 256 slices of 512x512 on the same geometry, Poisson noise at 1e4 counts/bin,
     # FP16 storage with a per-row FP32 scale (no FP32 residual refresh: it
     # measured worse than none with double-float recurrences)
