@@ -315,7 +315,9 @@ int ct_surrogate_stencil(ct_matrix_t A, int32_t r, int32_t square, int32_t capac
  * ct_split_bregman and ct_chambolle_pock at batch 1, where c_ata multiplies
  * Re(F^H F) and the data vectors f, g stay real sinograms [n_kept][n_bins]
  * (transformed to fhat inside the call).  Every other call returns
- * CT_ERR_UNSUPPORTED for it.  N must be a power of two in [16, 2048]. */
+ * CT_ERR_UNSUPPORTED for it.  N must be a power of two in [16, 2048].
+ * The products and solves use the handle's grid and sample buffers, so calls
+ * on one handle must be serialised (one stream, or external ordering). */
 enum {
     CT_FOURIER_FUSED = 0,    /* precomputed C = G^T G (convolution fusing, Eq. fusedop) */
     CT_FOURIER_GRIDDING = 1  /* interpolate with G, then spread with G^T, each product */
