@@ -133,6 +133,19 @@ def test_sb_constant_image_is_a_fixed_point():
         assert np.abs(res[key]).max() <= 1e-13
 
 
+def test_sb_update_size_is_the_l1_norm_in_closed_form():
+    """Sec. 4 measures each Bregman update by its L1 norm.  With A = I and
+    constant data f = c on an n x 1 image, grad f = 0, so the first CG step
+    from u = 0 lands exactly on u = f (step size 1/alpha) and the residual is
+    zero: the first update is n |c| in L1 (sqrt(n) |c| in L2, n c if signed),
+    and the second is 0."""
+    n, c = 40, -0.5
+    A = sp.identity(n, format="csr")
+    res = tv.split_bregman(A, np.full(n, c), (n, 1), 2.0, 0.5, outer=2, inner=5)
+    np.testing.assert_array_equal(res["u"].ravel(), np.full(n, c))
+    assert res["updates"] == [n * abs(c), 0.0]
+
+
 def test_sb_limit_satisfies_tv_kkt_conditions():
     """At convergence z = lambda b certifies optimality of u for
     min alpha/2 ||A u - f||^2 + ||grad u||_1: |z| <= 1, z = sign(grad u) where
