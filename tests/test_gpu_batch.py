@@ -264,6 +264,37 @@ def test_batched_512_fp16_first_update(dev):
     M.close()
 
 
+def test_batched_512_fp16_256_slices_first_update(dev):
+    """The batched workload's own launch configuration: 256 slices of the
+    512x512 geometry, FP16 storage, Poisson noise at 1e4 counts (forward
+    products on half-warps with 32-slice chunks, adjoint products on paired
+    lanes with 64-slice chunks).  Sampled slices of the first Bregman update
+    against the oracle on the dequantised matrix (kernel error) and on the
+    FP64 matrix (storage error).  Every slice's data come from the oracle's
+    projection of one of the sampled slices' phantoms, with noise of its own."""
+    geom = (512, 720, 4, 725)
+    ref = oracle_A(*geom)
+    A16, _, _ = oracle_A16(*geom)
+    M = ct.Matrix(*geom, FP16)
+    B, sampled = 256, (0, 127, 255)
+    clean = {b: ref @ inputs.ellipse_phantom(512, 2000 + b).ravel() for b in sampled}
+    F = np.stack([inputs.poisson_noisy(clean[sampled[b % 3]] if b not in clean else clean[b], 1e4, 12000 + b)
+                  for b in range(B)], axis=1)
+    u = torch.zeros((M.cols, B), device=dev)
+    st = M.split_bregman(t32(F, dev), u, 1.0, 1.0, 1, 20)
+    assert st["status"] == 0 and st["outer_done"] == 1
+    got = u.cpu().numpy()
+    assert np.isfinite(got).all()
+    for b in sampled:
+        want16 = tv.split_bregman(A16, F[:, b], (512, 512), 1.0, 1.0, 1, 20)["u"].ravel()
+        want = tv.split_bregman(ref, F[:, b], (512, 512), 1.0, 1.0, 1, 20)["u"].ravel()
+        assert rel(got[:, b], want16) <= 1e-4, b
+        assert rel(got[:, b], want) <= 1e-3, b
+    # a slice sharing a phantom with a sampled one but not its noise differs from it
+    assert rel(got[:, 3], got[:, 0]) > 1e-4
+    M.close()
+
+
 def test_spmm_unroll_variants_are_bit_identical_and_tuned(dev):
     """The batched products' launch variants (4 or 8 staged entries in flight)
     give the same bits; without a pinned choice the first batched solve times
