@@ -158,6 +158,18 @@ def make_data(wl, M, dev, seed):
     return truth, noisy(wl, clean, seed + 1)
 
 
+def oracle_data(wl, seed):
+    """(oracle A, sinogram) for a parity comparison: the phantom and the noise
+    drawn as make_data draws them, projected by the oracle's FP64 matrix, so
+    that the input both sides take comes from the oracle, not the library.
+    Called only in the CPU-baseline legs."""
+    from oracle import radon
+
+    A = radon.siddon_matrix(wl["n"], wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
+    truth = inputs.ellipse_phantom(wl["n"], seed)
+    return A, noisy(wl, A @ truth.ravel(), seed + 1)
+
+
 def oracle_sample_main(args):
     """Runs in a fresh single-threaded interpreter: the oracle on ORACLE_UPDATES
     Bregman updates of the workload; writes the iterate after every update and
@@ -366,8 +378,10 @@ def bench_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        secs_cpu, u_oracle = run_oracle_sample(args.workload, f_host, ORACLE_UPDATES)
-        _, u_oracle32 = run_oracle_sample(args.workload, f_host, ORACLE_UPDATES, f32_values=True)
+        _, f_or = oracle_data(wl, replicas.rank_seed(wl["seed"], rank))
+        f_par = torch.tensor(f_or, dtype=torch.float32, device=dev)
+        secs_cpu, u_oracle = run_oracle_sample(args.workload, f_or, ORACLE_UPDATES)
+        _, u_oracle32 = run_oracle_sample(args.workload, f_or, ORACLE_UPDATES, f32_values=True)
 
         def rel(a, b):
             return float(np.linalg.norm(a - b) / np.linalg.norm(b))
@@ -375,7 +389,7 @@ def bench_ours(args):
         errs = {}
         for k in range(1, ORACLE_UPDATES + 1):
             u2 = torch.zeros(n * n, dtype=torch.float32, device=dev)
-            M.split_bregman(f, u2, wl["alpha"], wl["lam"], k, wl["inner"])
+            M.split_bregman(f_par, u2, wl["alpha"], wl["lam"], k, wl["inner"])
             got = u2.cpu().double().numpy()
             errs["after_%d_updates" % k] = {
                 "gpu_vs_oracle": rel(got, u_oracle[k - 1]),
@@ -700,15 +714,16 @@ def bench_cp(args):
     }
     if not args.no_cpu_baseline:
         # the oracle on the first two updates, timed, and the GPU against it
-        from oracle import radon, tv
+        from oracle import tv
 
-        A = radon.siddon_matrix(n, wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
+        A, f_or = oracle_data(wl, wl["seed"])
         t0 = time.perf_counter()
-        ref = tv.chambolle_pock(A, f_host, (n, n), wl["alpha"], wl["tau"], wl["sigma"], 2, wl["inner"],
+        ref = tv.chambolle_pock(A, f_or, (n, n), wl["alpha"], wl["tau"], wl["sigma"], 2, wl["inner"],
                                 theta=wl["theta"])
         secs_cpu = time.perf_counter() - t0
         u2 = torch.zeros(n * n, dtype=torch.float32, device=dev)
-        M.chambolle_pock(f, u2, wl["alpha"], wl["tau"], wl["sigma"], 2, wl["inner"], theta=wl["theta"])
+        M.chambolle_pock(torch.tensor(f_or, dtype=torch.float32, device=dev), u2, wl["alpha"], wl["tau"],
+                         wl["sigma"], 2, wl["inner"], theta=wl["theta"])
         got = u2.cpu().double().numpy()
         out["parity"] = {"after_2_updates": float(np.linalg.norm(got - ref["u"].ravel()) /
                                                    np.linalg.norm(ref["u"].ravel()))}
@@ -815,17 +830,19 @@ def bench_kkt(args):
     }
     if not args.no_cpu_baseline:
         # the oracle on the first 10 CG steps of the same solve, timed, and the GPU against it
-        from oracle import radon, tv
+        from oracle import tv
 
-        A = radon.siddon_matrix(n, wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
+        # the right-hand side alpha A^T f by the oracle, rounded to FP32 once,
+        # is the input of both solves
+        A, f_or = oracle_data(wl, wl["seed"])
         k = 10
-        rhs64 = rhs.cpu().double().numpy()
+        rhs32 = (alpha * (A.T @ f_or)).astype(np.float32)
         op = tv.make_operator(A, (n, n), 0.0, alpha, 1.0)
         t0 = time.perf_counter()
-        ref, _ = tv.cg(op, rhs64, np.zeros(n * n), k)
+        ref, _ = tv.cg(op, rhs32.astype(np.float64), np.zeros(n * n), k)
         secs_cpu = time.perf_counter() - t0
         u.zero_()
-        M.cg_solve(rhs, u, 0.0, alpha, 1.0, k)
+        M.cg_solve(torch.tensor(rhs32, device=dev), u, 0.0, alpha, 1.0, k)
         got = u.cpu().double().numpy()
         out["parity"] = {"after_%d_cg_steps" % k: float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
         out["cpu_baseline"] = {"value": round(k / iters / secs_cpu, 6), "unit": "solves/s", "cores": 1,
@@ -969,7 +986,8 @@ def bench_fourier(args):
         t0 = time.perf_counter()
         g = fo.Gridding(n, na, ke, nb, wl["m_sp"])
         S = fo.FourierSystem(n, na, ke, nb, gridding=g)
-        fhat = fo.sinogram_dft(f_host, radon.num_kept(na, ke), nb)
+        _, f_or = oracle_data(wl, wl["seed"])
+        fhat = fo.sinogram_dft(f_or, radon.num_kept(na, ke), nb)
         ref = tv.split_bregman(S, fhat, (n, n), wl["alpha"], wl["lam"], 1, wl["inner"], normal=g.normal)
         secs_cpu = time.perf_counter() - t0
         # the oracle with the weights and E rounded to FP32 as the library stores them
@@ -986,7 +1004,8 @@ def bench_fourier(args):
         for mode, key in ((wl["fourier_mode"], "after_1_update"), (1 - wl["fourier_mode"], "other_mode_after_1_update")):
             Fm = F if mode == wl["fourier_mode"] else ct.FourierMatrix(n, na, ke, nb, m_sp=wl["m_sp"], mode=mode)
             u1 = torch.zeros(n * n, dtype=torch.float32, device=dev)
-            Fm.split_bregman(f, u1, wl["alpha"], wl["lam"], 1, wl["inner"])
+            Fm.split_bregman(torch.tensor(f_or, dtype=torch.float32, device=dev), u1, wl["alpha"], wl["lam"], 1,
+                             wl["inner"])
             par[key] = rel_to_ref(u1.cpu().double().numpy())
             if Fm is not F:
                 Fm.close()
