@@ -1184,7 +1184,9 @@ def _time_kernel_fn(args, M, fn, dev, reps):
 
 
 def bench_reference(args):
-    """The FP64 CPU oracle as it stands, on host cores; rank 0 only."""
+    """The FP64 CPU oracle as it stands, on host cores; rank 0 only.  Each
+    timed step is a bounded sample of the workload's own solver: one Bregman
+    (or primal-dual) update, or 20 CG steps of the normal equations."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -1198,25 +1200,64 @@ def bench_reference(args):
     A = radon.siddon_matrix(n, wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
     truth = inputs.ellipse_phantom(n, wl["seed"])
     f = noisy(wl, A @ truth.ravel(), wl["seed"] + 1)
-    per_step = 1  # Bregman updates per timed step (1/50 of a reconstruction)
+    solver = "fourier" if args.workload.startswith("fourier_") else wl.get("solver", "sb")
+    geom = "%dx%d slice, %d of %d angles (keep every %d), %d bins" % (
+        n, n, -(-wl["n_angles_total"] // wl["keep_every"]), wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
+    first_of = "the first of %d problems: " % wl["count"] if "count" in wl else ""
+    unit = "slices/s"
+    if solver == "kkt":
+        per_step = 20  # CG steps per timed step
+        op = tv.make_operator(A, (n, n), 0.0, wl["alpha"], 1.0)
+        rhs = wl["alpha"] * (A.T @ f)
+
+        def step(state):
+            return tv.cg(op, rhs, np.zeros(n * n) if state is None else state, per_step)[0]
+
+        units_per_step = per_step / wl["cg_iters"]
+        unit = "solves/s"
+        desc = "%s, p = 2 normal equations, %d CG steps from zero" % (geom, wl["cg_iters"])
+        sample = "each step = %d of %d CG steps" % (per_step, wl["cg_iters"])
+    elif solver == "cp":
+        def step(state):
+            return tv.chambolle_pock(A, f, (n, n), wl["alpha"], wl["tau"], wl["sigma"], 1, wl["inner"],
+                                     theta=wl["theta"], u0=state)["u"].ravel()
+
+        units_per_step = 1 / wl["outer"]
+        desc = "%s, Chambolle-Pock %d x %d CG" % (geom, wl["outer"], wl["inner"])
+        sample = "each step = 1 of %d primal-dual updates (%d CG steps)" % (wl["outer"], wl["inner"])
+    else:
+        normal, data, Aop = None, f, A
+        if solver == "fourier":
+            from oracle import fourier as fo
+
+            g = fo.Gridding(n, wl["n_angles_total"], wl["keep_every"], wl["n_bins"], wl["m_sp"])
+            Aop = fo.FourierSystem(n, wl["n_angles_total"], wl["keep_every"], wl["n_bins"], gridding=g)
+            data = fo.sinogram_dft(f, radon.num_kept(wl["n_angles_total"], wl["keep_every"]), wl["n_bins"])
+            normal = g.normal
+
+        def step(state):
+            res = tv.split_bregman(Aop, data, (n, n), wl["alpha"], wl["lam"], 1, wl["inner"], normal=normal,
+                                   state=state)
+            return (res["u"], res["dx"], res["dy"], res["bx"], res["by"])
+
+        units_per_step = 1 / wl["outer"]
+        desc = workload_desc(wl) + (", Fourier-domain data term by gridding (M_sp = %d)" % wl["m_sp"]
+                                    if solver == "fourier" else "")
+        sample = "each step = 1 of %d Bregman updates (%d CG steps)" % (wl["outer"], wl["inner"])
+
     state = None
-
-    def step(state):
-        res = tv.split_bregman(A, f, (n, n), wl["alpha"], wl["lam"], per_step, wl["inner"], state=state)
-        return (res["u"], res["dx"], res["dy"], res["bx"], res["by"])
-
     for _ in range(args.warmup):
         state = step(state)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         state = step(state)
     secs = time.perf_counter() - t0
-    value = args.steps * per_step / wl["outer"] / secs
+    value = args.steps * units_per_step / secs
     print(json.dumps({
         "impl": "reference",
         "metric": METRIC,
         "value": round(value, 6),
-        "unit": "slices/s",
+        "unit": unit,
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
         "steps": args.steps,
         "warmup": args.warmup,
@@ -1225,14 +1266,12 @@ def bench_reference(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
-        "data": "synthetic: seeded random-ellipse phantom, projected by the oracle's A, 1% Gaussian noise",
-        "config": {"workload": WORKLOAD + ": " + workload_desc(wl),
-                   "sample": "each step = 1 of 50 Bregman updates (20 CG steps)"},
-        "cpu_baseline": {"value": round(value, 6), "unit": "slices/s", "cores": 1, "kind": "oracle",
-                         "sample": "each step = 1 of %d Bregman updates, FP64 numpy/scipy, one thread"
-                                   % wl["outer"]},
-        "e2e": {"value": round(value, 6), "unit": "slices/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0},
+        "data": "synthetic: seeded random-ellipse phantom, projected by the oracle's A, %s noise"
+                % ("1% Gaussian" if wl["noise"] == "gauss" else wl["noise"]),
+        "config": {"workload": args.workload + ": " + first_of + desc, "sample": sample},
+        "cpu_baseline": {"value": round(value, 6), "unit": unit, "cores": 1, "kind": "oracle",
+                         "sample": sample + ", FP64 numpy/scipy, one thread"},
+        "e2e": {"value": round(value, 6), "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
