@@ -58,7 +58,9 @@ enum {
     CT_ERR_OOM = -3,         /* device or host allocation failed                 */
     CT_ERR_BREAKDOWN = -4,   /* CG saw p^T Op p <= 0 with a nonzero residual     */
     CT_ERR_NONFINITE = -5,   /* NaN or Inf met in a residual, dot or update      */
-    CT_ERR_TIMEOUT = -6,     /* a bounded device-side wait expired               */
+    CT_ERR_TIMEOUT = -6,     /* reserved: a bounded device-side wait expired (no
+                              * kernel of this library waits on another, so no
+                              * call returns it today)                           */
     CT_ERR_UNSUPPORTED = -7  /* option not available for this matrix / build     */
 };
 
