@@ -39,6 +39,8 @@ MUTANTS = {
         ("r = r - a * q", "r = r + a * q")]),
     "cg_residual_ignores_warm_start": ("test_oracle_tv.py", "tv.py", [
         ("    r = rhs - op(u)\n", "    r = rhs.copy()\n")]),
+    "cg_tolerance_on_squared_norm": ("test_oracle_tv.py", "tv.py", [
+        ("np.sqrt(np.real(rr)) <= rel_tol * rhs_norm", "np.real(rr) <= rel_tol * rhs_norm")]),
     # ---- tv.py: split Bregman ----
     "shrink_half_threshold": ("test_oracle_tv.py", "tv.py", [
         ("np.abs(xr) > gamma, x - gamma * np.sign(xr)",
@@ -58,6 +60,10 @@ MUTANTS = {
     "sb_update_size_l2": ("test_oracle_tv.py", "tv.py", [
         ("updates.append(float(np.abs(u - u_old).sum()))",
          "updates.append(float(np.sqrt(((u - u_old) ** 2).sum())))")]),
+    "tv_objective_drops_half": ("test_oracle_tv.py", "tv.py", [
+        ("return 0.5 * alpha * float(res @ res)", "return alpha * float(res @ res)")]),
+    "stop_rule_against_previous_update": ("test_oracle_tv.py", "tv.py", [
+        ("updates[-1] < stop_rel_update * updates[0]", "updates[-1] < stop_rel_update * updates[-2]")]),
     # ---- tv.py: resolvent, Chambolle-Pock ----
     "resolvent_rhs_drops_tau": ("test_oracle_tv.py", "tv.py", [
         ("rhs = u_tilde.ravel() + tau * alpha * (A.T @ g)", "rhs = u_tilde.ravel() + alpha * (A.T @ g)")]),
@@ -85,6 +91,8 @@ MUTANTS = {
         ("factor = 0.5", "factor = 1.0")]),
     "quantize_scale_is_row_sum": ("test_oracle_radon.py", "radon.py", [
         ("np.maximum.reduceat(A.data", "np.add.reduceat(A.data")]),
+    "dequantize_drops_scale": ("test_oracle_radon.py", "radon.py", [
+        ("return sp.diags(s.astype(np.float64)) @ Qd", "return Qd")]),
     # ---- siddon.c ----
     "c_edge_full_length": ("test_oracle_radon.py", "siddon.c", [
         ("e[cnt].val = 0.5;", "e[cnt].val = 1.0;")]),
@@ -131,6 +139,19 @@ MUTANTS = {
         ("(self.G.T @ self.G)", "(self.G @ self.G.T)")]),
     "fused_skips_ifft": ("test_oracle_fourier.py", "fourier.py", [
         ("P = np.fft.ifft2((C @ h).reshape(m_r, m_r)) * (m_r * m_r)", "P = (C @ h).reshape(m_r, m_r)")]),
+    "fourier_point_response_unscaled": ("test_oracle_fourier.py", "fourier.py", [
+        ("np.cos(wx * dj + wy * di).sum() / n_bins", "np.cos(wx * dj + wy * di).sum()")]),
+    "default_tau_per_n": ("test_oracle_fourier.py", "fourier.py", [
+        ("return m_sp / float(n * n)", "return m_sp / float(n)")]),
+    "deconvolution_not_centred": ("test_oracle_fourier.py", "fourier.py", [
+        ("k = np.arange(n, dtype=np.float64) - n // 2\n    return math.sqrt",
+         "k = np.arange(n, dtype=np.float64)\n    return math.sqrt")]),
+    "grid_placement_not_centred": ("test_oracle_fourier.py", "fourier.py", [
+        ("k = (np.arange(n) - n // 2) % m_r", "k = np.arange(n) % m_r")]),
+    "exact_normal_drops_conj": ("test_oracle_fourier.py", "fourier.py", [
+        ("return np.real(self.F.conj().T @ (self.F @ mu))", "return np.real(self.F.T @ (self.F @ mu))")]),
+    "exact_adjoint_drops_conj": ("test_oracle_fourier.py", "fourier.py", [
+        ("return np.real(self.s.F.conj().T @ c)", "return np.real(self.s.F.T @ c)")]),
     "adjoint_drops_conj_phase": ("test_oracle_fourier.py", "fourier.py", [
         ("s = self.G.T @ (np.conj(self.phase) * np.asarray(c))", "s = self.G.T @ (self.phase * np.asarray(c))")]),
     "adjoint_keeps_imaginary_part": ("test_oracle_fourier.py", "fourier.py", [

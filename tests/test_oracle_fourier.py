@@ -113,12 +113,33 @@ def test_data_transform_and_operator_agree_on_a_pixel():
 
 
 def test_point_response_is_the_normal_operator_column():
+    """The closed form n_bins^-1 sum_j cos(omega_j . d) is column c of
+    Re(F^H F), and the exact system's normal operator applied to the unit
+    image at c (off the image centre, so a point reflection of the image
+    would show) gives that column."""
     n, geom = 16, (16, 24, 1, 23)
     F = fo.nudft_matrix(*geom)
     c = (n // 2) * n + n // 2
     col = np.real(F.conj().T @ F[:, c]).reshape(n, n)
     h = fo.point_response(*geom, 3)
-    assert np.abs(h - col[n // 2 - 3:n // 2 + 4, n // 2 - 3:n // 2 + 4]).max() <= 1e-13
+    win = (slice(n // 2 - 3, n // 2 + 4), slice(n // 2 - 3, n // 2 + 4))
+    assert np.abs(h - col[win]).max() <= 1e-13
+    e = np.zeros(n * n)
+    e[c] = 1.0
+    got = fo.FourierSystem(*geom).normal(e).reshape(n, n)
+    assert np.abs(h - got[win]).max() <= 1e-13
+
+
+def test_exact_system_adjoint_identity():
+    """Re <F mu, c> = <mu, Re(F^H c)> for a real image mu and complex c."""
+    geom = (16, 24, 1, 23)
+    S = fo.FourierSystem(*geom)
+    rng = np.random.default_rng(21)
+    mu = rng.standard_normal(16 * 16)
+    c = rng.standard_normal(24 * 23) + 1j * rng.standard_normal(24 * 23)
+    lhs = float(np.real(np.vdot(c, S @ mu)))
+    rhs = float(mu @ (S.T @ c))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
 
 
 def test_cg_on_the_fourier_system_solves_the_dense_normal_equations():
@@ -153,7 +174,8 @@ def test_fourier_split_bregman_runs_on_the_system():
     n = geom[0]
     A = radon.siddon_matrix(*geom)
     x = np.zeros((n, n))
-    x[5:11, 4:12] = 1.0
+    x[5:11, 3:12] = 1.0  # not symmetric about the image centre
+    x[6, 9] = 2.0
     fhat = fo.sinogram_dft(A @ x.ravel(), 24, 23)
     exact = fo.FourierSystem(*geom)
     grid = fo.FourierSystem(*geom, gridding=fo.Gridding(*geom, 12))

@@ -159,6 +159,21 @@ def test_quantize_rowscale_bounds():
     assert np.float16(1.0 + 2.0 ** -11).view(np.uint16) == 0x3C00  # tie -> even
 
 
+def test_dequantized_matrix_is_within_binary16_rounding_of_a():
+    """diag(s) Q reproduces A entry by entry within the rounding binary16 allows
+    (2^-11 relative, 2^-25 s absolute below the normal range), and every
+    nonempty row's largest entry is exactly its FP32 scale (Q = 1 there)."""
+    A = radon.siddon_matrix(32, 40, 2, 46)
+    s, Q = radon.quantize_rowscale(A)
+    D = radon.dequantize(s, Q).toarray()
+    Ad = A.toarray()
+    srow = s.astype(np.float64)[:, None]
+    assert np.all(np.abs(D - Ad) <= 2.0 ** -11 * np.abs(Ad) + 2.0 ** -25 * srow + 1e-15)
+    assert np.all((D != 0) <= (Ad != 0))
+    nonempty = np.diff(A.indptr) > 0
+    np.testing.assert_array_equal(D.max(axis=1)[nonempty], s[nonempty].astype(np.float64))
+
+
 @pytest.mark.parametrize("geom", [(16, 12, 1, 23), (33, 37, 2, 47), (64, 90, 3, 91)])
 def test_siddon_rows_equal_the_full_matrix(geom):
     """The per-ray entry point (used at sizes too large to build whole) returns

@@ -146,6 +146,34 @@ def test_sb_update_size_is_the_l1_norm_in_closed_form():
     assert res["updates"] == [n * abs(c), 0.0]
 
 
+def test_stop_rule_ends_at_the_first_update_below_tol_times_the_first():
+    """Sec. 4's stopping rule: the run ends after the first update whose L1
+    size is below tol times the first update's (not the previous one's: the
+    sizes here are not monotone), holding the uninterrupted run's iterate."""
+    n = 16
+    A = _small_problem(n)
+    f = A @ inputs.ellipse_phantom(n, 17).ravel()
+    full = tv.split_bregman(A, f, (n, n), 1.0, 0.5, outer=60, inner=5)
+    U = np.array(full["updates"])
+    tol = 0.05
+    k = int(np.argmax(U < tol * U[0])) + 1
+    assert 2 < k < 60 and np.any(np.diff(U[:k]) > 0)
+    stop = tv.split_bregman(A, f, (n, n), 1.0, 0.5, outer=60, inner=5, stop_rel_update=tol)
+    assert stop["outer_done"] == k and len(stop["updates"]) == k
+    part = tv.split_bregman(A, f, (n, n), 1.0, 0.5, outer=k, inner=5)
+    np.testing.assert_array_equal(stop["u"], part["u"])
+
+
+def test_tv_objective_in_closed_form():
+    """Eq. objmin with p = 1, K = grad (anisotropic), on a 2 x 2 image with
+    A = I, f = 1 and alpha = 2: the residual u - f = (0, 2, -1, -3) gives
+    (2/2) 14 = 14, the differences 3-1, -2-0 (along x) and 0-1, -2-3 (along
+    y) give 2 + 2 + 1 + 5 = 10."""
+    A = sp.identity(4, format="csr")
+    u = np.array([[1.0, 3.0], [0.0, -2.0]])
+    assert tv.tv_objective(A, np.ones(4), u, 2.0) == 24.0
+
+
 def test_sb_limit_satisfies_tv_kkt_conditions():
     """At convergence z = lambda b certifies optimality of u for
     min alpha/2 ||A u - f||^2 + ||grad u||_1: |z| <= 1, z = sign(grad u) where
