@@ -57,6 +57,8 @@ MUTANTS = {
         ("dy = shrink(gy + by, 1.0 / lam)", "dy = shrink(gy, 1.0 / lam)")]),
     "sb_data_term_unscaled": ("test_oracle_tv.py", "tv.py", [
         ("atf = alpha * (A.T @ f)", "atf = A.T @ f")]),
+    "sb_inner_cg_not_warm_started": ("test_oracle_tv.py", "tv.py", [
+        ("u, _ = cg(op, rhs, u_old, inner, rel_tol=cg_tol)", "u, _ = cg(op, rhs, np.zeros_like(u_old), inner, rel_tol=cg_tol)")]),
     "sb_update_size_l2": ("test_oracle_tv.py", "tv.py", [
         ("updates.append(float(np.abs(u - u_old).sum()))",
          "updates.append(float(np.sqrt(((u - u_old) ** 2).sum())))")]),
@@ -71,6 +73,11 @@ MUTANTS = {
         ("ut = u - tau * grad_adj(px, py).ravel()", "ut = u + tau * grad_adj(px, py).ravel()")]),
     "cp_dual_ascent_sign": ("test_oracle_tv.py", "tv.py", [
         ("px = np.clip(px + sigma * gx, -1.0, 1.0)", "px = np.clip(px - sigma * gx, -1.0, 1.0)")]),
+    "cp_extrapolates_from_old_iterate": ("test_oracle_tv.py", "tv.py", [
+        ("ubar = u_new + theta * (u_new - u)", "ubar = u + theta * (u_new - u)")]),
+    "cp_resolvent_not_warm_started": ("test_oracle_tv.py", "tv.py", [
+        ("u_new, _ = resolvent(A, shape, tau, alpha, ut, g, inner, u0=u)",
+         "u_new, _ = resolvent(A, shape, tau, alpha, ut, g, inner, u0=np.zeros_like(u))")]),
     # ---- tv.py: surrogate ----
     "point_response_off_centre": ("test_oracle_tv.py", "tv.py", [
         ("e[(n // 2) * n + n // 2] = 1.0", "e[(n // 2) * n + n // 2 - 1] = 1.0")]),

@@ -337,6 +337,19 @@ def test_chambolle_pock_reaches_the_split_bregman_minimiser_with_a_kkt_certifica
     assert np.abs(stat).max() <= 1e-7
 
 
+def test_chambolle_pock_two_steps_in_closed_form():
+    """Two primal-dual steps by hand on a 1 x 2 image with A = I, g = (0, 1),
+    alpha = 1, tau = sigma = 1/2 (each resolvent is (3/2) u = rhs, exact after
+    one CG step): u1 = (0, 1/3), extrapolated ubar1 = (0, 2/3), dual
+    p_x = clip(sigma 2/3) = 1/3, grad^T p = (-1/3, 1/3), u2 = ((1/6, 1/6) +
+    (0, 1/2)) / (3/2) = (1/9, 4/9).  Without the extrapolation u2 would be
+    (1/18, 1/2)."""
+    r = tv.chambolle_pock(sp.identity(2, format="csr"), np.array([0.0, 1.0]), (1, 2), 1.0, 0.5, 0.5, 2, 3)
+    np.testing.assert_allclose(r["u"].ravel(), [1.0 / 9.0, 4.0 / 9.0], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(r["px"].ravel(), [1.0 / 3.0, 0.0], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(r["updates"], [1.0 / 3.0, 2.0 / 9.0], rtol=1e-15)
+
+
 def test_chambolle_pock_constant_image_is_a_fixed_point():
     n = 16
     A = _small_problem(n)
