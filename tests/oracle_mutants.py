@@ -119,6 +119,18 @@ MUTANTS = {
         ("((double)m - 0.5 * n - x0) / dx", "((double)m - 0.5 * n + 0.5 - x0) / dx")]),
     "c_midpoint_lookup_off_by_one": ("test_oracle_radon.py", "siddon.c", [
         ("int j = (int)floor(x0 + tm * dx + half);", "int j = (int)floor(x0 + tm * dx + half + 0.5);")]),
+    "c_planes_not_reversed": ("test_oracle_radon.py", "siddon.c", [
+        ("    if (dx < 0) {\n        for (int a = 0, b = n; a < b; ++a, --b) {",
+         "    if (dx > 0) {\n        for (int a = 0, b = n; a < b; ++a, --b) {")]),
+    "c_boundary_rays_dropped": ("test_oracle_radon.py", "siddon.c", [
+        ("if (v < -half || v > half) return 0;", "if (v <= -half || v >= half) return 0;")]),
+    "c_angle_step_wrong": ("test_oracle_radon.py", "siddon.c", [
+        ("double th = (double)k * ORACLE_PI / (double)n_total;", "double th = (double)k * ORACLE_PI / (double)(n_total - 1);")]),
+    "c_keeps_wrong_angles": ("test_oracle_radon.py", "siddon.c", [
+        ("oracle_direction(kk * keep_every, n_total, &c, &s);\n        for (int b = 0; b < n_bins; ++b) {\n            const double sb = (double)b - 0.5 * (double)(n_bins - 1);\n            const int m = trace_ray(n, c, s, sb, e, tx, ty);\n            row_nnz",
+         "oracle_direction(kk, n_total, &c, &s);\n        for (int b = 0; b < n_bins; ++b) {\n            const double sb = (double)b - 0.5 * (double)(n_bins - 1);\n            const int m = trace_ray(n, c, s, sb, e, tx, ty);\n            row_nnz"),
+        ("oracle_direction(kk * keep_every, n_total, &c, &s);\n        for (int b = 0; b < n_bins; ++b) {\n            const double sb = (double)b - 0.5 * (double)(n_bins - 1);\n            const int m = trace_ray(n, c, s, sb, e, tx, ty);\n            const int64_t q",
+         "oracle_direction(kk, n_total, &c, &s);\n        for (int b = 0; b < n_bins; ++b) {\n            const double sb = (double)b - 0.5 * (double)(n_bins - 1);\n            const int m = trace_ray(n, c, s, sb, e, tx, ty);\n            const int64_t q")]),
     # ---- fourier.py ----
     "rho_centre_shifted": ("test_oracle_fourier.py", "fourier.py", [
         ("- (n_bins // 2)) / n_bins", "- (n_bins - 1) / 2.0) / n_bins")]),
