@@ -27,9 +27,10 @@ Readings taken where the paper is silent or garbled:
     unless given; 2-D kernel the product of 1-D Gaussians
     exp(-(x - eta)^2 / (4 tau)) of the nearest periodic image; deconvolution
     E(k) = sqrt(pi / tau) exp(k^2 tau) per dimension (the paper's diagonal
-    "A", Eq. fusedop).  The window: Sec. 3.1 writes both "the nearest 2 M_sp
-    points" and the set |m_j - m| <= M_sp with m_j = floor(x_j M_r / 2 pi);
-    the explicit set (2 M_sp + 1 points per dimension) is taken.
+    "A", Eq. fusedop).  The window: Sec. 3.1 describes it once as the 2 M_sp
+    grid points closest to a sample and once as the set |m_j - m| <= M_sp
+    with m_j = floor(x_j M_r / 2 pi); the explicit set (2 M_sp + 1 points per
+    dimension) is taken.
   * Convolution fusing (Eq. fusedop): with G the sample-by-grid matrix of
     kernel weights, F = c Phi G FFT Z E (Z zero padding, Phi the unit phases
     of the half-pixel centre offset, c = 1 / (M_r^2 n_bins^{1/2})) and the
