@@ -118,3 +118,46 @@ def test_fourier_argument_errors_without_a_gpu(lib, geom, params, code):
     assert h.value is None
     assert lib.ct_build_fourier(ctypes.byref(g), None, ctypes.byref(h)) == ct.CT_ERR_ARG
     assert lib.ct_fourier_forward(None, None, None, None) == ct.CT_ERR_ARG
+
+
+_STRUCTS = [
+    ("ct_geometry", "Geometry"),
+    ("ct_cg_params", "CgParams"),
+    ("ct_cg_stats", "CgStats"),
+    ("ct_sb_params", "SbParams"),
+    ("ct_sb_stats", "SbStats"),
+    ("ct_cp_params", "CpParams"),
+    ("ct_fourier_params", "FourierParams"),
+]
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    that a C compiler gives the struct of the same name in include/ct.h."""
+    import shutil
+    import subprocess
+
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "ct.h"', "int main(void) {"]
+    for cname, pyname in _STRUCTS:
+        lines.append('    printf("%s size %%zu\\n", sizeof(%s));' % (pyname, cname))
+        for fname, _ in getattr(ct, pyname)._fields_:
+            cf = "lambda" if fname == "lambda_" else fname
+            lines.append('    printf("%s %s %%zu\\n", offsetof(%s, %s));' % (pyname, fname, cname, cf))
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    seen = 0
+    for line in out:
+        if not line:
+            continue
+        pyname, what, value = line.split()
+        cls = getattr(ct, pyname)
+        want = ctypes.sizeof(cls) if what == "size" else getattr(cls, what).offset
+        assert int(value) == want, (pyname, what, int(value), want)
+        seen += 1
+    assert seen == sum(1 + len(getattr(ct, p)._fields_) for _, p in _STRUCTS)
