@@ -161,3 +161,20 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert int(value) == want, (pyname, what, int(value), want)
         seen += 1
     assert seen == sum(1 + len(getattr(ct, p)._fields_) for _, p in _STRUCTS)
+
+
+def test_binding_argument_counts_match_the_prototypes(lib):
+    """Each function the binding declares takes as many arguments as its
+    prototype in include/ct.h."""
+    text = open(os.path.join(ROOT, "include", "ct.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    protos = dict(re.findall(r"\b(ct_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", text))
+    checked = 0
+    for name, params in protos.items():
+        argtypes = getattr(lib, name).argtypes
+        if argtypes is None:
+            continue
+        n = 0 if params.strip() in ("", "void") else params.count(",") + 1
+        assert len(argtypes) == n, (name, len(argtypes), n)
+        checked += 1
+    assert checked >= len(protos) - 1
