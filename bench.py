@@ -158,16 +158,26 @@ def make_data(wl, M, dev, seed):
     return truth, noisy(wl, clean, seed + 1)
 
 
-def oracle_data(wl, seed):
+def single_problem(wl):
+    """The workload itself, or for a ragged workload its first problem (geometry
+    and seed merged into a copy of the workload)."""
+    if "count" not in wl:
+        return wl
+    n, a, d, nb, seed = inputs.ragged_problems(wl)[0]
+    return dict(wl, n=n, n_angles_total=a, keep_every=d, n_bins=nb, seed=seed)
+
+
+def oracle_data(wl, seed, noise_seed=None):
     """(oracle A, sinogram) for a parity comparison: the phantom and the noise
-    drawn as make_data draws them, projected by the oracle's FP64 matrix, so
-    that the input both sides take comes from the oracle, not the library.
-    Called only in the CPU-baseline legs."""
+    drawn as make_data draws them (noise seed: seed + 1 unless given),
+    projected by the oracle's FP64 matrix, so that the input both sides take
+    comes from the oracle, not the library.  Called only in the CPU-baseline
+    legs."""
     from oracle import radon
 
     A = radon.siddon_matrix(wl["n"], wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
     truth = inputs.ellipse_phantom(wl["n"], seed)
-    return A, noisy(wl, A @ truth.ravel(), seed + 1)
+    return A, noisy(wl, A @ truth.ravel(), seed + 1 if noise_seed is None else noise_seed)
 
 
 def oracle_sample_main(args):
@@ -176,7 +186,7 @@ def oracle_sample_main(args):
     prints the seconds taken."""
     from oracle import radon, tv
 
-    wl = inputs.WORKLOADS[args.workload]
+    wl = single_problem(inputs.WORKLOADS[args.workload])
     f = np.load(args.oracle_in)
     A = radon.siddon_matrix(wl["n"], wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
     if args.oracle_f32:
@@ -208,6 +218,20 @@ def run_oracle_sample(wl_name, f, updates, f32_values=False):
             capture_output=True, text=True, env=env, check=True)
         secs = json.loads(out.stdout.strip().splitlines()[-1])["seconds"]
         return secs, np.load(fout)
+
+
+def oracle_slice_baseline(wl_name, seed, noise_seed, note=""):
+    """cpu_baseline of a workload whose GPU step solves many slices or
+    problems: the oracle, in a fresh single-threaded interpreter, on the first
+    Bregman update of one of them (phantom `seed`, noise `noise_seed`, the
+    sinogram projected by the oracle's matrix), as slices/s of a whole
+    reconstruction."""
+    wl = single_problem(inputs.WORKLOADS[wl_name])
+    _, f = oracle_data(wl, seed, noise_seed)
+    secs, _ = run_oracle_sample(wl_name, f, 1)
+    return {"value": round(1 / wl["outer"] / secs, 6), "unit": "slices/s", "cores": 1, "kind": "oracle",
+            "sample": "1 of %d Bregman updates (%d CG steps) of one %dx%d problem, FP64 numpy/scipy CSR, one "
+                      "thread; %.1f s%s" % (wl["outer"], wl["inner"], wl["n"], wl["n"], secs, note)}
 
 
 def bench_ours(args):
@@ -534,6 +558,9 @@ def bench_batch(args):
         "gpu_launches": None,
         "clocks": clocks,
     }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_slice_baseline(args.workload, wl["seed"], wl["seed"] + 10000,
+                                                    " (slice 0, on the unquantised FP64 matrix)")
     print(json.dumps(out))
     M.close()
 
@@ -603,7 +630,7 @@ def bench_grad(args):
     mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak = sm_count(dev) * 2 * mhz * 1e6 / 1e12
     ach = M.nnz * B / t_f64 / 1e12
-    print(json.dumps({
+    out = {
         "metric": METRIC,
         "value": round(B * args.steps / secs, 4),
         "unit": "slices/s",
@@ -637,7 +664,12 @@ def bench_grad(args):
         "e2e": None,
         "gpu_launches": None,
         "clocks": clocks,
-    }))
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_slice_baseline(args.workload, wl["seed"], wl["seed"] + 100,
+                                                    " (slice 0, the forward pass only: the oracle has no "
+                                                    "reverse-mode gradient)")
+    print(json.dumps(out))
     M.close()
 
 
@@ -1115,6 +1147,10 @@ def bench_ragged(args):
         "gpu_launches": None,
         "clocks": clocks,
     }
+    if not args.no_cpu_baseline:
+        s0 = probs[0][4]
+        out["cpu_baseline"] = oracle_slice_baseline(args.workload, s0, s0 + 10000,
+                                                    " (problem 0 only, on the unquantised FP64 matrix)")
     print(json.dumps(out))
     for M in mats.values():
         M.close()
@@ -1192,10 +1228,7 @@ def bench_reference(args):
         return
     from oracle import radon, tv
 
-    wl = dict(inputs.WORKLOADS[args.workload])
-    if "count" in wl:  # ragged: the oracle on its first problem
-        n, a, d, nb, seed = inputs.ragged_problems(wl)[0]
-        wl.update(n=n, n_angles_total=a, keep_every=d, n_bins=nb, seed=seed)
+    wl = dict(single_problem(inputs.WORKLOADS[args.workload]))  # ragged: the oracle on its first problem
     n = wl["n"]
     A = radon.siddon_matrix(n, wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
     truth = inputs.ellipse_phantom(n, wl["seed"])

@@ -40,3 +40,21 @@ def test_reference_arm_other_ranks_do_no_work():
     p = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert p.returncode == 0, p.stderr[-2000:]
     assert p.stdout.strip() == ""
+
+
+def test_many_slice_workloads_time_the_oracle_on_one_problem():
+    """The CPU baseline of the batched, ragged and differentiable workloads:
+    the oracle in a single-threaded child on one problem's first update; for
+    the ragged workload that problem is its first draw."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1705_07497_gb300 import inputs
+
+    wl = inputs.WORKLOADS["ragged_64"]
+    one = bench.single_problem(wl)
+    n, a, d, nb, seed = inputs.ragged_problems(wl)[0]
+    assert (one["n"], one["n_angles_total"], one["keep_every"], one["n_bins"], one["seed"]) == (n, a, d, nb, seed)
+    assert bench.single_problem(inputs.WORKLOADS["grad_256x16"]) is inputs.WORKLOADS["grad_256x16"]
+    cb = bench.oracle_slice_baseline("grad_256x16", 3000, 3100, " (note)")
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["unit"] == "slices/s"
+    assert cb["value"] > 0 and cb["sample"].endswith("(note)")
