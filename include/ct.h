@@ -275,7 +275,14 @@ int ct_matrix_export_fp16(ct_matrix_t A, uint16_t *q_bits, float *scale);
  * (0-based) and offsets d = (di, dj) in the window (disc |d|_2 <= r, or square
  * when square != 0), averaged with s(-d) so that T is symmetric; computed in
  * FP64.  Writes up to `capacity` taps (di[], dj[], val[], host arrays) and the
- * number of taps to *count.  Synchronous. */
+ * number of taps to *count.  Synchronous.
+ * For the Siddon operator the point response decays like 1/|d| (a point
+ * back-projects along every kept angle), so the window keeps a small part of
+ * the response of A^T A to smooth images, and a surrogate solve returns an
+ * image whose smooth part is too large by about sum(h) / sum(s), where h is
+ * the whole point response and s the window's taps (about 290 for r = 1 at
+ * N = 512 with 180 angles); small windows can also make the surrogate system
+ * indefinite, which CG reports as CT_ERR_BREAKDOWN. */
 int ct_surrogate_stencil(ct_matrix_t A, int32_t r, int32_t square, int32_t capacity,
                          int32_t *di, int32_t *dj, double *val, int32_t *count);
 
