@@ -270,6 +270,26 @@ def test_surrogate_reconstruction_is_less_accurate_and_improves_with_r():
     assert errs[1] < errs[0]
 
 
+@pytest.mark.parametrize("r", [1, 3])
+def test_surrogate_image_mass_follows_the_dropped_response(r):
+    """Why the surrogate misses in this setting: summing the surrogate system
+    over all pixels (1^T grad^T = 0) gives sum(s) * sum(u) ~ sum over pixels of
+    (A^T A 1) times the phantom ~ sum(h) * sum(truth) for an object away from
+    the edges, so the reconstruction's mass is sum(h) / sum(s) times the
+    phantom's (h the whole point response, s the window's taps)."""
+    n = 64
+    A = radon.siddon_matrix(n, 90, 3, 91)
+    truth = inputs.ellipse_phantom(n, 0)
+    f = A @ truth.ravel()
+    h = tv.point_response(A, n)
+    taps = tv.surrogate_stencil(h, r)
+    T = tv.surrogate_matrix(taps, n)
+    u = tv.split_bregman(A, f, (n, n), 1.0, 1.0, 20, 10, normal=lambda x: T @ x)["u"]
+    ratio = h.sum() / sum(taps.values())
+    assert ratio > 10.0
+    assert abs(u.sum() / truth.sum() / ratio - 1.0) <= 0.1
+
+
 def _complex_step(A, f, shape, alpha, lam, outer, inner, w, d, h=1e-30):
     u = tv.split_bregman(A, f + 1j * h * d, shape, alpha, lam, outer, inner)["u"].ravel()
     return float(np.imag(w @ u)) / h
