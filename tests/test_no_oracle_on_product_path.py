@@ -62,3 +62,15 @@ def test_bench_touches_the_oracle_only_in_its_oracle_legs():
     # and the guarded legs exist: the check is not vacuous
     text = open(os.path.join(ROOT, "bench.py")).read()
     assert text.count("not args.no_cpu_baseline") >= 5
+
+
+def test_oracle_does_not_import_the_library():
+    """The other direction: nothing under oracle/ imports the package or
+    includes its CUDA sources or headers (the two share no code; the oracle
+    takes its inputs as arguments)."""
+    odir = os.path.join(ROOT, "oracle")
+    for name in os.listdir(odir):
+        if name.endswith((".py", ".c", ".h")):
+            text = open(os.path.join(odir, name)).read()
+            assert "paper_1705_07497_gb300" not in text, name
+            assert not re.search(r'#include\s+"', text), name
