@@ -248,9 +248,15 @@ int ct_get_spmm_unroll(ct_matrix_t A, int32_t batch, int32_t *unroll);
  *     plus 8 per sinogram sample; N = 512 with 130,500 rays fits) are rejected
  *     with CT_ERR_ARG and a message giving the size needed.
  *   - rhs and u must be device pointers (host staging would allocate).
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current) and caches it; make that
- *     first call before any stream capture.
+ *   - The runtime backs the array on a device when it first loads the
+ *     library's device code there.  ct_build_matrix and ct_build_fourier do
+ *     that on the handle's device (they look up the array's address with
+ *     cudaGetSymbolAddress), so the array is committed while allocating is
+ *     still allowed.  If the device had no room then, the first call of this
+ *     entry point on that device tries again and returns CT_ERR_OOM when it
+ *     still cannot; make that first call before any stream capture.  Every
+ *     call looks the address up again (with the handle's device current), so
+ *     no stale address survives a device reset.
  *   - All calls share the one array and it keeps the last call's contents:
  *     the call clears what must start at zero itself, but calls whose work
  *     overlaps on the GPU (other streams, other threads) race on it; serialise

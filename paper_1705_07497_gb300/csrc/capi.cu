@@ -126,6 +126,7 @@ int ct_build_matrix(const ct_geometry* g, uint32_t flags, ct_matrix_t* out)
         ct_destroy_matrix(M);
         return rc;
     }
+    noalloc_reserve();  // commit ct_cg_solve_noalloc's scratch while allocating is allowed
     *out = M;
     return CT_OK;
 }
@@ -155,6 +156,7 @@ int ct_build_fourier(const ct_geometry* g, const ct_fourier_params* params, ct_m
         ct_destroy_matrix(M);
         return rc;
     }
+    noalloc_reserve();  // commit ct_cg_solve_noalloc's scratch while allocating is allowed
     *out = M;
     return CT_OK;
 }

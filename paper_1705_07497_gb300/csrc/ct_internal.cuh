@@ -264,6 +264,10 @@ int split_bregman_ragged(int32_t count, ct_matrix* const* A, const float* const*
 int split_bregman_batched(ct_matrix* M, const ct_sb_params* P, const float* f, float* u, int32_t B,
                           ct_sb_stats* stats, cudaStream_t st);
 
+// noalloc.cu: commit the allocation-free entry point's scratch array on the
+// current device (best effort)
+void noalloc_reserve();
+
 // fourier.cu: the Fourier-domain data term (Eqs. four_obj, fusedop)
 int check_fourier_params(const ct_geometry& g, const ct_fourier_params& P);
 int build_fourier(ct_matrix* M, const ct_fourier_params* P);

@@ -6,10 +6,14 @@
 // The scratch is one file-scope __device__ array.  Every device that loads
 // the library holds it until the process exits.  Host code cannot use the
 // array's name as a device address (on the host it names a stand-in object),
-// so the first call on each device asks the runtime for the device address
-// with cudaGetSymbolAddress, with that device current, and caches it.
+// so the address is asked of the runtime with cudaGetSymbolAddress, with the
+// device current.  The runtime loads a module's device image (and with it
+// backs this array) on its first use, so the matrix builders ask for the
+// address once on the handle's device, where allocating is allowed; every
+// call asks again (cheap once the image is loaded), so no address outlives a
+// device reset.
 #include <algorithm>
-#include <mutex>
+#include <string>
 
 #include "ct_internal.cuh"
 
@@ -18,24 +22,20 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[CT_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mutex;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
-
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Device address of the scratch array on `dev` (the current device).
-int scratch_address(int dev, unsigned char** out)
+// Device address of the scratch array on the current device.
+int scratch_address(unsigned char** out)
 {
-    if (dev < 0 || dev >= kMaxDevices) return fail(CT_ERR_UNSUPPORTED, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)", __FILE__, __LINE__);
-        g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e == cudaErrorMemoryAllocation) {
+        (void)cudaGetLastError();
+        return fail(CT_ERR_OOM, "the device has no room for the allocation-free scratch array (" +
+                                    std::to_string((size_t)CT_NOALLOC_SCRATCH_BYTES) + " bytes)");
     }
-    *out = g_scratch_addr[dev];
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)", __FILE__, __LINE__);
+    *out = static_cast<unsigned char*>(p);
     return CT_OK;
 }
 
@@ -72,6 +72,19 @@ bool on_device(const void* p)
 }
 
 }  // namespace
+
+// Commits the scratch array on the current device (loads this file's device
+// image).  Called by the matrix builders, where allocating is allowed; a
+// failure is left for ct_cg_solve_noalloc to report.
+void noalloc_reserve()
+{
+    unsigned char* p = nullptr;
+    if (scratch_address(&p) != CT_OK) {
+        (void)cudaGetLastError();
+        set_error("");
+    }
+}
+
 }  // namespace ct
 
 using namespace ct;
@@ -94,7 +107,7 @@ extern "C" int ct_cg_solve_noalloc(ct_matrix_t A, const ct_cg_params* params, co
         return fail(CT_ERR_ARG, "problem needs " + std::to_string(L.total) + " bytes of scratch; the limit is " +
                                     std::to_string((size_t)CT_NOALLOC_SCRATCH_BYTES) + " (CT_NOALLOC_SCRATCH_BYTES)");
     unsigned char* base = nullptr;
-    CT_CHECK(scratch_address(dev, &base));
+    CT_CHECK(scratch_address(&base));
     Workspace w;
     w.batch = 1;
     w.n2 = A->npad;

@@ -35,10 +35,7 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("geom,coef", [((64, 90, 3, 91), (0.0, 1.0, 0.1)),
-                                       ((512, 720, 4, 725), (1.0, 0.05, 0.0))])
-def test_noalloc_matches_cg_solve_on_two_calls(dev, geom, coef):
-    M = ct.Matrix(*geom)
+def _two_calls(dev, M, coef, tol):
     n2 = M.cols
     params = ct.CgParams(coef[0], coef[1], coef[2], 12, 0.0, 0, 0, 0)
     for call in range(2):
@@ -49,11 +46,30 @@ def test_noalloc_matches_cg_solve_on_two_calls(dev, geom, coef):
         ct.ct_cg_solve(M.handle, params, rhs, u_ref, 1, st_ref)
         u_na = u0.clone()
         st_na = ct.CgStats()
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info(dev)[0]
         ct.ct_cg_solve_noalloc(M.handle, params, rhs, u_na, st_na)
         torch.cuda.synchronize()
+        # the call commits no device memory (the scratch array was committed
+        # when the handle was built)
+        assert torch.cuda.mem_get_info(dev)[0] == free_before
         assert st_na.status == 0 and st_na.iters == st_ref.iters == 12
-        assert _rel(u_na, u_ref) <= CG_TOL
-        assert abs(st_na.final_rel_res - st_ref.final_rel_res) <= CG_TOL * st_ref.final_rel_res
+        assert _rel(u_na, u_ref) <= tol
+        assert abs(st_na.final_rel_res - st_ref.final_rel_res) <= tol * st_ref.final_rel_res
+
+
+@pytest.mark.parametrize("geom,coef,flags", [((64, 90, 3, 91), (0.0, 1.0, 0.1), ct.CT_VAL_FP32),
+                                             ((512, 720, 4, 725), (1.0, 0.05, 0.0), ct.CT_VAL_FP32),
+                                             ((64, 90, 3, 91), (0.0, 1.0, 0.1), ct.CT_VAL_FP16_ROWSCALE)])
+def test_noalloc_matches_cg_solve_on_two_calls(dev, geom, coef, flags):
+    M = ct.Matrix(*geom, flags=flags)
+    _two_calls(dev, M, coef, CG_TOL)
+    M.close()
+
+
+def test_noalloc_on_a_fourier_handle_matches_cg_solve(dev):
+    M = ct.FourierMatrix(64, 90, 3, 91, m_sp=6)
+    _two_calls(dev, M, (0.0, 1.0, 0.1), CG_TOL)
     M.close()
 
 
