@@ -104,12 +104,18 @@ class Breakdown(ArithmeticError):
     """p^T Op p <= 0 with a nonzero residual: the operator is not SPD."""
 
 
-def cg(op, rhs, u0, iters, rel_tol=0.0):
+def cg(op, rhs, u0, iters, rel_tol=0.0, refresh_every=0, refresh_op=None):
     """Conjugate gradients (Hestenes-Stiefel) for Op u = rhs, warm-started at u0.
 
     Sec. 2: the systems have no closed-form solution, so an iterative solver
     is used.  Runs ``iters`` steps, or fewer if the residual is exactly zero
     or ||r|| <= rel_tol ||rhs||.  Returns (u, stats).
+
+    Residual replacement (the FP16-storage form's refresh, not in the paper):
+    with refresh_every = k > 0, after every k-th step that is not the last
+    one the recursively updated residual is replaced by rhs - refresh_op(u)
+    (refresh_op defaults to op: the FP32 operator when op is the quantised
+    one), and r.r with it; the search direction is kept (no restart).
     """
     # Complex inputs (complex-step differentiation) keep their dtype; the
     # dot products are plain sums of products and every decision below is
@@ -136,6 +142,9 @@ def cg(op, rhs, u0, iters, rel_tol=0.0):
         p = r + (rr_new / rr) * p
         rr = rr_new
         done += 1
+        if refresh_every > 0 and done % refresh_every == 0 and done < iters:
+            r = rhs - (op if refresh_op is None else refresh_op)(u)
+            rr = r @ r
     rel = float(np.sqrt(np.real(rr))) / rhs_norm if rhs_norm > 0 else 0.0
     return u, {"iters": done, "rel_res": rel}
 
@@ -144,7 +153,7 @@ def cg(op, rhs, u0, iters, rel_tol=0.0):
 # Split Bregman for min alpha/2 ||A u - f||^2 + ||grad u||_1 (Sec. 2, Sec. 4)
 # --------------------------------------------------------------------------
 def split_bregman(A, f, shape, alpha, lam, outer, inner, u0=None, normal=None,
-                  stop_rel_update=0.0, cg_tol=0.0, state=None):
+                  stop_rel_update=0.0, cg_tol=0.0, state=None, refresh_every=0, refresh_A=None):
     """Anisotropic-TV split Bregman with inexact CG solves of Eq. SB_solve.
 
     Each outer step:
@@ -158,6 +167,9 @@ def split_bregman(A, f, shape, alpha, lam, outer, inner, u0=None, normal=None,
     the right-hand side keeps the exact alpha A^T f in both cases.
     Stops after ``outer`` steps, or once update < stop_rel_update * first
     update (Sec. 4's rule).  ``state`` = (u, dx, dy, bx, by) resumes a run.
+    ``refresh_every`` / ``refresh_A``: every inner CG replaces its residual
+    every k steps with the one of alpha refresh_A^T refresh_A + lambda
+    grad^T grad (the FP32 matrix of the FP16-storage form; see ``cg``).
     """
     ny, nx = shape
     if state is not None:
@@ -170,13 +182,14 @@ def split_bregman(A, f, shape, alpha, lam, outer, inner, u0=None, normal=None,
         bx = np.zeros(shape)
         by = np.zeros(shape)
     op = make_operator(A, shape, 0.0, alpha, lam, normal=normal)
+    op_refresh = None if refresh_A is None else make_operator(refresh_A, shape, 0.0, alpha, lam)
     atf = alpha * (A.T @ f)
     updates = []
     k = 0
     for k in range(outer):
         rhs = atf + lam * grad_adj(dx - bx, dy - by).ravel()
         u_old = u
-        u, _ = cg(op, rhs, u_old, inner, rel_tol=cg_tol)
+        u, _ = cg(op, rhs, u_old, inner, rel_tol=cg_tol, refresh_every=refresh_every, refresh_op=op_refresh)
         gx, gy = grad(u.reshape(shape))
         dx = shrink(gx + bx, 1.0 / lam)
         dy = shrink(gy + by, 1.0 / lam)

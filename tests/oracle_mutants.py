@@ -41,6 +41,14 @@ MUTANTS = {
         ("    r = rhs - op(u)\n", "    r = rhs.copy()\n")]),
     "cg_tolerance_on_squared_norm": ("test_oracle_tv.py", "tv.py", [
         ("np.sqrt(np.real(rr)) <= rel_tol * rhs_norm", "np.real(rr) <= rel_tol * rhs_norm")]),
+    "cg_refresh_one_step_early": ("test_oracle_tv.py", "tv.py", [
+        ("done % refresh_every == 0 and done < iters", "(done - 1) % refresh_every == 0 and done < iters")]),
+    "cg_refresh_keeps_old_rr": ("test_oracle_tv.py", "tv.py", [
+        ("            rr = r @ r\n", "")]),
+    "cg_refresh_restarts_direction": ("test_oracle_tv.py", "tv.py", [
+        ("            rr = r @ r\n", "            rr = r @ r\n            p = r.copy()\n")]),
+    "sb_refresh_matrix_ignored": ("test_oracle_tv.py", "tv.py", [
+        ("refresh_op=op_refresh)", "refresh_op=None)")]),
     # ---- tv.py: split Bregman ----
     "shrink_half_threshold": ("test_oracle_tv.py", "tv.py", [
         ("np.abs(xr) > gamma, x - gamma * np.sign(xr)",
@@ -58,7 +66,7 @@ MUTANTS = {
     "sb_data_term_unscaled": ("test_oracle_tv.py", "tv.py", [
         ("atf = alpha * (A.T @ f)", "atf = A.T @ f")]),
     "sb_inner_cg_not_warm_started": ("test_oracle_tv.py", "tv.py", [
-        ("u, _ = cg(op, rhs, u_old, inner, rel_tol=cg_tol)", "u, _ = cg(op, rhs, np.zeros_like(u_old), inner, rel_tol=cg_tol)")]),
+        ("u, _ = cg(op, rhs, u_old, inner, rel_tol=cg_tol,", "u, _ = cg(op, rhs, np.zeros_like(u_old), inner, rel_tol=cg_tol,")]),
     "sb_update_size_l2": ("test_oracle_tv.py", "tv.py", [
         ("updates.append(float(np.abs(u - u_old).sum()))",
          "updates.append(float(np.sqrt(((u - u_old) ** 2).sum())))")]),

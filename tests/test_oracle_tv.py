@@ -101,6 +101,70 @@ def test_cg_iterate_minimises_energy_over_krylov_space(k):
     assert np.linalg.norm(got - want) <= 1e-8 * np.linalg.norm(want)
 
 
+def test_cg_refresh_beyond_the_last_step_is_plain_cg():
+    """A refresh period at or past the step count never replaces the residual:
+    the iterate is plain CG's, to the last bit."""
+    n = 16
+    A = _small_problem(n)
+    op = tv.make_operator(A, (n, n), 0.0, 1.0, 0.3)
+    op2 = tv.make_operator(A, (n, n), 0.0, 1.1, 0.3)
+    rhs = inputs.random_vector(n * n, 12)
+    x0 = inputs.random_vector(n * n, 13)
+    plain, _ = tv.cg(op, rhs, x0, 8)
+    for k in (8, 9, 100):
+        got, _ = tv.cg(op, rhs, x0, 8, refresh_every=k, refresh_op=op2)
+        np.testing.assert_array_equal(got, plain)
+
+
+def test_cg_refresh_with_the_same_operator_only_rounds():
+    """Replacing the recursive residual by the true one of the same operator
+    changes nothing in exact arithmetic (the two residuals are equal), so the
+    iterate agrees with plain CG to rounding while CG is far from converged
+    (a few steps: a fixed CG step count amplifies rounding as it grows)."""
+    n = 16
+    A = _small_problem(n)
+    op = tv.make_operator(A, (n, n), 0.0, 1.0, 0.3)
+    rhs = inputs.random_vector(n * n, 14)
+    plain, st = tv.cg(op, rhs, np.zeros(n * n), 6)
+    assert st["rel_res"] > 1e-2
+    for k in (1, 2, 5):
+        got, _ = tv.cg(op, rhs, np.zeros(n * n), 6, refresh_every=k)
+        assert np.linalg.norm(got - plain) <= 1e-13 * np.linalg.norm(plain)
+
+
+def test_cg_refresh_by_hand():
+    """Three steps by hand for Op = diag(1, 2, 4), rhs = (1, 1, 1), u0 = 0,
+    with the residual replaced after step 2 by that of B = diag(1, 2, 5):
+    step 1: alpha = 3/7, u1 = (3, 3, 3)/7, r1 = (4, 1, -5)/7, p1 = (6, 3, -3)/7;
+    step 2: alpha = 7/15, u2 = (29, 22, 8)/35, recursive r2 = (6, -9, 3)/35,
+    beta = 3/25, p2 = (48, -36, 6)/175; refresh: r2 = rhs - B u2 =
+    (6, -9, -5)/35, r.r = 142/1225; step 3: p2.Op p2 = 5040/30625,
+    alpha = 355/504, u3 = (751/735, 237/490, 743/2940).  Plain CG ends at the
+    solution (1, 1/2, 1/4); a refresh after step 1 instead would end at
+    (38949/30149, 24897/60298, 15123/60298)."""
+    d = np.array([1.0, 2.0, 4.0])
+    b = np.array([1.0, 2.0, 5.0])
+    got, st = tv.cg(lambda x: d * x, np.ones(3), np.zeros(3), 3, refresh_every=2, refresh_op=lambda x: b * x)
+    assert st["iters"] == 3
+    np.testing.assert_allclose(got, [751 / 735, 237 / 490, 743 / 2940], rtol=1e-14, atol=0)
+    plain, _ = tv.cg(lambda x: d * x, np.ones(3), np.zeros(3), 3)
+    np.testing.assert_allclose(plain, [1.0, 0.5, 0.25], rtol=1e-14, atol=0)
+
+
+def test_sb_refresh_uses_the_refresh_matrix_in_every_inner_solve():
+    """Split Bregman with a refresh matrix equal to A is split Bregman without
+    one, to rounding; with a different refresh matrix it moves."""
+    n = 16
+    A = _small_problem(n)
+    truth = inputs.ellipse_phantom(n, 2)
+    f = A @ truth.ravel()
+    plain = tv.split_bregman(A, f, (n, n), 1.0, 0.1, 4, 6)["u"]
+    same = tv.split_bregman(A, f, (n, n), 1.0, 0.1, 4, 6, refresh_every=2, refresh_A=A)["u"]
+    assert np.linalg.norm(same - plain) <= 1e-10 * np.linalg.norm(plain)
+    other = tv.split_bregman(A, f, (n, n), 1.0, 0.1, 4, 6, refresh_every=2, refresh_A=1.01 * A)["u"]
+    assert np.linalg.norm(other - plain) >= 1e-4 * np.linalg.norm(plain)
+
+
 def test_sb_1d_tv_denoising_satisfies_optimality_certificate():
     """A = I on an n x 1 image: SB must reach the 1-D TV-denoising minimiser of
     alpha/2 ||u - f||^2 + sum |u_{k+1} - u_k|.  Its certificate is
