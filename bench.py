@@ -14,6 +14,7 @@ path); rank 0 prints the job's aggregate.
 """
 
 import argparse
+import glob
 import hashlib
 import json
 import os
@@ -67,24 +68,28 @@ def kernel_source_hash():
 
 
 def profiled_traffic(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, if it still
-    describes the current kernel source (same hash); else None."""
-    path = os.path.join(ROOT, "profiles", "spmv_forward_slice512.md")
-    try:
-        text = open(path).read()
-    except OSError:
-        return None
-    vals = {}
-    for line in text.splitlines():
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
-            vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_hash") != kernel_source_hash():
-        return None
-    try:
-        return float(vals["%s_dram_bytes_per_launch" % kernel_key])
-    except (KeyError, ValueError):
-        return None
+    """DRAM bytes per launch of a kernel from the committed ncu summaries
+    (a line "- <key>_dram_bytes_per_launch: B" in a profiles/*.md file), if
+    that summary still describes the current kernel source (its
+    kernel_source_hash line matches); else None."""
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        try:
+            text = open(path).read()
+        except OSError:
+            continue
+        vals = {}
+        for line in text.splitlines():
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip()
+        key = "%s_dram_bytes_per_launch" % kernel_key
+        if key not in vals or vals.get("kernel_source_hash") != kernel_source_hash():
+            continue
+        try:
+            return float(vals[key])
+        except ValueError:
+            return None
+    return None
 
 
 class ClockSampler:
@@ -191,6 +196,15 @@ def oracle_sample_main(args):
     A = radon.siddon_matrix(wl["n"], wl["n_angles_total"], wl["keep_every"], wl["n_bins"])
     if args.oracle_f32:
         A.data = A.data.astype(np.float32).astype(np.float64)  # the values the library stores
+    if args.oracle_go:
+        # several children time the same sample at once: report ready, then
+        # start when the parent says so, so that every timed region overlaps
+        open(args.oracle_out + ".ready", "w").close()
+        t_wait = time.time()
+        while not os.path.exists(args.oracle_go):
+            if time.time() - t_wait > 900:
+                raise SystemExit("no start signal")
+            time.sleep(0.02)
     state, us = None, []
     t0 = time.perf_counter()
     for _ in range(args.oracle_updates):
@@ -218,6 +232,39 @@ def run_oracle_sample(wl_name, f, updates, f32_values=False):
             capture_output=True, text=True, env=env, check=True)
         secs = json.loads(out.stdout.strip().splitlines()[-1])["seconds"]
         return secs, np.load(fout)
+
+
+def run_oracle_parallel(wl_name, f, updates, nproc):
+    """The same bounded oracle sample in `nproc` single-threaded children at
+    once (one per host core): each builds its matrix, then all start their
+    timed updates together.  Returns the seconds of every child."""
+    with tempfile.TemporaryDirectory() as td:
+        fin, go = os.path.join(td, "f.npy"), os.path.join(td, "go")
+        np.save(fin, f)
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[k] = "1"
+        env["CUDA_VISIBLE_DEVICES"] = ""
+        outs = [os.path.join(td, "u%d.npy" % i) for i in range(nproc)]
+        procs = [subprocess.Popen([sys.executable, os.path.abspath(__file__), "--workload", wl_name,
+                                   "--_oracle-in", fin, "--_oracle-out", o, "--_oracle-updates", str(updates),
+                                   "--_oracle-go", go], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                  text=True, env=env) for o in outs]
+        t0 = time.time()
+        while not all(os.path.exists(o + ".ready") for o in outs):
+            if time.time() - t0 > 900 or any(p.poll() not in (None, 0) for p in procs):
+                for p in procs:
+                    p.kill()
+                raise RuntimeError("oracle children failed to start")
+            time.sleep(0.05)
+        open(go, "w").close()
+        secs = []
+        for p in procs:
+            out, err = p.communicate()
+            if p.returncode != 0:
+                raise RuntimeError("oracle child failed: " + err[-500:])
+            secs.append(json.loads(out.strip().splitlines()[-1])["seconds"])
+        return secs
 
 
 def oracle_slice_baseline(wl_name, seed, noise_seed, note=""):
@@ -299,20 +346,30 @@ def bench_ours(args):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / 1e3 / reps
 
-    t_fwd = time_kernel(lambda: M.forward(x, y))
-    t_adj = time_kernel(lambda: M.adjoint(y, xa))
+    t_fwd32 = time_kernel(lambda: M.forward(x, y))
+    t_adj32 = time_kernel(lambda: M.adjoint(y, xa))
+    # the solver's own kernels, launched as the solver launches them (double-
+    # float vectors), timed back to back with CUDA events on this stream
+    kms = ct.ct_time_cg_kernels(M.handle, wl["alpha"], wl["lam"], reps, stream.cuda_stream)
+    t_fwd, t_op, t_upd, t_dir = (v / 1e3 for v in kms)
+
     # algorithmic bytes: every stored entry once (A: int32 column + FP32 value;
-    # A^T: 16-bit band column + FP32 value), index data, input read once,
-    # output written once
-    # (SELL-32 index data: slice offsets, one per 32 rows, and row lengths)
+    # A^T: 16-bit band column + FP32 value), index data (SELL-32 slice offsets,
+    # one per 32 rows, and row lengths), input read once, output written once
     def index_bytes(rows):
         return (rows // 32 + 1) * 8 + rows * 4
 
-    bytes_fwd = M.nnz * 8 + index_bytes(M.rows) + M.cols * 4 + M.rows * 4
-    bytes_adj = M.nnz * 6 + index_bytes(M.cols) + M.rows * 4 + M.cols * 4
+    n2, npad = n * n, M.cols
+    npad = ((n + 15) // 16 * 16) ** 2
+    bytes_fwd = M.nnz * 8 + index_bytes(M.rows) + n2 * 8 + M.rows * 8          # double-float x, y
+    bytes_op = M.nnz * 6 + index_bytes(npad) + M.rows * 8 + n2 * 8 * 2         # y in, p in, q out
+    bytes_fwd32 = M.nnz * 8 + index_bytes(M.rows) + n2 * 4 + M.rows * 4
+    bytes_adj32 = M.nnz * 6 + index_bytes(npad) + M.rows * 4 + n2 * 4
+    bytes_upd = npad * 8 * 6                                                   # u, r rw; p, q read
+    bytes_dir = npad * 8 * 3                                                   # p rw; r read
     peak, peak_kind = measured_peak()
     ach_fwd = bytes_fwd / t_fwd / 1e9
-    ach_adj = bytes_adj / t_adj / 1e9
+    ach_op = bytes_op / t_op / 1e9
     # one CG step of the split-Bregman system (A p, A^T + operator epilogue,
     # two vector updates): time of 20 steps minus 0 steps, per step
     rhs = torch.empty(M.cols, dtype=torch.float32, device=dev)
@@ -331,7 +388,7 @@ def bench_ours(args):
         return a.elapsed_time(b) / 1e3 / 5
 
     t_cg = (cg_time(20) - cg_time(0)) / 20
-    bytes_cg = M.nnz * 14 + index_bytes(M.rows) + index_bytes(M.cols)
+    bytes_cg = M.nnz * 14 + index_bytes(M.rows) + index_bytes(npad)
 
     # end to end through the public API with pinned host buffers
     f_pin = torch.tensor(f_host, dtype=torch.float32).pin_memory()
@@ -364,28 +421,42 @@ def bench_ours(args):
             "matrix": "SELL-32 A (int32 columns into the tiled image) and A^T (tile order, 16-bit band "
                       "columns), FP32 values, nnz %d each" % M.nnz,
             "l2": "inputs larger than L2: A and A^T stream %.2f GB per operator application"
-                  % ((bytes_fwd + bytes_adj) / 1e9),
+                  % (bytes_cg / 1e9),
             "parallelism": "replicas over slices" if world > 1 else "single GPU",
         },
         "roofline": {
-            "kernel": "sell_fwd_kernel<float> on A (y = A x: SELL-32 FP32 values, int32 columns, one row per "
-                      "lane, double-float accumulation); the solver launches the same template, with "
-                      "double-float vectors, for every y = A p",
+            "kernel": "sell_fwd_kernel<float, float2, float2> on A: y = A p inside CG (SELL-32 FP32 values, "
+                      "int32 columns into the tiled image, double-float p and y, one row per lane), the "
+                      "step's largest kernel; timed as the solver launches it",
             "bound": "hbm",
             "achieved": round(ach_fwd, 1),
             "peak": peak,
             "peak_kind": peak_kind,
             "unit": "GB/s",
             "frac": round(ach_fwd / peak, 4),
-            "traffic": profiled_traffic("forward"),
+            "traffic": profiled_traffic("forward_df"),
             "algorithmic_bytes": int(bytes_fwd),
             "launch_ms": round(t_fwd * 1e3, 4),
         },
         "kernels": {
-            "adjoint_spmv": {"kernel": "band_adj_kernel<float> on A^T (x = A^T y, SELL-32 by image tile, "
-                                       "sinogram band staged in shared memory)",
-                             "achieved_gbs": round(ach_adj, 1), "frac": round(ach_adj / peak, 4),
-                             "launch_ms": round(t_adj * 1e3, 4), "algorithmic_bytes": int(bytes_adj)},
+            "op_adjoint": {"kernel": "band_op_kernel<float, 1> on A^T: q = Op(p) = alpha A^T y + lambda "
+                                     "grad^T grad p with p.q (SELL-32 by image tile, double-float sinogram "
+                                     "band staged in shared memory); timed as the solver launches it",
+                           "achieved_gbs": round(ach_op, 1), "frac": round(ach_op / peak, 4),
+                           "launch_ms": round(t_op * 1e3, 4), "algorithmic_bytes": int(bytes_op),
+                           "traffic": profiled_traffic("op_adjoint")},
+            "cg_update": {"achieved_gbs": round(bytes_upd / t_upd / 1e9, 1), "launch_ms": round(t_upd * 1e3, 4),
+                          "algorithmic_bytes": int(bytes_upd), "note": "L2-resident vectors"},
+            "cg_direction": {"achieved_gbs": round(bytes_dir / t_dir / 1e9, 1), "launch_ms": round(t_dir * 1e3, 4),
+                             "algorithmic_bytes": int(bytes_dir), "note": "L2-resident vectors"},
+            "forward_spmv_fp32": {"kernel": "sell_fwd_kernel<float, float, float> (public ct_forward, FP32 vectors)",
+                                  "achieved_gbs": round(bytes_fwd32 / t_fwd32 / 1e9, 1),
+                                  "frac": round(bytes_fwd32 / t_fwd32 / 1e9 / peak, 4),
+                                  "launch_ms": round(t_fwd32 * 1e3, 4), "algorithmic_bytes": int(bytes_fwd32)},
+            "adjoint_spmv_fp32": {"kernel": "band_adj_kernel<float> (public ct_adjoint, FP32 vectors)",
+                                  "achieved_gbs": round(bytes_adj32 / t_adj32 / 1e9, 1),
+                                  "frac": round(bytes_adj32 / t_adj32 / 1e9 / peak, 4),
+                                  "launch_ms": round(t_adj32 * 1e3, 4), "algorithmic_bytes": int(bytes_adj32)},
             "cg_step": {"what": "one CG step of the split-Bregman system: A p, A^T with the fused operator "
                                 "epilogue and p.q, two vector updates (matrix bytes only in the numerator)",
                         "achieved_gbs": round(bytes_cg / t_cg / 1e9, 1),
@@ -423,13 +494,22 @@ def bench_ours(args):
         errs["note"] = ("a fixed count of CG steps amplifies any rounding difference: the FP64 oracle on the "
                         "matrix rounded to FP32 drifts from the FP64 oracle by the last field; the GPU path "
                         "stores FP32 values")
+        ncores = os.cpu_count() or 1
+        secs_par = run_oracle_parallel(args.workload, f_or, 1, ncores)
+        # all children ran concurrently: the job took as long as the slowest
+        par_value = ncores / wl["outer"] / max(secs_par)
         out["cpu_baseline"] = {
-            "value": round(ORACLE_UPDATES / wl["outer"] / secs_cpu, 6),
+            "value": round(par_value, 6),
             "unit": "slices/s",
-            "cores": 1,
+            "cores": ncores,
             "kind": "oracle",
-            "sample": "%d of %d Bregman updates (20 CG steps each) of the same workload, FP64 numpy/scipy "
-                      "CSR, one thread; %.1f s" % (ORACLE_UPDATES, wl["outer"], secs_cpu),
+            "sample": "1 of %d Bregman updates (20 CG steps) of the same workload in each of %d concurrent "
+                      "single-threaded oracle processes (FP64 numpy/scipy CSR; slices are independent, so "
+                      "the host's cores work on different slices); slowest %.1f s, fastest %.1f s"
+                      % (wl["outer"], ncores, max(secs_par), min(secs_par)),
+            "single_core": {"value": round(ORACLE_UPDATES / wl["outer"] / secs_cpu, 6), "cores": 1,
+                            "sample": "%d of %d Bregman updates, one process, one thread; %.1f s"
+                                      % (ORACLE_UPDATES, wl["outer"], secs_cpu)},
         }
         out["parity"] = errs
     if rank == 0:
@@ -1324,6 +1404,7 @@ def main():
     ap.add_argument("--_oracle-out", dest="oracle_out", default=None)
     ap.add_argument("--_oracle-updates", dest="oracle_updates", type=int, default=ORACLE_UPDATES)
     ap.add_argument("--_oracle-f32", dest="oracle_f32", action="store_true")
+    ap.add_argument("--_oracle-go", dest="oracle_go", default=None)
     args = ap.parse_args()
     if args.oracle_in:
         oracle_sample_main(args)

@@ -157,6 +157,11 @@ typedef struct {
     int32_t surrogate_r;    /* 0: exact A^T A; > 0: surrogate T (Eq. surr_SBupd)    */
     int32_t refresh_every;  /* as in ct_cg_params                                    */
     int32_t surrogate_square;
+    double cg_rel_tol;      /* each inner solve also stops once ||r|| <= cg_rel_tol ||rhs||
+                               (inner_cg_iters is then the cap); 0 = the fixed count of
+                               Sec. 4.  A tight tolerance makes the reconstruction a
+                               function of the problem alone: a fixed count of CG steps
+                               amplifies rounding differences over many updates       */
 } ct_sb_params;
 
 typedef struct {
@@ -232,6 +237,24 @@ int ct_split_bregman_ragged(int32_t count, const ct_matrix_t *A, const float *co
  * Errors: CT_ERR_ARG (batch < 2, other unroll values, NULL output). */
 int ct_set_spmm_unroll(ct_matrix_t A, int32_t batch, int32_t unroll);
 int ct_get_spmm_unroll(ct_matrix_t A, int32_t batch, int32_t *unroll);
+
+/* Launch timing of the kernels of one CG step (measurement only; the paper's
+ * Sec. 4 times whole reconstructions).  On the handle's single-slice
+ * workspace, each kernel of a CG step on Op = c_ata A^T A + c_grad grad^T grad
+ * (Eq. SB_solve with alpha = c_ata, lambda = c_grad) is launched exactly as
+ * the solver launches it (the same template instance and launch shape),
+ * 3 times untimed and then `reps` times back to back between two CUDA events
+ * on cuda_stream; ms[k] (host array of 4) receives the mean milliseconds
+ * per launch of:
+ *   ms[0]  y = A p               (double-float vectors)
+ *   ms[1]  q = Op(p), p.q        (A^T y fused with the operator epilogue and
+ *                                 the grid-wide dot product)
+ *   ms[2]  u += alpha p, r -= alpha q, r.r
+ *   ms[3]  p = r + beta p
+ * The workspace's vectors are overwritten (p = r = 1, u = q = 0 first); the
+ * call synchronises.  Errors: CT_ERR_ARG (reps < 1, NULL ms),
+ * CT_ERR_UNSUPPORTED (Fourier handle), CT_ERR_OOM, CT_ERR_CUDA. */
+int ct_time_cg_kernels(ct_matrix_t A, double c_ata, double c_grad, int32_t reps, double *ms, void *cuda_stream);
 
 /* Allocation-free variant of ct_cg_solve.  The paper has no counterpart.
  *

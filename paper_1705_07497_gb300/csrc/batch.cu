@@ -1080,7 +1080,7 @@ int sb_prepare(ct_matrix* M, const ct_sb_params* Sp, BatchIn f, BatchIn u, int32
     R.Sp = Sp;
     R.B = B;
     BPlan& P = R.P;
-    CT_CHECK(bmake_plan(M, B, 0.0, Sp->alpha, Sp->lambda, 0.0, Sp->surrogate_r, Sp->surrogate_square,
+    CT_CHECK(bmake_plan(M, B, 0.0, Sp->alpha, Sp->lambda, Sp->cg_rel_tol, Sp->surrogate_r, Sp->surrogate_square,
                         Sp->refresh_every, P));
     P.sb = w.sb;
     P.base.sb = w.sb;

@@ -332,8 +332,8 @@ int ct_split_bregman_ragged(int32_t count, const ct_matrix_t* A, const float* co
     if (count < 1) return fail(CT_ERR_ARG, "count must be >= 1");
     if (!A || !f || !u) return fail(CT_ERR_ARG, "NULL array of handles or vector pointers");
     if (!params) return fail(CT_ERR_ARG, "NULL params");
-    if (!(params->lambda > 0.0) || params->outer_iters < 0 || params->inner_cg_iters < 0)
-        return fail(CT_ERR_ARG, "split Bregman needs lambda > 0 and non-negative iteration counts");
+    if (!(params->lambda > 0.0) || params->outer_iters < 0 || params->inner_cg_iters < 0 || !(params->cg_rel_tol >= 0.0))
+        return fail(CT_ERR_ARG, "split Bregman needs lambda > 0, non-negative iteration counts and cg_rel_tol >= 0");
     for (int32_t i = 0; i < count; ++i) {
         CT_CHECK(check_handle(A[i]));
         CT_CHECK(no_fourier(A[i], "ct_split_bregman_ragged"));
@@ -342,6 +342,14 @@ int ct_split_bregman_ragged(int32_t count, const ct_matrix_t* A, const float* co
             return fail(CT_ERR_ARG, "ct_split_bregman_ragged needs device pointers (problem " + std::to_string(i) + ")");
     }
     return split_bregman_ragged(count, A, f, u, params, stats, (cudaStream_t)cuda_stream);
+}
+
+int ct_time_cg_kernels(ct_matrix_t A, double c_ata, double c_grad, int32_t reps, double* ms, void* cuda_stream)
+{
+    CT_CHECK(check_handle(A));
+    if (!ms) return fail(CT_ERR_ARG, "NULL output array");
+    CT_CHECK(no_fourier(A, "ct_time_cg_kernels"));
+    return time_cg_kernels(A, c_ata, c_grad, reps, ms, (cudaStream_t)cuda_stream);
 }
 
 int ct_set_spmm_unroll(ct_matrix_t A, int32_t batch, int32_t unroll)

@@ -235,6 +235,7 @@ int cg_solve(ct_matrix* M, const ct_cg_params* P, const float* rhs, float* u, in
              ct_cg_stats* stats, cudaStream_t st);
 int split_bregman(ct_matrix* M, const ct_sb_params* P, const float* f, float* u, int32_t batch,
                   ct_sb_stats* stats, cudaStream_t st);
+int time_cg_kernels(ct_matrix* M, double c_ata, double c_grad, int32_t reps, double* ms, cudaStream_t st);
 
 int grid_for(const ct_matrix* M, int64_t work_items, int items_per_block, int max_per_sm);
 

@@ -447,6 +447,91 @@ int cg_solve(ct_matrix* M, const ct_cg_params* Pp, const float* rhs, float* u, i
 
 namespace {
 
+__global__ void fill_df_kernel(float2* __restrict__ v, int n, int tn, float hi)
+{
+    const int64_t npad = padded_pixels(n);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npad;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int i, j;
+        tiled_coords(t, tn, i, j);
+        v[t] = (i < n && j < n) ? make_float2(hi, 0.0f) : make_float2(0.0f, 0.0f);
+    }
+}
+
+}  // namespace
+
+// Mean launch time of each kernel of one CG step, launched as the solver
+// launches it (same template instances, the handle's workspace), `reps`
+// times back to back between two events on st.
+int time_cg_kernels(ct_matrix* M, double c_ata, double c_grad, int32_t reps, double* ms, cudaStream_t st)
+{
+    if (reps < 1) return fail(CT_ERR_ARG, "reps must be >= 1");
+    if (M->fourier) return fail(CT_ERR_UNSUPPORTED, "kernel timing needs the Siddon matrices");
+    CT_CHECK(ensure_workspace(M, 1, true));
+    Workspace& w = M->ws;
+    Plan P;
+    CT_CHECK(make_plan(M, &w, 0.0, c_ata, c_grad, 0.0, 0, 0, 0, P));
+    const int gv = grid_for(M, P.n2, 256, 8);
+    // p = r = 1 on the image, u = q = 0: every product is finite and p.q > 0,
+    // so the scalars keep the slice active through every launch
+    fill_df_kernel<<<gv, 256, 0, st>>>(w.p, M->g.n, M->tn, 1.0f);
+    fill_df_kernel<<<gv, 256, 0, st>>>(w.r, M->g.n, M->tn, 1.0f);
+    fill_df_kernel<<<gv, 256, 0, st>>>(w.u, M->g.n, M->tn, 0.0f);
+    fill_df_kernel<<<gv, 256, 0, st>>>(w.q, M->g.n, M->tn, 0.0f);
+    CT_CUDA(cudaGetLastError());
+    CgSlice h;
+    std::memset(&h, 0, sizeof(h));
+    h.rr = h.rhs2 = 1.0;
+    h.active = 1;
+    CT_CUDA(cudaMemcpyAsync(w.cg, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CT_CUDA(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ce, "cudaEventCreate", __FILE__, __LINE__);
+    }
+    OpEpilogue e1p = P.base;
+    e1p.mode = 1;
+    e1p.out = w.q;
+    e1p.in = w.p;
+    int rc = CT_OK;
+    for (int k = 0; k < 4 && rc == CT_OK; ++k) {
+        auto launch = [&]() -> int {
+            switch (k) {
+            case 0: return launch_forward_df(M, P.vk, w.p, w.y, P.vk == ValKind::F16 ? 2 : 0, w.cg, nullptr, st);
+            case 1: return launch_adjoint_op_df(M, P.vk, w.y, e1p, st);
+            case 2:
+                cg_update_kernel<<<gv, 256, 0, st>>>(w.u, w.r, w.p, w.q, P.n2, w.cg, 0.0, w.partials, w.counter,
+                                                     nullptr);
+                return cudaGetLastError() == cudaSuccess ? CT_OK : fail(CT_ERR_CUDA, "launch failed");
+            default:
+                cg_direction_kernel<<<gv, 256, 0, st>>>(w.p, w.r, P.n2, w.cg, nullptr);
+                return cudaGetLastError() == cudaSuccess ? CT_OK : fail(CT_ERR_CUDA, "launch failed");
+            }
+        };
+        for (int i = 0; i < 3 && rc == CT_OK; ++i) rc = launch();  // warm-up
+        if (rc != CT_OK) break;
+        if (cudaEventRecord(e0, st) != cudaSuccess) rc = fail(CT_ERR_CUDA, "cudaEventRecord failed");
+        for (int i = 0; i < reps && rc == CT_OK; ++i) rc = launch();
+        if (rc == CT_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = fail(CT_ERR_CUDA, "cudaEventRecord failed");
+        if (rc == CT_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(CT_ERR_CUDA, "cudaEventSynchronize failed");
+        float t = 0.0f;
+        if (rc == CT_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) rc = fail(CT_ERR_CUDA, "event timing failed");
+        if (rc == CT_OK) ms[k] = (double)t / reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != CT_OK) return rc;
+    CgSlice back;
+    CT_CUDA(cudaMemcpyAsync(&back, w.cg, sizeof(back), cudaMemcpyDeviceToHost, st));
+    CT_CUDA(cudaStreamSynchronize(st));
+    if (!back.active) return fail(CT_ERR_CUDA, "internal: the timed CG scalars went inactive");
+    return CT_OK;
+}
+
+namespace {
+
 int enqueue_sb_outer(const Plan& P, const ct_sb_params* Sp, cudaStream_t st)
 {
     Workspace& w = *P.w;
@@ -482,7 +567,7 @@ int sb1_prepare(ct_matrix* M, Workspace& w, const ct_sb_params* Sp, const float*
     R->Sp = Sp;
     CT_CHECK(ensure_workspace_in(M, w, batch));
     Plan& P = R->P;
-    CT_CHECK(make_plan(M, &w, 0.0, Sp->alpha, Sp->lambda, 0.0, Sp->surrogate_r, Sp->surrogate_square,
+    CT_CHECK(make_plan(M, &w, 0.0, Sp->alpha, Sp->lambda, Sp->cg_rel_tol, Sp->surrogate_r, Sp->surrogate_square,
                        Sp->refresh_every, P));
     P.base.gate = &w.sb->stopped;
     P.base.atf = w.atf;
@@ -593,8 +678,8 @@ int run_updates(const std::vector<UpdateFn>& fns, const std::vector<cudaStream_t
 int split_bregman(ct_matrix* M, const ct_sb_params* Sp, const float* f, float* u, int32_t batch,
                   ct_sb_stats* stats, cudaStream_t st)
 {
-    if (!(Sp->lambda > 0.0) || Sp->outer_iters < 0 || Sp->inner_cg_iters < 0)
-        return fail(CT_ERR_ARG, "split Bregman needs lambda > 0 and non-negative iteration counts");
+    if (!(Sp->lambda > 0.0) || Sp->outer_iters < 0 || Sp->inner_cg_iters < 0 || !(Sp->cg_rel_tol >= 0.0))
+        return fail(CT_ERR_ARG, "split Bregman needs lambda > 0, non-negative iteration counts and cg_rel_tol >= 0");
     if (batch != 1 && M->fourier) return fail(CT_ERR_UNSUPPORTED, "the Fourier operator solves one slice per call");
     if (batch != 1) return split_bregman_batched(M, Sp, f, u, batch, stats, st);
     Sb1Run* r = nullptr;

@@ -50,6 +50,7 @@ SYMBOLS = (
     "ct_chambolle_pock",
     "ct_set_spmm_unroll",
     "ct_get_spmm_unroll",
+    "ct_time_cg_kernels",
     "ct_matrix_export",
     "ct_matrix_export_fp16",
     "ct_surrogate_stencil",
@@ -103,6 +104,7 @@ class SbParams(ctypes.Structure):
         ("surrogate_r", ctypes.c_int32),
         ("refresh_every", ctypes.c_int32),
         ("surrogate_square", ctypes.c_int32),
+        ("cg_rel_tol", ctypes.c_double),
     ]
 
 
@@ -169,6 +171,7 @@ def lib():
         L.ct_chambolle_pock.argtypes = [vp, P(CpParams), vp, vp, i32, P(SbStats), vp]
         L.ct_set_spmm_unroll.argtypes = [vp, i32, i32]
         L.ct_get_spmm_unroll.argtypes = [vp, i32, P(i32)]
+        L.ct_time_cg_kernels.argtypes = [vp, ctypes.c_double, ctypes.c_double, i32, vp, vp]
         L.ct_matrix_export.argtypes = [vp, i32, vp, vp, vp]
         L.ct_matrix_export_fp16.argtypes = [vp, vp, vp]
         L.ct_surrogate_stencil.argtypes = [vp, i32, i32, i32, vp, vp, vp, P(i32)]
@@ -309,6 +312,18 @@ def ct_split_bregman_ragged(handles, params, fs, us, stats=None, stream=None):
                                                 sf if stream is None else stream))
 
 
+def ct_time_cg_kernels(h, c_ata, c_grad, reps, stream=None):
+    """Mean ms per launch of the CG step's kernels: [A p, Op(p) fused into
+    A^T, u/r update, direction update]."""
+    ms = (ctypes.c_double * 4)()
+    if stream is None:
+        import torch
+
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _check(lib().ct_time_cg_kernels(h, c_ata, c_grad, reps, ms, stream))
+    return list(ms)
+
+
 def ct_matrix_export(h, which):
     rows, cols, nnz = ct_matrix_info(h)
     n_rows = rows if which == 0 else cols
@@ -430,8 +445,8 @@ class Matrix:
         return {"iters": st.iters, "final_rel_res": st.final_rel_res, "status": st.status}
 
     def split_bregman(self, f, u, alpha, lam, outer, inner, stop_rel_update=0.0, surrogate_r=0,
-                      refresh_every=0, square=False, stats=True):
-        p = SbParams(alpha, lam, outer, inner, stop_rel_update, surrogate_r, refresh_every, int(square))
+                      refresh_every=0, square=False, stats=True, cg_rel_tol=0.0):
+        p = SbParams(alpha, lam, outer, inner, stop_rel_update, surrogate_r, refresh_every, int(square), cg_rel_tol)
         st = SbStats() if stats else None
         ct_split_bregman(self.handle, p, f, u, self._batch(u, self.cols), st)
         if st is None:
@@ -506,11 +521,11 @@ class FourierMatrix(Matrix):
 
 
 def split_bregman_ragged(matrices, fs, us, alpha, lam, outer, inner, stop_rel_update=0.0, surrogate_r=0,
-                         refresh_every=0, square=False, stats=True):
+                         refresh_every=0, square=False, stats=True, cg_rel_tol=0.0):
     """Split Bregman over problems of possibly different geometries in one
     call: problem i reconstructs us[i] (N_i*N_i, in = initial guess) from
     fs[i] with matrices[i].  Returns per-problem stats (or None)."""
-    p = SbParams(alpha, lam, outer, inner, stop_rel_update, surrogate_r, refresh_every, int(square))
+    p = SbParams(alpha, lam, outer, inner, stop_rel_update, surrogate_r, refresh_every, int(square), cg_rel_tol)
     st = (SbStats * len(matrices))() if stats else None
     ct_split_bregman_ragged([m.handle for m in matrices], p, fs, us, st)
     if st is None:
