@@ -14,6 +14,8 @@ Contents
              anisotropic-TV split Bregman (Sec. 2, Eq. SB_solve; Sec. 4), the
              Chambolle-Pock resolvent (Sec. 2, Eq. PD_resolve), and the sparse
              surrogate T (Sec. 3.2, Eq. def_sparse_surr / surr_SBupd).
+  spmv       the CSR products on several host threads (rows summed in
+             storage order, so the result does not depend on the threads).
   fourier    the Fourier-domain data term (Sec. 2, Eq. four_obj): the exact
              nonuniform DFT on polar samples, the data's 1-D DFTs, Gaussian
              gridding and the fused matrix B* B (Sec. 3.1, Eq. fusedop).
@@ -22,4 +24,4 @@ Every floating-point result is FP64.  Readings of the paper where it is
 silent or garbled are stated in the docstring of the function that takes them.
 """
 
-from . import fourier, radon, tv  # noqa: F401
+from . import fourier, radon, spmv, tv  # noqa: F401

@@ -1,4 +1,4 @@
-"""Builds and loads the oracle's C part (``siddon.c``) with gcc.
+"""Builds and loads the oracle's C parts (``siddon.c``, ``spmv.c``) with gcc.
 
 Test infrastructure only (see the package docstring).
 """
@@ -12,8 +12,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "siddon.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT_DIR, "liboracle_siddon.so")
+_SPMV_SRC = os.path.join(_HERE, "spmv.c")
+_SPMV_LIB = os.path.join(_OUT_DIR, "liboracle_spmv.so")
 
 _lib = None
+_spmv = None
 
 
 def build(force=False):
@@ -28,7 +31,28 @@ def build(force=False):
                 ["gcc", "-O2", "-std=c11", "-Wall", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
             )
             os.replace(tmp, _LIB)
+        fresh = os.path.exists(_SPMV_LIB) and os.path.getmtime(_SPMV_LIB) >= os.path.getmtime(_SPMV_SRC)
+        if force or not fresh:
+            tmp = _SPMV_LIB + ".tmp%d" % os.getpid()
+            subprocess.check_call(
+                ["gcc", "-O2", "-std=c11", "-Wall", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                 "-o", tmp, _SPMV_SRC]
+            )
+            os.replace(tmp, _SPMV_LIB)
     return _LIB
+
+
+def spmv_lib():
+    """The threaded CSR product of ``spmv.c``."""
+    global _spmv
+    if _spmv is None:
+        build()
+        L = ctypes.CDLL(_SPMV_LIB)
+        L.oracle_csr_matvec.restype = None
+        L.oracle_csr_matvec.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+        _spmv = L
+    return _spmv
 
 
 def lib():
