@@ -267,6 +267,151 @@ def run_oracle_parallel(wl_name, f, updates, nproc):
         return secs
 
 
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+FULL_TOL, FULL_CAP = 1e-8, 3000  # the stored runs' inner CG tolerance and step cap
+
+
+def read_golden(name):
+    """Values of a whole FP64-oracle run stored by tests/golden/make_fullrun_golden.py
+    (sample pixel indices and values, norms, objective), or None if absent."""
+    path = os.path.join(GOLDEN, "fullrun_%s.txt" % name)
+    if not os.path.exists(path):
+        return None
+    g = {"idx": [], "val": []}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        key, rest = line.split(" ", 1)
+        if key.isdigit():
+            g["idx"].append(int(key))
+            g["val"].append(float(rest))
+        elif key in ("cg_iters", "update_l1", "name"):
+            g[key] = rest.split()
+        else:
+            g[key] = float(rest)
+    g["idx"] = np.array(g["idx"])
+    g["val"] = np.array(g["val"])
+    return g
+
+
+def sample_rel(u, g):
+    """Relative L2 difference of an image from a stored run over its sample pixels."""
+    flat = np.asarray(u, np.float64).ravel()
+    return float(np.linalg.norm(flat[g["idx"]] - g["val"]) / np.linalg.norm(g["val"]))
+
+
+def full_length_parity(M, wl, f_par, dev):
+    """Whole-run errors of the slice workload against the oracle's stored whole
+    runs: the tolerance-stopped form (a function of the problem alone) and the
+    timed fixed-count form beside the oracle's own drift in that form."""
+    import torch
+
+    n = wl["n"]
+    g_tol, g_fix, g_pert = (read_golden(k) for k in ("slice512_f64", "slice512_fixed_f64", "slice512_fixed_pert"))
+    res = {"compared_on": "4096 seeded sample pixels of the 512x512 image (stored by the oracle)"}
+    if g_tol is not None:
+        u = torch.zeros(n * n, dtype=torch.float32, device=dev)
+        t0 = time.perf_counter()
+        st = M.split_bregman(f_par, u, wl["alpha"], wl["lam"], wl["outer"], FULL_CAP, cg_rel_tol=FULL_TOL)
+        secs = time.perf_counter() - t0
+        res["tolerance_form"] = {
+            "what": "%d updates, every inner CG to ||r|| <= %g ||rhs|| (at most %d steps)"
+                    % (wl["outer"], FULL_TOL, FULL_CAP),
+            "gpu_vs_oracle": sample_rel(u.cpu().numpy(), g_tol),
+            "outer_done": st["outer_done"], "gpu_seconds": round(secs, 3),
+            "oracle_cg_steps": int(sum(int(v) for v in g_tol["cg_iters"])),
+        }
+    if g_fix is not None:
+        u = torch.zeros(n * n, dtype=torch.float32, device=dev)
+        M.split_bregman(f_par, u, wl["alpha"], wl["lam"], wl["outer"], wl["inner"])
+        res["fixed_count_form"] = {
+            "what": "the timed form: %d updates of %d CG steps" % (wl["outer"], wl["inner"]),
+            "gpu_vs_oracle": sample_rel(u.cpu().numpy(), g_fix),
+            "oracle_vs_oracle_with_matrix_times_1_plus_1e-15z":
+                sample_rel(g_pert["val"], g_fix) if g_pert is not None and
+                np.array_equal(g_pert["idx"], g_fix["idx"]) else None,
+        }
+    return res
+
+
+def batched_fp16_block(dev, A_or, steps=2):
+    """The batched FP16 workload (256 slices of 512 x 512, FP16 storage with an
+    FP32 row scale, Poisson data) timed beside the single-slice line, with the
+    batched SpMM's rooflines and the whole-run error of slice 0 in the
+    tolerance-stopped form against the FP64 oracle's stored run (on the
+    dequantised FP16 matrix: the kernels' error; on the FP64 matrix: what the
+    storage costs).  A_or: the oracle's FP64 matrix of the geometry."""
+    import torch
+
+    from paper_1705_07497_gb300 import ct
+
+    wl = inputs.WORKLOADS["batch_512x256"]
+    n, B = wl["n"], wl["batch"]
+    M = ct.Matrix(n, wl["n_angles_total"], wl["keep_every"], wl["n_bins"], ct.CT_VAL_FP16_ROWSCALE)
+    X = torch.empty((n * n, B), dtype=torch.float32, device=dev)
+    for b in range(B):
+        X[:, b] = torch.tensor(inputs.ellipse_phantom(n, wl["seed"] + b).ravel(), dtype=torch.float32)
+    Y = torch.empty((M.rows, B), dtype=torch.float32, device=dev)
+    M.forward(X, Y)
+    clean = Y.double().cpu().numpy()
+    F = torch.tensor(np.stack([noisy(wl, clean[:, b], wl["seed"] + 10000 + b) for b in range(B)], axis=1),
+                     dtype=torch.float32, device=dev)
+    U = torch.zeros((n * n, B), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    st = M.split_bregman(F, U, wl["alpha"], wl["lam"], wl["outer"], wl["inner"])  # warm-up (tunes the SpMM)
+    assert st["status"] == 0 and st["outer_done"] == wl["outer"], st
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        U.zero_()
+        M.split_bregman(F, U, wl["alpha"], wl["lam"], wl["outer"], wl["inner"], stats=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    # the batched forward SpMM alone
+    for _ in range(2):
+        M.forward(X, Y)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(5):
+        M.forward(X, Y)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_spmm = a.elapsed_time(b) / 1e3 / 5
+    mhz = 2070.0
+    peak_ops = sm_count(dev) * 128 * mhz * 1e6 / 1e12
+    ach_ops = M.nnz * B * 11 / t_spmm / 1e12
+    hbm_bytes = M.nnz * 6 + M.rows * 4 + (n * n + M.rows) * B * 4  # FP16 value + int32 column, scale, X, Y
+    peak, _ = measured_peak()
+    res = {
+        "workload": "batch_512x256: %d slices of %dx%d, FP16 values with FP32 row scale, Poisson 1e4 counts, "
+                    "split Bregman %d x %d" % (B, n, n, wl["outer"], wl["inner"]),
+        "value": round(B * steps / secs, 4), "unit": "slices/s", "steps": steps, "warmup": 1,
+        "ms_per_step": round(1e3 * secs / steps, 1),
+        "spmm_forward": {"launch_ms": round(t_spmm * 1e3, 3),
+                         "alu_frac": round(ach_ops / peak_ops, 4),
+                         "alu_note": "11 FP32 operations per entry and slice (compensated multiply-add) against "
+                                     "152 SMs x 128 lanes x 2070 MHz",
+                         "hbm_gbs": round(hbm_bytes / t_spmm / 1e9, 1),
+                         "hbm_frac": round(hbm_bytes / t_spmm / 1e9 / peak, 4)},
+    }
+    g16, g64 = read_golden("batch512_s0_fp16"), read_golden("batch512_s0_f64")
+    if g16 is not None and g64 is not None:
+        F2 = np.stack([inputs.poisson_noisy(A_or @ inputs.ellipse_phantom(n, wl["seed"] + k).ravel(), wl["counts"],
+                                            wl["seed"] + 10000 + k) for k in (0, 1)], axis=1)
+        U2 = torch.zeros((n * n, 2), dtype=torch.float32, device=dev)
+        M.split_bregman(torch.tensor(F2, dtype=torch.float32, device=dev), U2, wl["alpha"], wl["lam"], wl["outer"],
+                        FULL_CAP, cg_rel_tol=FULL_TOL)
+        got = U2[:, 0].cpu().numpy()
+        res["recon_rel_err_slice0"] = {
+            "form": "tolerance-stopped (%d updates, inner CG to %g), batch of 2 slices" % (wl["outer"], FULL_TOL),
+            "vs_oracle_dequantised_fp16": sample_rel(got, g16),
+            "vs_fp64_oracle": sample_rel(got, g64),
+        }
+    M.close()
+    return res
+
+
 def oracle_slice_baseline(wl_name, seed, noise_seed, note=""):
     """cpu_baseline of a workload whose GPU step solves many slices or
     problems: the oracle, in a fresh single-threaded interpreter, on the first
@@ -473,7 +618,7 @@ def bench_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        _, f_or = oracle_data(wl, replicas.rank_seed(wl["seed"], rank))
+        A_or, f_or = oracle_data(wl, replicas.rank_seed(wl["seed"], rank))
         f_par = torch.tensor(f_or, dtype=torch.float32, device=dev)
         secs_cpu, u_oracle = run_oracle_sample(args.workload, f_or, ORACLE_UPDATES)
         _, u_oracle32 = run_oracle_sample(args.workload, f_or, ORACLE_UPDATES, f32_values=True)
@@ -494,6 +639,17 @@ def bench_ours(args):
         errs["note"] = ("a fixed count of CG steps amplifies any rounding difference: the FP64 oracle on the "
                         "matrix rounded to FP32 drifts from the FP64 oracle by the last field; the GPU path "
                         "stores FP32 values")
+        errs["after_%d_updates" % wl["outer"]] = full_length_parity(M, wl, f_par, dev)
+        if not args.no_batched:
+            out["batched_fp16"] = batched_fp16_block(dev, A_or)
+        full = errs["after_%d_updates" % wl["outer"]]
+        out["recon_rel_err"] = {
+            "vs": "FP64 oracle, whole %d-update run, relative L2 over sampled pixels" % wl["outer"],
+            "tolerance_form": full.get("tolerance_form", {}).get("gpu_vs_oracle"),
+            "fixed_count_form": full.get("fixed_count_form", {}).get("gpu_vs_oracle"),
+            "oracle_self_drift_fixed_count":
+                full.get("fixed_count_form", {}).get("oracle_vs_oracle_with_matrix_times_1_plus_1e-15z"),
+        }
         ncores = os.cpu_count() or 1
         secs_par = run_oracle_parallel(args.workload, f_or, 1, ncores)
         # all children ran concurrently: the job took as long as the slowest
@@ -1259,6 +1415,8 @@ def bench_kernel(args):
         out = torch.empty_like(x)
         fn = lambda: F.normal(x, out)  # noqa: E731
         return _time_kernel_fn(args, F, fn, dev, args.steps)
+    if args.kernel == "shapes":
+        return bench_shapes(args, dev)
     if args.kernel == "spmm":
         bl = inputs.WORKLOADS["batch_512x256"]
         M = ct.Matrix(bl["n"], bl["n_angles_total"], bl["keep_every"], bl["n_bins"], ct.CT_VAL_FP16_ROWSCALE)
@@ -1281,6 +1439,50 @@ def bench_kernel(args):
         u = torch.zeros(M.cols, dtype=torch.float32, device=dev)
         fn = lambda: M.cg_solve(rhs, u, 0.0, wl["alpha"], wl["lam"], args.steps)  # noqa: E731
     return _time_kernel_fn(args, M, fn, dev, 1 if args.kernel == "solver" else args.steps)
+
+
+def bench_shapes(args, dev):
+    """Every launch shape of the single-slice products (ct_set_tuning), timed
+    with ct_time_cg_kernels, on the slice workload's geometry and on the
+    distinct geometries of the ragged workload (FP16 storage, as it runs
+    them); then the shape ct_tune picks.  One JSON line per geometry."""
+    import torch
+
+    from paper_1705_07497_gb300 import ct
+
+    geoms = [("slice_512", inputs.WORKLOADS["slice_512"], ct.CT_VAL_FP32)]
+    rl = inputs.WORKLOADS["ragged_64"]
+    seen = set()
+    for n, a, d, nb, _ in inputs.ragged_problems(rl):
+        if (n, a) not in seen:
+            seen.add((n, a))
+            geoms.append(("ragged %dx%d, %d angles" % (n, n, a),
+                          dict(n=n, n_angles_total=a, keep_every=d, n_bins=nb), ct.CT_VAL_FP16_ROWSCALE))
+    for name, g, flags in geoms:
+        M = ct.Matrix(g["n"], g["n_angles_total"], g["keep_every"], g["n_bins"], flags)
+        rows = []
+        for w in (8, 4):
+            for u in (8, 4, 2, 16):
+                for c in ((7, 4), (5, 3)):
+                    try:
+                        ct.ct_set_tuning(M.handle, 1, fwd_warps=w, fwd_unroll=u, op_ctas=c[0])
+                    except ct.CtError:
+                        continue
+                    for cc in c:
+                        ct.ct_set_tuning(M.handle, 1, fwd_warps=w, fwd_unroll=u, op_ctas=cc)
+                        ms = ct.ct_time_cg_kernels(M.handle, 1.0, 1.0, args.steps, torch.cuda.current_stream().cuda_stream)
+                        rows.append({"fwd_warps": w, "fwd_unroll": u, "op_ctas": cc, "fwd_ms": round(ms[0], 5),
+                                     "op_ms": round(ms[1], 5)})
+        ct.ct_set_tuning(M.handle, 1)
+        ct.ct_tune(M.handle, 1)
+        chosen = ct.ct_get_tuning(M.handle, 1)
+        default = next(r for r in rows if r["fwd_warps"] == 8 and r["fwd_unroll"] == 8)
+        best_f = min(rows, key=lambda r: r["fwd_ms"])
+        best_o = min(rows, key=lambda r: r["op_ms"])
+        print(json.dumps({"geometry": name, "nnz": M.nnz, "chosen": chosen,
+                          "default_fwd_ms": default["fwd_ms"], "best_fwd": best_f,
+                          "default_op_ms": default["op_ms"], "best_op": best_o, "all": rows}))
+        M.close()
 
 
 def _time_kernel_fn(args, M, fn, dev, reps):
@@ -1396,7 +1598,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(inputs.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default=None, choices=["forward", "adjoint", "solver", "spmm", "fourier"],
+    ap.add_argument("--kernel", default=None, choices=["forward", "adjoint", "solver", "spmm", "fourier", "shapes"],
                     help="time one product kernel in isolation (small case for profilers)")
     ap.add_argument("--m-sp", dest="m_sp", type=int, default=6,
                     help="--kernel fourier: gridding window half-width")
@@ -1405,6 +1607,8 @@ def main():
     ap.add_argument("--_oracle-updates", dest="oracle_updates", type=int, default=ORACLE_UPDATES)
     ap.add_argument("--_oracle-f32", dest="oracle_f32", action="store_true")
     ap.add_argument("--_oracle-go", dest="oracle_go", default=None)
+    ap.add_argument("--no-batched", action="store_true",
+                    help="leave out the batched FP16 block of the default workload's line")
     args = ap.parse_args()
     if args.oracle_in:
         oracle_sample_main(args)

@@ -238,6 +238,41 @@ int ct_split_bregman_ragged(int32_t count, const ct_matrix_t *A, const float *co
 int ct_set_spmm_unroll(ct_matrix_t A, int32_t batch, int32_t unroll);
 int ct_get_spmm_unroll(ct_matrix_t A, int32_t batch, int32_t *unroll);
 
+/* Launch shapes of the sparse products (no counterpart in the paper).  Each
+ * product comes in launch shapes that all compute the same bits (every row is
+ * summed in the same order whatever the shape); only speed depends on the
+ * choice.  Fields (0 = not chosen yet / automatic):
+ *   fwd_warps    one slice, y = A x: warps per block, 4 or 8 (a warp takes
+ *                four neighbouring rays of a 32-ray slice)
+ *   fwd_unroll   one slice, y = A x: 8-entry chunks each lane keeps in flight,
+ *                2, 4, 8 or 16
+ *   op_ctas      one slice, the A^T kernel fused with the CG operator: CTAs
+ *                per SM its registers are sized for, 7 or 4 (5 or 3 when the
+ *                sinogram band is staged in angle chunks, above about 180 kept
+ *                angles)
+ *   spmm_unroll  batches of 2 or more: staged entries in flight, 4 or 8
+ * By default the first solve on a handle (batch 1: ct_cg_solve,
+ * ct_split_bregman, ct_chambolle_pock, and the single-slice groups of
+ * ct_split_bregman_ragged; batch B: the batched solves) times the candidates
+ * on the handle's own matrices, never inside a stream capture, and keeps the
+ * fastest; batch-1 choices are also cached for the process by geometry and
+ * storage flags, so later handles of the same geometry take them untimed.
+ * ct_tune runs that search now (synchronising cuda_stream); ct_set_tuning pins
+ * fields for a batch size (0 returns one to automatic); ct_get_tuning reports
+ * them.  Fields of the other batch kind must be 0.  Errors: CT_ERR_ARG (batch
+ * < 1, values outside the lists, NULL pointers), CT_ERR_UNSUPPORTED (Fourier
+ * handle), CT_ERR_CUDA. */
+typedef struct {
+    int32_t fwd_warps;
+    int32_t fwd_unroll;
+    int32_t op_ctas;
+    int32_t spmm_unroll;
+} ct_tuning;
+
+int ct_get_tuning(ct_matrix_t A, int32_t batch, ct_tuning *t);
+int ct_set_tuning(ct_matrix_t A, int32_t batch, const ct_tuning *t);
+int ct_tune(ct_matrix_t A, int32_t batch, void *cuda_stream);
+
 /* Launch timing of the kernels of one CG step (measurement only; the paper's
  * Sec. 4 times whole reconstructions).  On the handle's single-slice
  * workspace, each kernel of a CG step on Op = c_ata A^T A + c_grad grad^T grad

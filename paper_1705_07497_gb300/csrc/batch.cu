@@ -1281,4 +1281,14 @@ int split_bregman_ragged(int32_t count, ct_matrix* const* A, const float* const*
     return CT_OK;
 }
 
+// ct_tune for a batch of B >= 2: the staged-entry unroll of the batched
+// products, timed on the handle's workspace (see tune_spmm).
+int tune_batched(ct_matrix* M, int32_t B, cudaStream_t st)
+{
+    CT_CHECK(ensure_workspace(M, B, true));
+    const ValKind vk = (M->flags & CT_VAL_FP16_ROWSCALE) ? ValKind::F16 : ValKind::F32;
+    CT_CUDA(cudaMemsetAsync(M->ws.u, 0, sizeof(float2) * M->npad * B, st));
+    return tune_spmm(M, vk, B, M->ws.u, M->ws.y, st);
+}
+
 }  // namespace ct

@@ -344,6 +344,60 @@ int ct_split_bregman_ragged(int32_t count, const ct_matrix_t* A, const float* co
     return split_bregman_ragged(count, A, f, u, params, stats, (cudaStream_t)cuda_stream);
 }
 
+int ct_get_tuning(ct_matrix_t A, int32_t batch, ct_tuning* t)
+{
+    CT_CHECK(check_handle(A));
+    if (!t) return fail(CT_ERR_ARG, "NULL output pointer");
+    if (batch < 1) return fail(CT_ERR_ARG, "batch must be >= 1");
+    std::memset(t, 0, sizeof(*t));
+    if (batch == 1) {
+        t->fwd_warps = A->fwd_warps;
+        t->fwd_unroll = A->fwd_unroll;
+        t->op_ctas = A->op_ctas;
+    } else {
+        auto it = A->spmm_unroll.find(batch);
+        t->spmm_unroll = it == A->spmm_unroll.end() ? 0 : it->second;
+    }
+    return CT_OK;
+}
+
+int ct_set_tuning(ct_matrix_t A, int32_t batch, const ct_tuning* t)
+{
+    CT_CHECK(check_handle(A));
+    CT_CHECK(no_fourier(A, "ct_set_tuning"));
+    if (!t) return fail(CT_ERR_ARG, "NULL tuning");
+    if (batch < 1) return fail(CT_ERR_ARG, "batch must be >= 1");
+    if (batch == 1) {
+        const bool chunked = A->h_band_chunk.size() > 2;
+        if (t->fwd_warps != 0 && t->fwd_warps != 4 && t->fwd_warps != 8)
+            return fail(CT_ERR_ARG, "fwd_warps must be 0, 4 or 8");
+        if (t->fwd_unroll != 0 && t->fwd_unroll != 2 && t->fwd_unroll != 4 && t->fwd_unroll != 8 &&
+            t->fwd_unroll != 16)
+            return fail(CT_ERR_ARG, "fwd_unroll must be 0, 2, 4, 8 or 16");
+        if (t->op_ctas != 0 && t->op_ctas != (chunked ? 5 : 7) && t->op_ctas != (chunked ? 3 : 4))
+            return fail(CT_ERR_ARG, chunked ? "op_ctas must be 0, 5 or 3 for this matrix (band staged in chunks)"
+                                            : "op_ctas must be 0, 7 or 4 for this matrix");
+        if (t->spmm_unroll != 0) return fail(CT_ERR_ARG, "spmm_unroll applies to batches of 2 or more");
+        A->fwd_warps = t->fwd_warps;
+        A->fwd_unroll = t->fwd_unroll;
+        A->op_ctas = t->op_ctas;
+        return CT_OK;
+    }
+    if (t->fwd_warps || t->fwd_unroll || t->op_ctas)
+        return fail(CT_ERR_ARG, "fwd_warps, fwd_unroll and op_ctas apply to batch 1");
+    return ct_set_spmm_unroll(A, batch, t->spmm_unroll);
+}
+
+int ct_tune(ct_matrix_t A, int32_t batch, void* cuda_stream)
+{
+    CT_CHECK(check_handle(A));
+    CT_CHECK(no_fourier(A, "ct_tune"));
+    if (batch < 1) return fail(CT_ERR_ARG, "batch must be >= 1");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (batch == 1) return tune_single(A, st);
+    return tune_batched(A, batch, st);
+}
+
 int ct_time_cg_kernels(ct_matrix_t A, double c_ata, double c_grad, int32_t reps, double* ms, void* cuda_stream)
 {
     CT_CHECK(check_handle(A));

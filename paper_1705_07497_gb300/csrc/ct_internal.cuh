@@ -156,6 +156,10 @@ struct ct_matrix {
     float* row_scale = nullptr;  // FP16 form: s [rows]
     std::map<std::pair<int, int>, ct::Stencil> stencils;
     std::map<int, int> spmm_unroll;  // batch size -> staged-entry unroll of the batched products (tuned or pinned)
+    // launch shape of the single-slice products (0 = not chosen: the defaults)
+    int fwd_warps = 0;       // y = A x: warps per block (4 or 8)
+    int fwd_unroll = 0;      // y = A x: chunks in flight per lane (2, 4 or 8)
+    int op_ctas = 0;         // A^T kernels: CTAs per SM the registers are sized for
     ct::Workspace ws;
     // extra single-slice workspaces: ct_split_bregman_ragged runs the
     // problems of a small group on one handle side by side
@@ -236,6 +240,9 @@ int cg_solve(ct_matrix* M, const ct_cg_params* P, const float* rhs, float* u, in
 int split_bregman(ct_matrix* M, const ct_sb_params* P, const float* f, float* u, int32_t batch,
                   ct_sb_stats* stats, cudaStream_t st);
 int time_cg_kernels(ct_matrix* M, double c_ata, double c_grad, int32_t reps, double* ms, cudaStream_t st);
+// launch shape of the single-slice products (timed on the handle, cached by geometry)
+int tune_single(ct_matrix* M, cudaStream_t st);
+int tune_batched(ct_matrix* M, int32_t B, cudaStream_t st);
 
 int grid_for(const ct_matrix* M, int64_t work_items, int items_per_block, int max_per_sm);
 

@@ -14,8 +14,11 @@
 #include <cmath>
 #include <cstring>
 
+#include <map>
 #include <memory>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 #include "ct_internal.cuh"
 #include "dfloat.cuh"
@@ -441,6 +444,7 @@ int cg_solve(ct_matrix* M, const ct_cg_params* Pp, const float* rhs, float* u, i
     if (Pp->max_iters < 0) return fail(CT_ERR_ARG, "max_iters < 0");
     if (batch != 1 && M->fourier) return fail(CT_ERR_UNSUPPORTED, "the Fourier operator solves one slice per call");
     if (batch != 1) return cg_solve_batched(M, Pp, rhs, u, batch, stats, st);
+    CT_CHECK(tune_single(M, st));
     CT_CHECK(ensure_workspace(M, batch, true));
     return cg_solve_in(M, M->ws, Pp, rhs, u, stats, st);
 }
@@ -458,22 +462,12 @@ __global__ void fill_df_kernel(float2* __restrict__ v, int n, int tn, float hi)
     }
 }
 
-}  // namespace
-
-// Mean launch time of each kernel of one CG step, launched as the solver
-// launches it (same template instances, the handle's workspace), `reps`
-// times back to back between two events on st.
-int time_cg_kernels(ct_matrix* M, double c_ata, double c_grad, int32_t reps, double* ms, cudaStream_t st)
+// p = r = 1 on the image, u = q = 0 and an active slice: every product of a
+// CG step is then finite with p.q > 0, so the scalars keep the slice active
+// through any number of launches (for timing).
+int prime_cg_workspace(ct_matrix* M, Workspace& w, int64_t n2, cudaStream_t st)
 {
-    if (reps < 1) return fail(CT_ERR_ARG, "reps must be >= 1");
-    if (M->fourier) return fail(CT_ERR_UNSUPPORTED, "kernel timing needs the Siddon matrices");
-    CT_CHECK(ensure_workspace(M, 1, true));
-    Workspace& w = M->ws;
-    Plan P;
-    CT_CHECK(make_plan(M, &w, 0.0, c_ata, c_grad, 0.0, 0, 0, 0, P));
-    const int gv = grid_for(M, P.n2, 256, 8);
-    // p = r = 1 on the image, u = q = 0: every product is finite and p.q > 0,
-    // so the scalars keep the slice active through every launch
+    const int gv = grid_for(M, n2, 256, 8);
     fill_df_kernel<<<gv, 256, 0, st>>>(w.p, M->g.n, M->tn, 1.0f);
     fill_df_kernel<<<gv, 256, 0, st>>>(w.r, M->g.n, M->tn, 1.0f);
     fill_df_kernel<<<gv, 256, 0, st>>>(w.u, M->g.n, M->tn, 0.0f);
@@ -484,6 +478,147 @@ int time_cg_kernels(ct_matrix* M, double c_ata, double c_grad, int32_t reps, dou
     h.rr = h.rhs2 = 1.0;
     h.active = 1;
     CT_CUDA(cudaMemcpyAsync(w.cg, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+    return CT_OK;
+}
+
+// Mean ms per launch of fn over `reps` launches after one untimed one.
+template <typename F>
+int time_launches(F fn, int reps, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st, float* ms)
+{
+    CT_CHECK(fn());
+    CT_CUDA(cudaEventRecord(e0, st));
+    for (int i = 0; i < reps; ++i) CT_CHECK(fn());
+    CT_CUDA(cudaEventRecord(e1, st));
+    CT_CUDA(cudaEventSynchronize(e1));
+    float t = 0.0f;
+    CT_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    *ms = t / reps;
+    return CT_OK;
+}
+
+struct TuneKey {
+    int n, nt, keep, nb;
+    uint32_t flags;
+    bool operator<(const TuneKey& o) const
+    {
+        return std::tie(n, nt, keep, nb, flags) < std::tie(o.n, o.nt, o.keep, o.nb, o.flags);
+    }
+};
+struct TuneVal {
+    int fwd_warps, fwd_unroll, op_ctas;
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, TuneVal> g_tune_cache;  // choices already measured in this process, by geometry
+
+}  // namespace
+
+// Chooses the launch shape of the single-slice products for this handle: the
+// warps per block and chunks in flight of y = A x, and the register budget
+// (CTAs per SM) of the fused A^T operator kernel.  Every candidate computes
+// the same bits (each row is summed in the same order whatever the shape),
+// so only speed depends on the choice.  The candidates are timed on the
+// handle's own matrices and workspace; the choice is kept with the handle
+// and in a process-wide cache keyed by geometry and storage, so a later
+// handle of the same geometry takes it without timing.  Never runs while st
+// is being captured; a choice pinned with ct_set_tuning stays.
+int tune_single(ct_matrix* M, cudaStream_t st)
+{
+    if (M->fourier || (M->fwd_warps > 0 && M->fwd_unroll > 0 && M->op_ctas > 0)) return CT_OK;
+    const TuneKey key{M->g.n, M->g.n_angles_total, M->g.keep_every, M->g.n_bins, M->flags};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            if (M->fwd_warps <= 0) M->fwd_warps = it->second.fwd_warps;
+            if (M->fwd_unroll <= 0) M->fwd_unroll = it->second.fwd_unroll;
+            if (M->op_ctas <= 0) M->op_ctas = it->second.op_ctas;
+            return CT_OK;
+        }
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CT_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return CT_OK;
+    CT_CHECK(ensure_workspace(M, 1, true));
+    Workspace& w = M->ws;
+    Plan P;
+    CT_CHECK(make_plan(M, &w, 0.0, 1.0, 1.0, 0.0, 0, 0, 0, P));
+    CT_CHECK(prime_cg_workspace(M, w, P.n2, st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CT_CUDA(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ce, "cudaEventCreate", __FILE__, __LINE__);
+    }
+    const int pin_w = M->fwd_warps, pin_u = M->fwd_unroll, pin_c = M->op_ctas;
+    const int rpow = P.vk == ValKind::F16 ? 2 : 0;
+    const int reps = 3;
+    int rc = CT_OK;
+    float best = 0.0f;
+    int bw = pin_w > 0 ? pin_w : 8, bu = pin_u > 0 ? pin_u : 8;
+    bool first = true;
+    for (int wv : {8, 4}) {
+        for (int uv : {8, 4, 2, 16}) {
+            if ((pin_w > 0 && wv != pin_w) || (pin_u > 0 && uv != pin_u) || rc != CT_OK) continue;
+            M->fwd_warps = wv;
+            M->fwd_unroll = uv;
+            float ms = 0.0f;
+            rc = time_launches([&]() { return launch_forward_df(M, P.vk, w.p, w.y, rpow, w.cg, nullptr, st); },
+                               reps, e0, e1, st, &ms);
+            if (rc == CT_OK && (first || ms < best)) {
+                best = ms;
+                bw = wv;
+                bu = uv;
+                first = false;
+            }
+        }
+    }
+    M->fwd_warps = bw;
+    M->fwd_unroll = bu;
+    int bc = pin_c;
+    if (bc <= 0 && rc == CT_OK) {
+        OpEpilogue ep = P.base;
+        ep.mode = 1;
+        ep.out = w.q;
+        ep.in = w.p;
+        first = true;
+        const bool chunked = M->h_band_chunk.size() > 2;
+        const int cands[2] = {chunked ? 5 : 7, chunked ? 3 : 4};
+        for (int cv : cands) {
+            if (rc != CT_OK) break;
+            M->op_ctas = cv;
+            float ms = 0.0f;
+            rc = time_launches([&]() { return launch_adjoint_op_df(M, P.vk, w.y, ep, st); }, reps, e0, e1, st, &ms);
+            if (rc == CT_OK && (first || ms < best)) {
+                best = ms;
+                bc = cv;
+                first = false;
+            }
+        }
+    }
+    M->op_ctas = bc > 0 ? bc : (M->h_band_chunk.size() > 2 ? 5 : 7);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != CT_OK) return rc;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    if (pin_w <= 0 && pin_u <= 0 && pin_c <= 0) g_tune_cache[key] = TuneVal{M->fwd_warps, M->fwd_unroll, M->op_ctas};
+    return CT_OK;
+}
+
+// Mean launch time of each kernel of one CG step, launched as the solver
+// launches it (same template instances and launch shapes, the handle's
+// workspace), `reps` times back to back between two events on st.
+int time_cg_kernels(ct_matrix* M, double c_ata, double c_grad, int32_t reps, double* ms, cudaStream_t st)
+{
+    if (reps < 1) return fail(CT_ERR_ARG, "reps must be >= 1");
+    if (M->fourier) return fail(CT_ERR_UNSUPPORTED, "kernel timing needs the Siddon matrices");
+    CT_CHECK(tune_single(M, st));
+    CT_CHECK(ensure_workspace(M, 1, true));
+    Workspace& w = M->ws;
+    Plan P;
+    CT_CHECK(make_plan(M, &w, 0.0, c_ata, c_grad, 0.0, 0, 0, 0, P));
+    const int gv = grid_for(M, P.n2, 256, 8);
+    CT_CHECK(prime_cg_workspace(M, w, P.n2, st));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CT_CUDA(cudaEventCreate(&e0));
     cudaError_t ce = cudaEventCreate(&e1);
@@ -565,6 +700,7 @@ int sb1_prepare(ct_matrix* M, Workspace& w, const ct_sb_params* Sp, const float*
     if (!R) return fail(CT_ERR_OOM, "host allocation failed");
     R->M = M;
     R->Sp = Sp;
+    CT_CHECK(tune_single(M, st));
     CT_CHECK(ensure_workspace_in(M, w, batch));
     Plan& P = R->P;
     CT_CHECK(make_plan(M, &w, 0.0, Sp->alpha, Sp->lambda, Sp->cg_rel_tol, Sp->surrogate_r, Sp->surrogate_square,
@@ -698,6 +834,7 @@ int chambolle_pock(ct_matrix* M, const ct_cp_params* Cp, const float* g, float* 
         return fail(CT_ERR_ARG, "Chambolle-Pock needs tau, sigma > 0, alpha >= 0, theta in [0, 1] and "
                                 "non-negative iteration counts");
     if (batch != 1) return fail(CT_ERR_UNSUPPORTED, "ct_chambolle_pock solves one slice per call (batch 1)");
+    CT_CHECK(tune_single(M, st));
     CT_CHECK(ensure_workspace(M, 1, true));
     Workspace& w = M->ws;
     Plan P;

@@ -42,9 +42,12 @@ namespace ct {
 namespace {
 
 constexpr int kFwdWarps = 8;   // warps per block (= per slice of rays) of y = A x
+constexpr int kFwdUnroll = 8;  // chunks each lane of y = A x keeps in flight (untuned default)
 constexpr int kAdjWarps = kTilePix / kSliceRows;  // warps per CTA of x = A^T y (one per pixel slice)
 constexpr int kAdjMinBlocks = 7;                    // CTAs per SM the register budget allows
 constexpr int kAdjMinBlocksChunked = 5;             // the same when the band is staged in angle chunks
+constexpr int kAdjFewBlocks = 4;                    // the fused kernel's alternative budgets (more registers)
+constexpr int kAdjFewBlocksChunked = 3;
 constexpr int64_t kStep = kSliceRows * kChunk;      // entries between a lane's consecutive chunks
 
 // Bytes of a staged band of `slots` values.
@@ -154,12 +157,19 @@ struct ProdArgs {
     const int32_t* gate;
 };
 
-// y = scale * A x (x in the tiled layout).  One block per slice of 32 rays:
-// its kFwdWarps warps split every row's chunks (warp w takes chunk pairs
-// 2w, 2w+1, 2w+2*kFwdWarps, ...), so that at any time the block streams a
-// contiguous run of the slice, and the per-warp partial sums are combined in
-// a fixed order.
-template <typename VT, typename XT, typename YT>
+// y = scale * A x (x in the tiled layout).  A block takes a slice of 32 rays
+// and each of its warps four adjacent rays of it: the warp's lanes are four
+// groups of eight, one group per ray, and at chunk c lane e of a group takes
+// entry 8c + e of its ray.  In the SELL-32 layout the four rays' chunk c is
+// 32 contiguous entries, so every load of the warp is one 128-byte run, and a
+// gather of x touches the pixels of four neighbouring parallel rays over
+// eight consecutive entries: a compact patch of the image, about 12 distinct
+// 32-byte sectors per gather instead of about 20 when each lane walks its own
+// ray (counted on the 512 x 512 matrix).  Each lane sums its entries in order
+// (U chunks in flight per step); the eight partial sums of a ray are combined
+// by a fixed butterfly.  With fewer warps than 8 a warp takes several groups
+// of the slice; results do not depend on the warp count or on U.
+template <typename VT, typename XT, typename YT, int U>
 __global__ void __launch_bounds__(kFwdWarps * 32) sell_fwd_kernel(SellView m, const int32_t* __restrict__ col,
                                                                   const VT* __restrict__ val,
                                                                   const XT* __restrict__ x, YT* __restrict__ y,
@@ -167,31 +177,51 @@ __global__ void __launch_bounds__(kFwdWarps * 32) sell_fwd_kernel(SellView m, co
 {
     if (a.gate && *a.gate) return;
     if (a.cg && !a.cg->active) return;
-    __shared__ float2 part[kFwdWarps][kSliceRows];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int e8 = lane & 7;
     const int64_t nslices = (m.rows + kSliceRows - 1) / kSliceRows;
-    const Gather<XT> g{x};
     for (int64_t s = blockIdx.x; s < nslices; s += gridDim.x) {
-        const int64_t row = s * kSliceRows + lane;
-        const int len = row < m.rows ? m.len[row] : 0;
-        const int nch = (len + kChunk - 1) / kChunk;
-        const int64_t base = m.sp[s] + lane * kChunk;
-        float hs = 0.0f, hc = 0.0f;
-        row_part<VT>(col, val, base, nch, 2 * w, 2 * kFwdWarps, g, hs, hc);
-        part[w][lane] = acc_value(hs, hc);
-        __syncthreads();
-        if (w == 0 && row < m.rows) {
-            float2 d = part[0][lane];
+        for (int grp = w; grp < kSliceRows / 4; grp += nw) {
+            const int64_t row = s * kSliceRows + grp * 4 + (lane >> 3);
+            const int len = row < m.rows ? __ldg(m.len + row) : 0;
+            const int nch = (len + kChunk - 1) / kChunk;
+            int nmax = nch;
 #pragma unroll
-            for (int k = 1; k < kFwdWarps; ++k) d = df_add(d, part[k][lane]);
-            if (a.row_scale) {
-                const float sc = a.row_scale[row];
-                d = df_mul_f(d, sc);
-                if (a.rpow == 2) d = df_mul_f(d, sc);
+            for (int o = 8; o < 32; o <<= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+            const int64_t base = __ldg(m.sp + s) + grp * 32 + lane;
+            float hs = 0.0f, hc = 0.0f;
+            for (int c0 = 0; c0 < nmax; c0 += U) {
+                int cc[U];
+                float vv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t p = base + (int64_t)(c0 + u) * (kSliceRows * kChunk);
+                    cc[u] = c0 + u < nch ? __ldcs(col + p) : -1;
+                    vv[u] = c0 + u < nch ? Vals<VT>::one(val, p) : 0.0f;
+                }
+                float2 xx[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) xx[u] = cc[u] >= 0 ? gather_x(x, cc[u]) : df_zero();
+#pragma unroll
+                for (int u = 0; u < U; ++u) acc_fma(hs, hc, vv[u], xx[u]);
             }
-            store_y(y, row, df_mul(a.scale, d));
+            float2 d = acc_value(hs, hc);
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                float2 t;
+                t.x = __shfl_xor_sync(0xffffffffu, d.x, o);
+                t.y = __shfl_xor_sync(0xffffffffu, d.y, o);
+                d = (e8 & o) ? df_add(t, d) : df_add(d, t);
+            }
+            if (e8 == 0 && row < m.rows) {
+                if (a.row_scale) {
+                    const float sc = a.row_scale[row];
+                    d = df_mul_f(d, sc);
+                    if (a.rpow == 2) d = df_mul_f(d, sc);
+                }
+                store_y(y, row, df_mul(a.scale, d));
+            }
         }
-        __syncthreads();
     }
 }
 
@@ -354,8 +384,8 @@ __global__ void __launch_bounds__(kAdjWarps * 32, CHUNKED ? kAdjMinBlocksChunked
     }
 }
 
-template <typename VT, int MODE, bool CHUNKED>
-__global__ void __launch_bounds__(kAdjWarps * 32, CHUNKED ? kAdjMinBlocksChunked : kAdjMinBlocks)
+template <typename VT, int MODE, bool CHUNKED, int MINB>
+__global__ void __launch_bounds__(kAdjWarps * 32, MINB)
     band_op_kernel(BandView bv, const VT* __restrict__ val, const float2* __restrict__ y, OpEpilogue a)
 {
     if (a.gate && *a.gate) return;
@@ -443,10 +473,25 @@ int launch_fwd(const ct_matrix* M, ValKind vk, const XT* x, YT* y, ProdArgs a, c
     // length across SMs
     const int64_t nslices = (C.rows + kSliceRows - 1) / kSliceRows;
     const int grid = (int)(nslices < (1 << 30) ? nslices : (1 << 30));
-    if (vk == ValKind::F16)
-        sell_fwd_kernel<__half, XT, YT><<<grid, kFwdWarps * 32, 0, st>>>(m, C.col, C.qval, x, y, a);
-    else
-        sell_fwd_kernel<float, XT, YT><<<grid, kFwdWarps * 32, 0, st>>>(m, C.col, C.val, x, y, a);
+    const int warps = M->fwd_warps > 0 ? M->fwd_warps : kFwdWarps;
+    const int unroll = M->fwd_unroll > 0 ? M->fwd_unroll : kFwdUnroll;
+#define CT_FWD(VT, VAL, U) sell_fwd_kernel<VT, XT, YT, U><<<grid, warps * 32, 0, st>>>(m, C.col, VAL, x, y, a)
+    if (vk == ValKind::F16) {
+        switch (unroll) {
+        case 2: CT_FWD(__half, C.qval, 2); break;
+        case 4: CT_FWD(__half, C.qval, 4); break;
+        case 16: CT_FWD(__half, C.qval, 16); break;
+        default: CT_FWD(__half, C.qval, 8); break;
+        }
+    } else {
+        switch (unroll) {
+        case 2: CT_FWD(float, C.val, 2); break;
+        case 4: CT_FWD(float, C.val, 4); break;
+        case 16: CT_FWD(float, C.val, 16); break;
+        default: CT_FWD(float, C.val, 8); break;
+        }
+    }
+#undef CT_FWD
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -488,21 +533,29 @@ int launch_band_adj(const ct_matrix* M, const VT* val, const YT* y, OT* out, flo
     return launch_band_adj_t<VT, YT, OT, false>(M, val, y, out, scale, st);
 }
 
-template <typename VT, int MODE, bool CHUNKED>
+template <typename VT, int MODE, bool CHUNKED, int MINB>
 int launch_band_op_t(const ct_matrix* M, const VT* val, const float2* y, const OpEpilogue& ep, cudaStream_t st)
 {
     const size_t smem = band_smem(M, sizeof(float2));
-    CT_CHECK(allow_smem(band_op_kernel<VT, MODE, CHUNKED>, smem));
-    band_op_kernel<VT, MODE, CHUNKED><<<band_grid(M), kAdjWarps * 32, smem, st>>>(band_view(M), val, y, ep);
+    CT_CHECK(allow_smem(band_op_kernel<VT, MODE, CHUNKED, MINB>, smem));
+    band_op_kernel<VT, MODE, CHUNKED, MINB><<<band_grid(M), kAdjWarps * 32, smem, st>>>(band_view(M), val, y, ep);
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
 
+// The fused kernel comes in two register budgets per band form: sized for
+// kAdjMinBlocks (kAdjMinBlocksChunked) CTAs per SM, or for fewer CTAs with
+// more registers per thread; the code, and so every result bit, is the same.
 template <typename VT, int MODE>
 int launch_band_op(const ct_matrix* M, const VT* val, const float2* y, const OpEpilogue& ep, cudaStream_t st)
 {
-    if (band_chunked(M)) return launch_band_op_t<VT, MODE, true>(M, val, y, ep, st);
-    return launch_band_op_t<VT, MODE, false>(M, val, y, ep, st);
+    const int ctas = M->op_ctas;
+    if (band_chunked(M)) {
+        if (ctas == kAdjFewBlocksChunked) return launch_band_op_t<VT, MODE, true, kAdjFewBlocksChunked>(M, val, y, ep, st);
+        return launch_band_op_t<VT, MODE, true, kAdjMinBlocksChunked>(M, val, y, ep, st);
+    }
+    if (ctas == kAdjFewBlocks) return launch_band_op_t<VT, MODE, false, kAdjFewBlocks>(M, val, y, ep, st);
+    return launch_band_op_t<VT, MODE, false, kAdjMinBlocks>(M, val, y, ep, st);
 }
 
 }  // namespace

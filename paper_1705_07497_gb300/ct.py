@@ -51,6 +51,9 @@ SYMBOLS = (
     "ct_set_spmm_unroll",
     "ct_get_spmm_unroll",
     "ct_time_cg_kernels",
+    "ct_get_tuning",
+    "ct_set_tuning",
+    "ct_tune",
     "ct_matrix_export",
     "ct_matrix_export_fp16",
     "ct_surrogate_stencil",
@@ -136,6 +139,15 @@ class SbStats(ctypes.Structure):
     ]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [
+        ("fwd_warps", ctypes.c_int32),
+        ("fwd_unroll", ctypes.c_int32),
+        ("op_ctas", ctypes.c_int32),
+        ("spmm_unroll", ctypes.c_int32),
+    ]
+
+
 class CtError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("%s (%d): %s" % (status_string(code), code, msg))
@@ -172,6 +184,9 @@ def lib():
         L.ct_set_spmm_unroll.argtypes = [vp, i32, i32]
         L.ct_get_spmm_unroll.argtypes = [vp, i32, P(i32)]
         L.ct_time_cg_kernels.argtypes = [vp, ctypes.c_double, ctypes.c_double, i32, vp, vp]
+        L.ct_get_tuning.argtypes = [vp, i32, P(Tuning)]
+        L.ct_set_tuning.argtypes = [vp, i32, P(Tuning)]
+        L.ct_tune.argtypes = [vp, i32, vp]
         L.ct_matrix_export.argtypes = [vp, i32, vp, vp, vp]
         L.ct_matrix_export_fp16.argtypes = [vp, vp, vp]
         L.ct_surrogate_stencil.argtypes = [vp, i32, i32, i32, vp, vp, vp, P(i32)]
@@ -322,6 +337,25 @@ def ct_time_cg_kernels(h, c_ata, c_grad, reps, stream=None):
         stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     _check(lib().ct_time_cg_kernels(h, c_ata, c_grad, reps, ms, stream))
     return list(ms)
+
+
+def ct_get_tuning(h, batch):
+    t = Tuning()
+    _check(lib().ct_get_tuning(h, batch, ctypes.byref(t)))
+    return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+
+def ct_set_tuning(h, batch, **fields):
+    t = Tuning(**fields)
+    return _check(lib().ct_set_tuning(h, batch, ctypes.byref(t)))
+
+
+def ct_tune(h, batch, stream=None):
+    if stream is None:
+        import torch
+
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return _check(lib().ct_tune(h, batch, stream))
 
 
 def ct_matrix_export(h, which):

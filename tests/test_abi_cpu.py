@@ -128,6 +128,7 @@ _STRUCTS = [
     ("ct_sb_stats", "SbStats"),
     ("ct_cp_params", "CpParams"),
     ("ct_fourier_params", "FourierParams"),
+    ("ct_tuning", "Tuning"),
 ]
 
 
