@@ -850,6 +850,25 @@ def bench_grad(args):
     clocks = sampler.stop()
     secs = e0.elapsed_time(e1) / 1e3
     assert torch.isfinite(g).all()
+    # kernels launched by one step (forward and backward), counted by the
+    # torch profiler outside the timed region: the library's and torch's
+    launches = None
+    try:
+        from torch.profiler import ProfilerActivity, profile
+
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            step()
+            torch.cuda.synchronize()
+        kern = [e for e in prof.events() if e.device_type == torch.autograd.DeviceType.CUDA
+                and "memcpy" not in e.name.lower() and "memset" not in e.name.lower()]
+        ours = [e for e in kern if "ct::" in e.name or "unnamed" in e.name]
+        cg_steps = wl["outer"] * (wl["inner"] + 1)
+        launches = {"per_step": len(kern), "library_kernels": len(ours), "torch_kernels": len(kern) - len(ours),
+                    "per_cg_step_forward_and_backward": round(len(kern) / cg_steps, 1),
+                    "note": "one step = forward with checkpoints, recomputation and backward; %d CG steps "
+                            "(with the warm-start residual) per forward" % cg_steps}
+    except Exception as exc:  # the profiler is optional here
+        launches = {"unavailable": str(exc)[:200]}
     # the FP64 forward product alone: one FP64 FMA per entry and slice
     Xd = torch.zeros((n * n, B), dtype=torch.float64, device=dev)
     Yd = torch.empty((M.rows, B), dtype=torch.float64, device=dev)
@@ -898,7 +917,8 @@ def bench_grad(args):
             "launch_ms": round(t_f64 * 1e3, 3),
         },
         "e2e": None,
-        "gpu_launches": None,
+        "gpu_launches": (launches["per_step"] * args.steps) if "per_step" in launches else None,
+        "launch_count": launches,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:

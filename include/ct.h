@@ -58,9 +58,8 @@ enum {
     CT_ERR_OOM = -3,         /* device or host allocation failed                 */
     CT_ERR_BREAKDOWN = -4,   /* CG saw p^T Op p <= 0 with a nonzero residual     */
     CT_ERR_NONFINITE = -5,   /* NaN or Inf met in a residual, dot or update      */
-    CT_ERR_TIMEOUT = -6,     /* reserved: a bounded device-side wait expired (no
-                              * kernel of this library waits on another, so no
-                              * call returns it today)                           */
+    CT_ERR_TIMEOUT = -6,     /* a bounded device-side wait expired (the persistent
+                              * ragged-batch kernel of ct_split_bregman_ragged)  */
     CT_ERR_UNSUPPORTED = -7  /* option not available for this matrix / build     */
 };
 
@@ -119,6 +118,17 @@ int ct_adjoint(ct_matrix_t A, const float *y, float *x, int32_t batch, void *cud
  * derivatives of the unrolled reconstruction need the accuracy). */
 int ct_forward_f64(ct_matrix_t A, const double *x, double *y, int32_t batch, void *cuda_stream);
 int ct_adjoint_f64(ct_matrix_t A, const double *y, double *x, int32_t batch, void *cuda_stream);
+
+/* out = alpha A^T A x + lambda grad^T grad x: the operator of Eq. SB_solve
+ * (with "+ lambda K*K", K = grad) on FP64 vectors [N*N][batch] in the
+ * caller's row-major image order (forward differences, last difference
+ * zero).  Two FP64-vector products (as ct_forward_f64 / ct_adjoint_f64) and
+ * one fused stencil pass; the operator is symmetric, so it is also its own
+ * derivative (the differentiable reconstruction's backward pass uses it).
+ * Device pointers only; x and out must not overlap.  Asynchronous.
+ * Errors: CT_ERR_ARG, CT_ERR_UNSUPPORTED (Fourier handle), CT_ERR_CUDA. */
+int ct_normal_f64(ct_matrix_t A, double alpha, double lambda, const double *x, double *out, int32_t batch,
+                  void *cuda_stream);
 
 typedef struct {
     double c_id, c_ata, c_grad; /* Op = c_id I + c_ata A^T A (or T) + c_grad grad^T grad.
@@ -212,16 +222,28 @@ int ct_chambolle_pock(ct_matrix_t A, const ct_cp_params *params, const float *g,
  * scanners at once).  Problem i uses matrix A[i] (its geometry), data f[i]
  * ([rows_i], device pointer) and image u[i] ([N_i*N_i], device pointer; in =
  * initial guess, out = reconstruction); every problem runs with the same
- * params.  Problems that share a handle are solved together as one batch of
- * that handle (SpMM); the groups' Bregman updates are captured in one CUDA
- * graph, each group on its own stream so small problems run side by side,
- * and the graph is replayed outer_iters times.  The u[i] must not overlap
+ * params.  When every handle serves at most eight of the problems and the
+ * operator is the exact one (surrogate_r = 0, refresh_every = 0), each
+ * problem runs as a single-slice solve and one Bregman update of all of them
+ * is ONE persistent cooperative kernel launch: its CTAs take work items
+ * (a few 32-ray slices, an image tile or a run of pixels of one phase of one
+ * problem) from a device queue that interleaves the problems phase by phase,
+ * and an item waits, with a bounded spin, until the previous phase of its
+ * problem is complete; the launch is captured into a CUDA graph that is
+ * replayed outer_iters times.  A wait that runs out sets CT_ERR_TIMEOUT and
+ * makes every CTA stop (see ct_set_wait_limit).  Otherwise problems that
+ * share a handle are solved together as one batch of that handle (SpMM), the
+ * groups' Bregman updates are captured in one CUDA graph, each group on its
+ * own stream, and the graph is replayed outer_iters times.  The call
+ * synchronises cuda_stream when it takes the persistent form.  The u[i] must not overlap
  * each other or any f[j].  stats: NULL, or an array of `count` entries, one
  * per problem (then the call synchronises on cuda_stream).  Handles must live
  * on the current device; calls sharing a handle must be serialised like any
  * solver call.  Errors: CT_ERR_ARG (count < 1, NULL arrays or pointers, host
- * pointers, bad params), CT_ERR_OOM, CT_ERR_CUDA, and per problem
- * CT_ERR_BREAKDOWN / CT_ERR_NONFINITE (the first one met is returned). */
+ * pointers, bad params), CT_ERR_OOM, CT_ERR_CUDA, CT_ERR_TIMEOUT (a bounded
+ * wait of the persistent kernel expired; the problems' images are then not
+ * valid), and per problem CT_ERR_BREAKDOWN / CT_ERR_NONFINITE (the first one
+ * met is returned). */
 int ct_split_bregman_ragged(int32_t count, const ct_matrix_t *A, const float *const *f, float *const *u,
                             const ct_sb_params *params, ct_sb_stats *stats, void *cuda_stream);
 
@@ -237,6 +259,17 @@ int ct_split_bregman_ragged(int32_t count, const ct_matrix_t *A, const float *co
  * Errors: CT_ERR_ARG (batch < 2, other unroll values, NULL output). */
 int ct_set_spmm_unroll(ct_matrix_t A, int32_t batch, int32_t unroll);
 int ct_get_spmm_unroll(ct_matrix_t A, int32_t batch, int32_t *unroll);
+
+/* Bounded waits of the persistent ragged-batch kernel (no counterpart in the
+ * paper).  Every wait of that kernel polls at most `polls` times (about
+ * 128 ns or more apart) and then gives up with CT_ERR_TIMEOUT; polls <= 0
+ * restores the default (about a second).  hold_first != 0 makes the first
+ * phase of every problem wait for a flag that nothing ever sets, so that the
+ * next ct_split_bregman_ragged call in persistent form runs out of its waits
+ * and returns CT_ERR_TIMEOUT without touching the images: this exercises the
+ * timeout path on a GPU without faulting it.  Process-wide; takes effect at
+ * the next call.  Always returns CT_OK. */
+int ct_set_wait_limit(int64_t polls, int32_t hold_first);
 
 /* Launch shapes of the sparse products (no counterpart in the paper).  Each
  * product comes in launch shapes that all compute the same bits (every row is

@@ -6,9 +6,10 @@ Test infrastructure only (see the package docstring).
 ``A.T @ y`` of real FP64 vectors run the plain row loop of ``spmv.c`` on
 several host threads; every row is still summed in storage order by one
 thread, so the products equal a sequential loop's whatever the thread count.
-Anything else (complex vectors for complex-step derivatives, 2-D operands)
-falls back to scipy.  The solvers in ``tv`` take any object with ``@`` and
-``.T``, so a wrapped matrix drops in for the plain one.
+A complex vector (complex-step derivatives) takes two real products, one per
+part; anything else (2-D operands) falls back to scipy.  The solvers in
+``tv`` take any object with ``@`` and ``.T``, so a wrapped matrix drops in
+for the plain one.
 """
 
 import os
@@ -43,6 +44,10 @@ class ThreadedCSR:
 
     def __matmul__(self, x):
         x = np.asarray(x)
+        if x.ndim == 1 and x.dtype == np.complex128:
+            # A is real: the real and imaginary parts are two real products,
+            # each row summed in the same order as the complex product
+            return self @ np.ascontiguousarray(x.real) + 1j * (self @ np.ascontiguousarray(x.imag))
         if x.ndim != 1 or x.dtype != np.float64:
             return self.A @ x
         x = np.ascontiguousarray(x)

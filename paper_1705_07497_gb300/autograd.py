@@ -11,10 +11,11 @@ ct_adjoint_f64.  Vectors are [N*N] or [N*N, B] (images) and [rows] or
 ``split_bregman_unrolled`` writes anisotropic-TV split Bregman (Sec. 4 of the
 paper, the system of Eq. SB_solve with "+ lambda K*K" and v = d - b) with a
 fixed number of warm-started CG steps per update, in torch operations around
-those two Functions, so that the reconstruction is differentiable with
-respect to the data f.  Each Bregman update can be wrapped in
-torch.utils.checkpoint, so the backward pass keeps one update's graph at a
-time and recomputes it.
+those Functions (and, for FP64 vectors, ``NormalOp``: the whole operator of
+Eq. SB_solve in one library call), so that the reconstruction is
+differentiable with respect to the data f.  Each Bregman update can be
+wrapped in torch.utils.checkpoint, so the backward pass keeps one update's
+graph at a time and recomputes it.
 """
 
 import torch
@@ -66,6 +67,31 @@ class RadonAdjoint(torch.autograd.Function):
         return None, gy
 
 
+class NormalOp(torch.autograd.Function):
+    """out = alpha A^T A x + lambda grad^T grad x on FP64 vectors, the library's
+    fused ct_normal_f64 (two products and one stencil pass).  The operator is
+    symmetric, so its backward is the same operator applied to the incoming
+    gradient."""
+
+    @staticmethod
+    def forward(ctx, M, x, alpha, lam):
+        ctx.M, ctx.alpha, ctx.lam = M, alpha, lam
+        return _normal_f64(M, x.contiguous(), alpha, lam)
+
+    @staticmethod
+    def backward(ctx, g):
+        return None, _normal_f64(ctx.M, g.contiguous(), ctx.alpha, ctx.lam), None, None
+
+
+def _normal_f64(M, x, alpha, lam):
+    from . import ct
+
+    out = torch.empty_like(x)
+    ct.ct_normal_f64(M.handle, alpha, lam, x, out, x.shape[1] if x.dim() == 2 else 1,
+                     torch.cuda.current_stream(x.device).cuda_stream)
+    return out
+
+
 def radon(M, x):
     return RadonForward.apply(M, x)
 
@@ -104,6 +130,10 @@ def shrink(x, gamma):
 
 
 def _normal_op(M, p, alpha, lam, n):
+    """alpha A^T A p + lambda grad^T grad p: the fused library operator for FP64
+    vectors; FP32 vectors compose the FP32 products with torch's differences."""
+    if p.dtype == torch.float64:
+        return NormalOp.apply(M, p, alpha, lam)
     return alpha * radon_adjoint(M, radon(M, p)) + lam * grad2d_adj(*grad2d(p, n), n)
 
 

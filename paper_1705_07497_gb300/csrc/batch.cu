@@ -1255,7 +1255,16 @@ int split_bregman_ragged(int32_t count, ct_matrix* const* A, const float* const*
             caps.push_back(M->ws.cap_stream);
         }
     }
-    CT_CHECK(run_updates(fns, caps, Sp->outer_iters, st));
+    // every group a set of single-slice runs: one persistent launch per
+    // update (ragged.cu); else one captured graph of the groups' launches
+    bool persistent = false;
+    if (std::all_of(members.begin(), members.end(), [](const std::vector<int>& m) { return (int)m.size() <= kRaggedSingles; })) {
+        std::vector<Sb1Run*> all;
+        for (size_t g = 0; g < G; ++g)
+            for (auto& r : runs1[g]) all.push_back(r.get());
+        CT_CHECK(ragged_persistent(all, Sp->outer_iters, st, caps[0], &persistent));
+    }
+    if (!persistent) CT_CHECK(run_updates(fns, caps, Sp->outer_iters, st));
     int status = CT_OK;
     std::vector<ct_sb_stats> gs;
     for (size_t g = 0; g < G; ++g) {

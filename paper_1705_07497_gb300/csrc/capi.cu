@@ -257,6 +257,18 @@ int ct_adjoint_f64(ct_matrix_t A, const double* y, double* x, int32_t batch, voi
     return launch_adjoint_f64(A, storage_kind(A), y, x, batch, (cudaStream_t)cuda_stream);
 }
 
+int ct_normal_f64(ct_matrix_t A, double alpha, double lambda, const double* x, double* out, int32_t batch,
+                  void* cuda_stream)
+{
+    CT_CHECK(check_handle(A));
+    CT_CHECK(no_fourier(A, "ct_normal_f64"));
+    if (batch < 1) return fail(CT_ERR_ARG, "batch must be >= 1");
+    if (!x || !out || !is_device_ptr(x) || !is_device_ptr(out))
+        return fail(CT_ERR_ARG, "ct_normal_f64 needs device pointers");
+    if (x == out) return fail(CT_ERR_ARG, "ct_normal_f64 cannot work in place");
+    return normal_f64(A, alpha, lambda, x, out, batch, (cudaStream_t)cuda_stream);
+}
+
 int ct_cg_solve(ct_matrix_t A, const ct_cg_params* params, const float* rhs, float* u,
                 int32_t batch, ct_cg_stats* stats, void* cuda_stream)
 {
@@ -404,6 +416,12 @@ int ct_time_cg_kernels(ct_matrix_t A, double c_ata, double c_grad, int32_t reps,
     if (!ms) return fail(CT_ERR_ARG, "NULL output array");
     CT_CHECK(no_fourier(A, "ct_time_cg_kernels"));
     return time_cg_kernels(A, c_ata, c_grad, reps, ms, (cudaStream_t)cuda_stream);
+}
+
+int ct_set_wait_limit(int64_t polls, int32_t hold_first)
+{
+    set_wait_limit((long long)polls, hold_first);
+    return CT_OK;
 }
 
 int ct_set_spmm_unroll(ct_matrix_t A, int32_t batch, int32_t unroll)

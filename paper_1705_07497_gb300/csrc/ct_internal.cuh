@@ -111,6 +111,8 @@ struct Workspace {
     float2 *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *rhs = nullptr;
     float2 *atf = nullptr, *u_old = nullptr, *bx = nullptr, *by = nullptr, *vx = nullptr, *vy = nullptr;
     float2* y = nullptr;                   // sinogram temp [rows][batch]
+    double* f64_y = nullptr;               // ct_normal_f64: the sinogram temp [rows][batch]
+    int64_t f64_y_len = 0;
     float2* pub_y2 = nullptr;              // ct_adjoint with FP16 storage: s .* y
     int64_t pub_y2_len = 0;
     float* pub_x = nullptr;                // ct_forward: the caller's image in tile order
@@ -189,6 +191,9 @@ int launch_forward(const ct_matrix* M, ValKind vk, const float* x, float* y, int
 int launch_adjoint(const ct_matrix* M, ValKind vk, const float* y, float* x, int32_t batch, cudaStream_t st);
 int launch_forward_f64(const ct_matrix* M, ValKind vk, const double* x, double* y, int32_t batch, cudaStream_t st);
 int launch_adjoint_f64(const ct_matrix* M, ValKind vk, const double* y, double* x, int32_t batch, cudaStream_t st);
+// out = alpha A^T A x + lambda grad^T grad x in FP64 (row-major vectors)
+int normal_f64(const ct_matrix* M, double alpha, double lam, const double* x, double* out, int32_t B,
+               cudaStream_t st);
 
 // Epilogue of the adjoint product inside the CG operator (double-float vectors).
 struct OpEpilogue {
@@ -265,6 +270,24 @@ int sb1_prepare(ct_matrix* M, Workspace& w, const ct_sb_params* Sp, const float*
 int sb1_update(Sb1Run* r, cudaStream_t s);
 int sb1_finish(Sb1Run* r, float* u, ct_sb_stats* stats, cudaStream_t st);
 void sb1_free(Sb1Run* r);
+// What the persistent ragged-batch kernel (ragged.cu) takes from a prepared
+// single-slice run: the operator's plan and the solver parameters.
+struct Sb1Desc {
+    ct_matrix* M;
+    Workspace* w;
+    OpEpilogue base;   // the plan's epilogue (coefficients, gate, data term, CG scalars)
+    ValKind vk;
+    bool exact;        // A^T A through the sparse products (no surrogate, no refresh)
+    double gamma;      // shrink threshold 1 / lambda
+    double stop_tol;   // Sec. 4 stopping rule
+    int inner;         // CG steps per update
+};
+void sb1_describe(const Sb1Run* r, Sb1Desc* d);
+// ragged.cu: every prepared single-slice run's updates as one persistent
+// launch per update; *used = false when a run is outside its scope.
+int ragged_persistent(const std::vector<Sb1Run*>& runs, int outer, cudaStream_t st, cudaStream_t cap, bool* used);
+// bounded-wait limit (polls) of the persistent kernel and the held-dependency test switch
+void set_wait_limit(long long polls, int hold);
 int chambolle_pock(ct_matrix* M, const ct_cp_params* Cp, const float* g, float* u, int32_t batch,
                    ct_sb_stats* stats, cudaStream_t st);
 int split_bregman_ragged(int32_t count, ct_matrix* const* A, const float* const* f, float* const* u,

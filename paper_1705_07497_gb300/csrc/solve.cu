@@ -348,6 +348,7 @@ void free_workspace(Workspace& w)
     cudaFree(w.stage_a);
     cudaFree(w.stage_b);
     cudaFree(w.pub_x);
+    cudaFree(w.f64_y);
     cudaFree(w.partials);
     cudaFree(w.counter);
     cudaFree(w.cg);
@@ -690,6 +691,18 @@ struct Sb1Run {
 };
 
 void sb1_free(Sb1Run* r) { delete r; }
+
+void sb1_describe(const Sb1Run* r, Sb1Desc* d)
+{
+    d->M = r->M;
+    d->w = r->P.w;
+    d->base = r->P.base;
+    d->vk = r->P.vk;
+    d->exact = r->P.sparse && !r->M->fourier && r->P.refresh == 0;
+    d->gamma = 1.0 / r->Sp->lambda;
+    d->stop_tol = r->Sp->stop_rel_update;
+    d->inner = r->Sp->inner_cg_iters;
+}
 
 int sb1_prepare(ct_matrix* M, Workspace& w, const ct_sb_params* Sp, const float* f, const float* u, Sb1Run** out,
                 cudaStream_t st)

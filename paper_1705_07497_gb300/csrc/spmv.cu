@@ -167,7 +167,49 @@ int product_f64(const ct_matrix* M, int which, const double* in, double* out, in
     return CT_OK;
 }
 
+// out = alpha * out + lambda * (grad^T grad x), FP64 vectors [N*N][B] in the
+// caller's row-major order; forward differences with a zero last difference.
+__global__ void normal_epilogue_f64_kernel(const double* __restrict__ x, double* __restrict__ out, int n, int B,
+                                           double alpha, double lam)
+{
+    const int64_t total = (int64_t)n * n * B;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = k / B;
+        const int i = (int)(p / n), j = (int)(p - (int64_t)i * n);
+        const double c = x[k];
+        double lap = 0.0;
+        if (j > 0) lap += c - x[k - B];
+        if (j < n - 1) lap += c - x[k + B];
+        if (i > 0) lap += c - x[k - (int64_t)n * B];
+        if (i < n - 1) lap += c - x[k + (int64_t)n * B];
+        out[k] = alpha * out[k] + lam * lap;
+    }
+}
+
 }  // namespace
+
+int normal_f64(const ct_matrix* M, double alpha, double lam, const double* x, double* out, int32_t B,
+               cudaStream_t st)
+{
+    ct_matrix* Mm = const_cast<ct_matrix*>(M);
+    Workspace& w = Mm->ws;
+    const int64_t need = M->rows * (int64_t)B;
+    if (w.f64_y_len < need) {
+        cudaFree(w.f64_y);
+        w.f64_y = nullptr;
+        w.f64_y_len = 0;
+        const cudaError_t e = cudaMalloc((void**)&w.f64_y, (size_t)need * sizeof(double));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(FP64 sinogram temp)", __FILE__, __LINE__);
+        w.f64_y_len = need;
+    }
+    CT_CHECK(product_f64(M, 0, x, w.f64_y, B, st));
+    CT_CHECK(product_f64(M, 1, w.f64_y, out, B, st));
+    const int64_t total = (int64_t)M->g.n * M->g.n * B;
+    normal_epilogue_f64_kernel<<<grid_for(M, total, 256, 8), 256, 0, st>>>(x, out, M->g.n, B, alpha, lam);
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
 
 int grid_for(const ct_matrix* M, int64_t work_items, int items_per_block, int max_per_sm)
 {

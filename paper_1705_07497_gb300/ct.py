@@ -54,6 +54,8 @@ SYMBOLS = (
     "ct_get_tuning",
     "ct_set_tuning",
     "ct_tune",
+    "ct_set_wait_limit",
+    "ct_normal_f64",
     "ct_matrix_export",
     "ct_matrix_export_fp16",
     "ct_surrogate_stencil",
@@ -187,6 +189,8 @@ def lib():
         L.ct_get_tuning.argtypes = [vp, i32, P(Tuning)]
         L.ct_set_tuning.argtypes = [vp, i32, P(Tuning)]
         L.ct_tune.argtypes = [vp, i32, vp]
+        L.ct_set_wait_limit.argtypes = [i64, i32]
+        L.ct_normal_f64.argtypes = [vp, ctypes.c_double, ctypes.c_double, vp, vp, i32, vp]
         L.ct_matrix_export.argtypes = [vp, i32, vp, vp, vp]
         L.ct_matrix_export_fp16.argtypes = [vp, vp, vp]
         L.ct_surrogate_stencil.argtypes = [vp, i32, i32, i32, vp, vp, vp, P(i32)]
@@ -279,6 +283,12 @@ def ct_adjoint_f64(h, y, x, batch, stream=None):
     return _check(lib().ct_adjoint_f64(h, py, px, batch, sy if stream is None else stream))
 
 
+def ct_normal_f64(h, alpha, lam, x, out, batch, stream=None):
+    px, sx = _vec(x, f64=True)
+    po, _ = _vec(out, f64=True)
+    return _check(lib().ct_normal_f64(h, alpha, lam, px, po, batch, sx if stream is None else stream))
+
+
 def ct_cg_solve(h, params, rhs, u, batch, stats=None, stream=None):
     pr, sr = _vec(rhs)
     pu, _ = _vec(u)
@@ -356,6 +366,12 @@ def ct_tune(h, batch, stream=None):
 
         stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     return _check(lib().ct_tune(h, batch, stream))
+
+
+def ct_set_wait_limit(polls, hold_first=False):
+    """Bounded-wait limit of the persistent ragged kernel (polls <= 0: the
+    default); hold_first makes the next persistent call run out of its waits."""
+    return _check(lib().ct_set_wait_limit(int(polls), int(bool(hold_first))))
 
 
 def ct_matrix_export(h, which):

@@ -122,3 +122,52 @@ def test_ragged_large_group_uses_the_batched_products(dev):
         want = tv.split_bregman(oracle_A(*geom), f, (n, n), 1.0, 0.5, 5, 8)
         assert rel(us[k].cpu().numpy(), want["u"].ravel()) <= 1e-4, k
         assert stats[k]["outer_done"] == 5
+
+
+def test_ragged_persistent_kernel_with_staged_band_chunks_and_fp16(dev):
+    """The persistent kernel on geometries whose sinogram band is staged in
+    angle chunks (360 kept angles) beside small ones, FP16 and FP32 storage."""
+    geoms = [(64, 360, 1, 91), (32, 40, 1, 46), (48, 400, 1, 68)]
+    flags = [ct.CT_VAL_FP32, ct.CT_VAL_FP16_ROWSCALE, ct.CT_VAL_FP32]
+    mats, fs, us, refs = [], [], [], []
+    for k, (geom, fl) in enumerate(zip(geoms, flags)):
+        A = oracle_A(*geom)
+        f = inputs.gaussian_noisy(A @ inputs.ellipse_phantom(geom[0], 4500 + k).ravel(), 0.01, 4600 + k)
+        if fl == ct.CT_VAL_FP16_ROWSCALE:
+            s, Q = radon.quantize_rowscale(A)
+            A = radon.dequantize(s, Q).tocsr()
+        refs.append(tv.split_bregman(A, f, (geom[0], geom[0]), 1.0, 0.5, 4, 6)["u"].ravel())
+        mats.append(gpu_A(geom, fl))
+        fs.append(torch.tensor(f, dtype=torch.float32, device=dev))
+        us.append(torch.zeros(geom[0] * geom[0], dtype=torch.float32, device=dev))
+    stats = ct.split_bregman_ragged(mats, fs, us, 1.0, 0.5, 4, 6)
+    for k in range(len(geoms)):
+        assert stats[k]["status"] == 0 and stats[k]["outer_done"] == 4
+        assert rel(us[k].cpu().numpy(), refs[k]) <= 1e-4, k
+
+
+def test_ragged_bounded_wait_runs_out_and_the_gpu_answers_after(dev):
+    """A dependency held back on purpose (a flag nothing sets) with a short
+    wait limit: the persistent kernel returns CT_ERR_TIMEOUT instead of
+    hanging, and the next call (default limit) solves correctly."""
+    probs = _problems([0, 2, 1], 4700)
+    mats = [gpu_A(g) for g, _ in probs]
+    fs = [torch.tensor(f, dtype=torch.float32, device=dev) for _, f in probs]
+    us = [torch.zeros(g[0] * g[0], dtype=torch.float32, device=dev) for g, _ in probs]
+    ct.ct_set_wait_limit(2000, hold_first=True)
+    try:
+        with pytest.raises(ct.CtError) as e:
+            ct.split_bregman_ragged(mats, fs, us, 1.0, 0.5, 3, 8)
+        assert e.value.code == ct.CT_ERR_TIMEOUT
+        assert "bounded wait" in str(e.value)
+    finally:
+        ct.ct_set_wait_limit(0, hold_first=False)
+    torch.cuda.synchronize()
+    for u in us:
+        u.zero_()
+    stats = ct.split_bregman_ragged(mats, fs, us, 1.0, 0.5, 3, 8)
+    for k, (geom, f) in enumerate(probs):
+        n = geom[0]
+        want = tv.split_bregman(oracle_A(*geom), f, (n, n), 1.0, 0.5, 3, 8)
+        assert stats[k]["status"] == 0
+        assert rel(us[k].cpu().numpy(), want["u"].ravel()) <= 1e-4, k
