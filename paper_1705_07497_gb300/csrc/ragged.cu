@@ -573,13 +573,14 @@ int ragged_persistent(const std::vector<Sb1Run*>& runs, int outer, cudaStream_t 
         return CT_OK;
     };
     rc = run_updates({update}, {cap}, outer, st);
+    bool direct = false;
     if (rc != CT_OK) {
         // a capture the runtime refused: run the updates directly on st
         (void)cudaGetLastError();
-        set_error("");
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
             rc = CT_OK;
+            direct = true;
             for (int k = 0; k < outer && rc == CT_OK; ++k) rc = update(st);
         }
     }
@@ -594,6 +595,11 @@ int ragged_persistent(const std::vector<Sb1Run*>& runs, int outer, cudaStream_t 
     release();
     if (rc != CT_OK) return rc;
     *used = true;
+    // a note, not a failure: ct_last_error() tells that the updates ran as
+    // separate launches because the graph capture was refused
+    set_error(direct ? "ragged: the CUDA graph capture of the persistent kernel was refused; the updates ran as "
+                       "direct launches"
+                     : "");
     if (h.status != CT_OK) {
         const int w = h.where;
         std::string where = "?";

@@ -58,6 +58,8 @@ def test_ragged_matches_per_problem_oracle(dev, outer):
     fs = [torch.tensor(f, dtype=torch.float32, device=dev) for _, f in probs]
     us = [torch.zeros(g[0] * g[0], dtype=torch.float32, device=dev) for g, _ in probs]
     stats = ct.split_bregman_ragged(mats, fs, us, 1.0, 0.5, outer, 8)
+    # the persistent launch was captured into a graph (outer > 2) or launched directly
+    assert ct.lib().ct_last_error() == b"", ct.lib().ct_last_error()
     for k, (geom, f) in enumerate(probs):
         n = geom[0]
         want = tv.split_bregman(oracle_A(*geom), f, (n, n), 1.0, 0.5, outer, 8)
