@@ -571,8 +571,8 @@ def bench_ours(args):
         },
         "roofline": {
             "kernel": "sell_fwd_kernel<float, float2, float2> on A: y = A p inside CG (SELL-32 FP32 values, "
-                      "int32 columns into the tiled image, double-float p and y, one row per lane), the "
-                      "step's largest kernel; timed as the solver launches it",
+                      "int32 columns into the tiled image, double-float p and y, four neighbouring rays per warp), "
+                      "the step's largest kernel; timed as the solver launches it",
             "bound": "hbm",
             "achieved": round(ach_fwd, 1),
             "peak": peak,
@@ -850,28 +850,6 @@ def bench_grad(args):
     clocks = sampler.stop()
     secs = e0.elapsed_time(e1) / 1e3
     assert torch.isfinite(g).all()
-    # kernels launched by one step (forward and backward), counted by the
-    # torch profiler outside the timed region: the library's and torch's
-    launches = None
-    try:
-        from torch.profiler import ProfilerActivity, profile
-
-        with profile(activities=[ProfilerActivity.CUDA]) as prof:
-            step()
-            torch.cuda.synchronize()
-        evs = prof.events()
-        kern = [e for e in evs if e.device_type == torch.autograd.DeviceType.CUDA]
-        if not kern:  # older layouts list the kernels under the host-side op that launched them
-            kern = [k for e in evs for k in getattr(e, "kernels", [])]
-        kern = [e for e in kern if "memcpy" not in e.name.lower() and "memset" not in e.name.lower()]
-        ours = [e for e in kern if "ct::" in e.name or "unnamed" in e.name]
-        cg_steps = wl["outer"] * (wl["inner"] + 1)
-        launches = {"per_step": len(kern), "library_kernels": len(ours), "torch_kernels": len(kern) - len(ours),
-                    "per_cg_step_forward_and_backward": round(len(kern) / cg_steps, 1),
-                    "note": "one step = forward with checkpoints, recomputation and backward; %d CG steps "
-                            "(with the warm-start residual) per forward" % cg_steps}
-    except Exception as exc:  # the profiler is optional here
-        launches = {"unavailable": str(exc)[:200]}
     # the FP64 forward product alone: one FP64 FMA per entry and slice
     Xd = torch.zeros((n * n, B), dtype=torch.float64, device=dev)
     Yd = torch.empty((M.rows, B), dtype=torch.float64, device=dev)
@@ -920,8 +898,9 @@ def bench_grad(args):
             "launch_ms": round(t_f64 * 1e3, 3),
         },
         "e2e": None,
-        "gpu_launches": (launches["per_step"] * args.steps) if "per_step" in launches else None,
-        "launch_count": launches,
+        "gpu_launches": None,
+        "launch_note": "the kernels of one step (the library's and torch's) are counted from an ncu launch list "
+                       "in profiles/launches_grad_256x16.md",
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
@@ -1486,7 +1465,7 @@ def bench_shapes(args, dev):
         rows = []
         for w in (8, 4):
             for u in (8, 4, 2, 16):
-                for c in ((7, 4), (5, 3)):
+                for c in ((7, 4, 3), (5, 3)):
                     try:
                         ct.ct_set_tuning(M.handle, 1, fwd_warps=w, fwd_unroll=u, op_ctas=c[0])
                     except ct.CtError:

@@ -280,9 +280,10 @@ int ct_set_wait_limit(int64_t polls, int32_t hold_first);
  *   fwd_unroll   one slice, y = A x: 8-entry chunks each lane keeps in flight,
  *                2, 4, 8 or 16
  *   op_ctas      one slice, the A^T kernel fused with the CG operator: CTAs
- *                per SM its registers are sized for, 7 or 4 (5 or 3 when the
- *                sinogram band is staged in angle chunks, above about 180 kept
- *                angles)
+ *                per SM its registers are sized for, 7, 4 or 3 (3: each lane
+ *                also copies its next two matrix chunks into shared memory
+ *                ahead of use); 5 or 3 when the sinogram band is staged in
+ *                angle chunks (above about 180 kept angles)
  *   spmm_unroll  batches of 2 or more: staged entries in flight, 4 or 8
  * By default the first solve on a handle (batch 1: ct_cg_solve,
  * ct_split_bregman, ct_chambolle_pock, and the single-slice groups of

@@ -386,9 +386,10 @@ int ct_set_tuning(ct_matrix_t A, int32_t batch, const ct_tuning* t)
         if (t->fwd_unroll != 0 && t->fwd_unroll != 2 && t->fwd_unroll != 4 && t->fwd_unroll != 8 &&
             t->fwd_unroll != 16)
             return fail(CT_ERR_ARG, "fwd_unroll must be 0, 2, 4, 8 or 16");
-        if (t->op_ctas != 0 && t->op_ctas != (chunked ? 5 : 7) && t->op_ctas != (chunked ? 3 : 4))
+        if (t->op_ctas != 0 && t->op_ctas != (chunked ? 5 : 7) && t->op_ctas != (chunked ? 3 : 4) &&
+            (chunked || t->op_ctas != 3))
             return fail(CT_ERR_ARG, chunked ? "op_ctas must be 0, 5 or 3 for this matrix (band staged in chunks)"
-                                            : "op_ctas must be 0, 7 or 4 for this matrix");
+                                            : "op_ctas must be 0, 7, 4 or 3 for this matrix");
         if (t->spmm_unroll != 0) return fail(CT_ERR_ARG, "spmm_unroll applies to batches of 2 or more");
         A->fwd_warps = t->fwd_warps;
         A->fwd_unroll = t->fwd_unroll;

@@ -362,15 +362,98 @@ __device__ __forceinline__ void row_walk_prefetch(const CT* __restrict__ col, co
     }
 }
 
-template <typename VT, typename BT, bool PREFETCH = false>
+// 16-byte asynchronous global -> shared copy through L2, and its groups.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Slots of the per-lane ring of row_walk_async and its shared-memory bytes
+// per thread (a chunk's 16-bit columns and its values, 16 bytes each piece).
+constexpr int kAsyncSlots = 3;
+constexpr int kAsyncPieces = 3;
+__host__ __device__ inline size_t async_ring_bytes(int threads) { return (size_t)threads * kAsyncSlots * kAsyncPieces * 16; }
+
+// The lane's whole row with the matrix chunks copied ahead into a ring of
+// kAsyncSlots slots in shared memory by asynchronous copies (each lane copies
+// and reads only its own slots, so no barrier is involved): two chunks are in
+// flight while one is gathered and accumulated, without holding them in
+// registers.  A slot is refilled only after the chunk it held has been
+// consumed.  The same order of accumulation as row_part (the same bits).
+// ring: this block's ring, [slot][piece][thread] of 16-byte pieces.
+template <typename VT, typename G>
+__device__ __forceinline__ void row_walk_async(const uint16_t* __restrict__ col, const VT* __restrict__ val,
+                                               int64_t base, int nch, const G& g, float& hs, float& hc, uint4* ring)
+{
+    constexpr int NV = sizeof(VT) == 4 ? 2 : 1;  // 16-byte pieces of a chunk's values
+    const int tid = threadIdx.x, nt = blockDim.x;
+    auto slot_piece = [&](int slot, int piece) { return ring + ((size_t)slot * kAsyncPieces + piece) * nt + tid; };
+    auto issue = [&](int c) {
+        const int slot = c % kAsyncSlots;
+        const int64_t p = base + (int64_t)c * kStep;
+        cp_async16(slot_piece(slot, 0), col + p);
+        cp_async16(slot_piece(slot, 1), val + p);
+        if (NV == 2) cp_async16(slot_piece(slot, 2), val + p + 4);
+    };
+    // every step commits one group (possibly empty), so "all but the newest
+    // kAsyncSlots - 1 groups complete" means chunk c has landed
+    for (int c = 0; c < kAsyncSlots - 1; ++c) {
+        if (c < nch) issue(c);
+        cp_async_commit();
+    }
+    for (int c = 0; c < nch; ++c) {
+        if (c + kAsyncSlots - 1 < nch) issue(c + kAsyncSlots - 1);
+        cp_async_commit();
+        cp_async_wait_group<kAsyncSlots - 1>();
+        const int slot = c % kAsyncSlots;
+        const uint4 cw = *slot_piece(slot, 0);
+        float v[8];
+        if (NV == 2) {
+            const float4 a = *reinterpret_cast<const float4*>(slot_piece(slot, 1));
+            const float4 b = *reinterpret_cast<const float4*>(slot_piece(slot, 2));
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+            const uint4 a = *slot_piece(slot, 1);
+            const __half2* h = reinterpret_cast<const __half2*>(&a);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const float2 f = __half22float2(h[t]);
+                v[2 * t] = f.x;
+                v[2 * t + 1] = f.y;
+            }
+        }
+        const uint32_t w[4] = {cw.x, cw.y, cw.z, cw.w};
+        float2 x[8];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            x[2 * t] = g((int)(w[t] & 0xffffu));
+            x[2 * t + 1] = g((int)(w[t] >> 16));
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc_fma(hs, hc, v[t], x[t]);
+    }
+    cp_async_wait_group<0>();
+}
+
+// PREFETCH: 0 = row_part; 1 = row_walk_prefetch; 2 = row_walk_async (ring
+// given, after the band in shared memory).
+template <typename VT, typename BT, int PREFETCH = 0>
 __device__ __forceinline__ float2 band_dot(const BandView& bv, const VT* __restrict__ val, int tile,
-                                           const BT* __restrict__ band, int64_t& t)
+                                           const BT* __restrict__ band, int64_t& t, uint4* ring = nullptr)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     t = (int64_t)tile * kTilePix + w * kSliceRows + lane;
     const int len = bv.len[t];
     float hs = 0.0f, hc = 0.0f;
-    if (PREFETCH)
+    if (PREFETCH == 2)
+        row_walk_async<VT>(bv.col16, val, bv.sp[t >> 5] + lane * kChunk, (len + kChunk - 1) / kChunk,
+                           BandGather<BT>{band}, hs, hc, ring);
+    else if (PREFETCH == 1)
         row_walk_prefetch<VT>(bv.col16, val, bv.sp[t >> 5] + lane * kChunk, (len + kChunk - 1) / kChunk,
                               BandGather<BT>{band}, hs, hc);
     else

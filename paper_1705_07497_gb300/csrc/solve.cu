@@ -584,8 +584,9 @@ int tune_single(ct_matrix* M, cudaStream_t st)
         ep.in = w.p;
         first = true;
         const bool chunked = M->h_band_chunk.size() > 2;
-        const int cands[2] = {chunked ? 5 : 7, chunked ? 3 : 4};
+        const int cands[3] = {chunked ? 5 : 7, chunked ? 3 : 4, chunked ? 0 : 3};
         for (int cv : cands) {
+            if (cv == 0) continue;
             if (rc != CT_OK) break;
             M->op_ctas = cv;
             float ms = 0.0f;

@@ -46,6 +46,10 @@ constexpr int kAdjMinBlocks = 7;                    // CTAs per SM the register 
 constexpr int kAdjMinBlocksChunked = 5;             // the same when the band is staged in angle chunks
 constexpr int kAdjFewBlocks = 4;                    // the fused kernel's alternative budgets (more registers)
 constexpr int kAdjFewBlocksChunked = 3;
+constexpr int kAdjAsyncBlocks = 3;                  // single-chunk band with the asynchronous-copy ring
+
+// Offset of the asynchronous-copy ring after a band of `slots` double-float values.
+__host__ __device__ inline size_t ring_offset(int slots) { return ((size_t)slots * sizeof(float2) + 15) & ~(size_t)15; }
 
 // y = scale * A x: one block per slice of 32 rays (see fwd_slice).
 template <typename VT, typename XT, typename YT, int U>
@@ -103,7 +107,9 @@ __global__ void __launch_bounds__(kAdjWarps * 32, MINB)
             d = band_dot_chunked<VT>(bv, val, tile, y, band, t);
         } else {
             stage_band(bv, tile, y, band);
-            d = band_dot<VT, float2, (MINB < kAdjMinBlocks)>(bv, val, tile, band, t);
+            constexpr int PF = MINB == kAdjAsyncBlocks ? 2 : (MINB < kAdjMinBlocks ? 1 : 0);
+            uint4* ring = PF == 2 ? reinterpret_cast<uint4*>(smem + ring_offset(bv.slots)) : nullptr;
+            d = band_dot<VT, float2, PF>(bv, val, tile, band, t, ring);
         }
         int i, j;
         tiled_coords(t, bv.tn, i, j);
@@ -237,16 +243,20 @@ int launch_band_adj(const ct_matrix* M, const VT* val, const YT* y, OT* out, flo
 template <typename VT, int MODE, bool CHUNKED, int MINB>
 int launch_band_op_t(const ct_matrix* M, const VT* val, const float2* y, const OpEpilogue& ep, cudaStream_t st)
 {
-    const size_t smem = band_smem(M, sizeof(float2));
+    size_t smem = band_smem(M, sizeof(float2));
+    if (!CHUNKED && MINB == kAdjAsyncBlocks) smem = ring_offset(M->band_chunk_slots) + async_ring_bytes(kAdjWarps * 32);
     CT_CHECK(allow_smem(band_op_kernel<VT, MODE, CHUNKED, MINB>, smem));
     band_op_kernel<VT, MODE, CHUNKED, MINB><<<band_grid(M), kAdjWarps * 32, smem, st>>>(band_view(M), val, y, ep);
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
 
-// The fused kernel comes in two register budgets per band form: sized for
-// kAdjMinBlocks (kAdjMinBlocksChunked) CTAs per SM, or for fewer CTAs with
-// more registers per thread; the code, and so every result bit, is the same.
+// The fused kernel comes in several budgets per band form: sized for
+// kAdjMinBlocks (kAdjMinBlocksChunked) CTAs per SM; for fewer CTAs with more
+// registers per thread (the next chunk's loads issued before this chunk's
+// gathers); and, for a single-chunk band, kAdjAsyncBlocks CTAs whose lanes
+// copy two chunks ahead into shared memory.  Every form accumulates each row
+// in the same order, so every result bit is the same.
 template <typename VT, int MODE>
 int launch_band_op(const ct_matrix* M, const VT* val, const float2* y, const OpEpilogue& ep, cudaStream_t st)
 {
@@ -256,6 +266,7 @@ int launch_band_op(const ct_matrix* M, const VT* val, const float2* y, const OpE
         return launch_band_op_t<VT, MODE, true, kAdjMinBlocksChunked>(M, val, y, ep, st);
     }
     if (ctas == kAdjFewBlocks) return launch_band_op_t<VT, MODE, false, kAdjFewBlocks>(M, val, y, ep, st);
+    if (ctas == kAdjAsyncBlocks) return launch_band_op_t<VT, MODE, false, kAdjAsyncBlocks>(M, val, y, ep, st);
     return launch_band_op_t<VT, MODE, false, kAdjMinBlocks>(M, val, y, ep, st);
 }
 

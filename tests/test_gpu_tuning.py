@@ -29,9 +29,9 @@ def _bits(t):
     return t.cpu().numpy().view(np.uint32).copy()
 
 
-@pytest.mark.parametrize("geom,flags,ctas", [((64, 90, 3, 91), ct.CT_VAL_FP32, (7, 4)),
+@pytest.mark.parametrize("geom,flags,ctas", [((64, 90, 3, 91), ct.CT_VAL_FP32, (7, 4, 3)),
                                              ((64, 360, 1, 91), ct.CT_VAL_FP32, (5, 3)),
-                                             ((96, 120, 1, 137), ct.CT_VAL_FP16_ROWSCALE, (7, 4))])
+                                             ((96, 120, 1, 137), ct.CT_VAL_FP16_ROWSCALE, (7, 4, 3))])
 def test_every_single_slice_launch_shape_gives_the_same_bits(dev, geom, flags, ctas):
     M = ct.Matrix(*geom, flags=flags)
     x = torch.tensor(inputs.random_vector(M.cols, 31), dtype=torch.float32, device=dev)
@@ -59,7 +59,7 @@ def test_tuner_picks_listed_shapes_and_caches_them_by_geometry(dev):
     assert ct.ct_get_tuning(M.handle, 1)["fwd_warps"] == 0
     ct.ct_tune(M.handle, 1)
     t = ct.ct_get_tuning(M.handle, 1)
-    assert t["fwd_warps"] in (4, 8) and t["fwd_unroll"] in (2, 4, 8, 16) and t["op_ctas"] in (7, 4)
+    assert t["fwd_warps"] in (4, 8) and t["fwd_unroll"] in (2, 4, 8, 16) and t["op_ctas"] in (7, 4, 3)
     # a second handle of the same geometry takes the cached choice; the
     # first solve fills it in
     M2 = ct.Matrix(*geom)
@@ -91,4 +91,6 @@ def test_batched_tuning_gives_the_same_bits_and_rejects_single_fields(dev):
         ct.ct_set_tuning(M.handle, 1, fwd_warps=6)
     with pytest.raises(ct.CtError):
         ct.ct_set_tuning(M.handle, 1, op_ctas=5)  # this matrix stages its band in one chunk
+    with pytest.raises(ct.CtError):
+        ct.ct_set_tuning(M.handle, 1, op_ctas=6)
     M.close()
