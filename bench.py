@@ -1465,16 +1465,14 @@ def bench_shapes(args, dev):
         rows = []
         for w in (8, 4):
             for u in (8, 4, 2, 16):
-                for c in ((7, 4, 3), (5, 3)):
+                for cc, px in ((7, 1), (4, 1), (3, 1), (7, 2), (5, 1)):
                     try:
-                        ct.ct_set_tuning(M.handle, 1, fwd_warps=w, fwd_unroll=u, op_ctas=c[0])
+                        ct.ct_set_tuning(M.handle, 1, fwd_warps=w, fwd_unroll=u, op_ctas=cc, op_pixels=px)
                     except ct.CtError:
                         continue
-                    for cc in c:
-                        ct.ct_set_tuning(M.handle, 1, fwd_warps=w, fwd_unroll=u, op_ctas=cc)
-                        ms = ct.ct_time_cg_kernels(M.handle, 1.0, 1.0, args.steps, torch.cuda.current_stream().cuda_stream)
-                        rows.append({"fwd_warps": w, "fwd_unroll": u, "op_ctas": cc, "fwd_ms": round(ms[0], 5),
-                                     "op_ms": round(ms[1], 5)})
+                    ms = ct.ct_time_cg_kernels(M.handle, 1.0, 1.0, args.steps, torch.cuda.current_stream().cuda_stream)
+                    rows.append({"fwd_warps": w, "fwd_unroll": u, "op_ctas": cc, "op_pixels": px,
+                                 "fwd_ms": round(ms[0], 5), "op_ms": round(ms[1], 5)})
         ct.ct_set_tuning(M.handle, 1)
         ct.ct_tune(M.handle, 1)
         chosen = ct.ct_get_tuning(M.handle, 1)

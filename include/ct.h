@@ -284,6 +284,9 @@ int ct_set_wait_limit(int64_t polls, int32_t hold_first);
  *                also copies its next two matrix chunks into shared memory
  *                ahead of use); 5 or 3 when the sinogram band is staged in
  *                angle chunks (above about 180 kept angles)
+ *   op_pixels    one slice, the same kernel: pixel rows per lane, 1, or 2
+ *                (four warps per image tile, seven CTAs per SM; single-chunk
+ *                bands only, with op_ctas 0 or 7)
  *   spmm_unroll  batches of 2 or more: staged entries in flight, 4 or 8
  * By default the first solve on a handle (batch 1: ct_cg_solve,
  * ct_split_bregman, ct_chambolle_pock, and the single-slice groups of
@@ -300,6 +303,7 @@ typedef struct {
     int32_t fwd_warps;
     int32_t fwd_unroll;
     int32_t op_ctas;
+    int32_t op_pixels;
     int32_t spmm_unroll;
 } ct_tuning;
 

@@ -366,6 +366,7 @@ int ct_get_tuning(ct_matrix_t A, int32_t batch, ct_tuning* t)
         t->fwd_warps = A->fwd_warps;
         t->fwd_unroll = A->fwd_unroll;
         t->op_ctas = A->op_ctas;
+        t->op_pixels = A->op_pixels;
     } else {
         auto it = A->spmm_unroll.find(batch);
         t->spmm_unroll = it == A->spmm_unroll.end() ? 0 : it->second;
@@ -390,14 +391,19 @@ int ct_set_tuning(ct_matrix_t A, int32_t batch, const ct_tuning* t)
             (chunked || t->op_ctas != 3))
             return fail(CT_ERR_ARG, chunked ? "op_ctas must be 0, 5 or 3 for this matrix (band staged in chunks)"
                                             : "op_ctas must be 0, 7, 4 or 3 for this matrix");
+        if (t->op_pixels != 0 && t->op_pixels != 1 && t->op_pixels != 2)
+            return fail(CT_ERR_ARG, "op_pixels must be 0, 1 or 2");
+        if (t->op_pixels == 2 && (chunked || (t->op_ctas != 0 && t->op_ctas != 7)))
+            return fail(CT_ERR_ARG, "op_pixels = 2 needs a single-chunk band and op_ctas 0 or 7");
         if (t->spmm_unroll != 0) return fail(CT_ERR_ARG, "spmm_unroll applies to batches of 2 or more");
         A->fwd_warps = t->fwd_warps;
         A->fwd_unroll = t->fwd_unroll;
         A->op_ctas = t->op_ctas;
+        A->op_pixels = t->op_pixels;
         return CT_OK;
     }
-    if (t->fwd_warps || t->fwd_unroll || t->op_ctas)
-        return fail(CT_ERR_ARG, "fwd_warps, fwd_unroll and op_ctas apply to batch 1");
+    if (t->fwd_warps || t->fwd_unroll || t->op_ctas || t->op_pixels)
+        return fail(CT_ERR_ARG, "fwd_warps, fwd_unroll, op_ctas and op_pixels apply to batch 1");
     return ct_set_spmm_unroll(A, batch, t->spmm_unroll);
 }
 

@@ -162,6 +162,7 @@ struct ct_matrix {
     int fwd_warps = 0;       // y = A x: warps per block (4 or 8)
     int fwd_unroll = 0;      // y = A x: chunks in flight per lane (2, 4 or 8)
     int op_ctas = 0;         // A^T kernels: CTAs per SM the registers are sized for
+    int op_pixels = 0;       // A^T kernels: pixel rows per lane (1, or 2 with four warps per tile)
     ct::Workspace ws;
     // extra single-slice workspaces: ct_split_bregman_ragged runs the
     // problems of a small group on one handle side by side

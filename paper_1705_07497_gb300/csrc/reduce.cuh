@@ -62,6 +62,70 @@ __device__ bool grid_reduce_last(const float2 (&v)[NQ], float2* partials, unsign
     return threadIdx.x == 0;
 }
 
+// grid_reduce_last for a block of 128 threads in which every thread carries
+// the values of two pixels of a 256-pixel tile: va of pixel slice 2w and vb of
+// slice 2w + 1 (w its warp).  Every sum is grouped exactly as grid_reduce_last
+// groups it in a block of 256 threads with one pixel per thread (warp sums
+// per slice, slices in order, and the last block's partials summed by 256
+// virtual threads t and t + 128), so both give the same bits.
+template <int NQ>
+__device__ bool grid_reduce_last_pair(const float2 (&va)[NQ], const float2 (&vb)[NQ], float2* partials,
+                                      unsigned* counter, double (&tot)[NQ])
+{
+    __shared__ float2 sh[NQ][8];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const float2 sa = warp_sum_df(va[q]);
+        const float2 sb = warp_sum_df(vb[q]);
+        if (lane == 0) {
+            sh[q][2 * warp] = sa;
+            sh[q][2 * warp + 1] = sb;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            float2 s = sh[q][0];
+            for (int w = 1; w < 8; ++w) s = df_add(s, sh[q][w]);
+            partials[(size_t)q * gridDim.x + blockIdx.x] = s;
+        }
+        __threadfence();
+        const unsigned prev = atomicAdd(counter, 1u);
+        last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        float2 s1 = df_zero(), s2 = df_zero();
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += 256)
+            s1 = df_add(s1, __ldcg(partials + (size_t)q * gridDim.x + b));
+        for (unsigned b = threadIdx.x + 128; b < gridDim.x; b += 256)
+            s2 = df_add(s2, __ldcg(partials + (size_t)q * gridDim.x + b));
+        s1 = warp_sum_df(s1);
+        s2 = warp_sum_df(s2);
+        if (lane == 0) {
+            sh[q][warp] = s1;
+            sh[q][warp + 4] = s2;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            float2 s = sh[q][0];
+            for (int w = 1; w < 8; ++w) s = df_add(s, sh[q][w]);
+            tot[q] = df_to_double(s);
+        }
+        *counter = 0u;
+    }
+    return threadIdx.x == 0;
+}
+
 __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
 
 // r0 = rhs - Op(u0) has been formed: start the iteration.

@@ -440,6 +440,66 @@ __device__ __forceinline__ void row_walk_async(const uint16_t* __restrict__ col,
     cp_async_wait_group<0>();
 }
 
+// Two rows per lane (rows a and b of A^T, both against the staged band):
+// their chunks are walked as one stream a0, b0, a1, b1, ... (a row that has
+// run out drops out of it), with the next chunk's loads issued before the
+// current chunk's gathers, so a lane keeps one chunk in flight while it works
+// on the other row.  Each row is summed in its own order, as row_part sums
+// it (the same bits).
+template <typename VT, typename G>
+__device__ __forceinline__ void row_pair_walk(const uint16_t* __restrict__ col, const VT* __restrict__ val,
+                                              int64_t base_a, int nch_a, int64_t base_b, int nch_b, const G& g,
+                                              float2& da, float2& db)
+{
+    float hs[2] = {0.0f, 0.0f}, hc[2] = {0.0f, 0.0f};
+    const int K = 2 * max(nch_a, nch_b);
+    auto valid = [&](int k) { return (k & 1) ? (k >> 1) < nch_b : (k >> 1) < nch_a; };
+    auto addr = [&](int k) { return ((k & 1) ? base_b : base_a) + (int64_t)(k >> 1) * kStep; };
+    int k = 0;
+    while (k < K && !valid(k)) ++k;
+    int cc[8];
+    float vv[8];
+    if (k < K) {
+        load8_col(col, addr(k), cc);
+        Vals<VT>::load8(val, addr(k), vv);
+    }
+    while (k < K) {
+        int kn = k + 1;
+        while (kn < K && !valid(kn)) ++kn;
+        int cn[8];
+        float vn[8];
+        if (kn < K) {
+            load8_col(col, addr(kn), cn);
+            Vals<VT>::load8(val, addr(kn), vn);
+        }
+        float2 x[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) x[t] = g(cc[t]);
+        // accumulate into the row's pair: swap the pairs so that slot 0 holds it
+        const bool rb = k & 1;
+        float s0 = rb ? hs[1] : hs[0], c0 = rb ? hc[1] : hc[0];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc_fma(s0, c0, vv[t], x[t]);
+        if (rb) {
+            hs[1] = s0;
+            hc[1] = c0;
+        } else {
+            hs[0] = s0;
+            hc[0] = c0;
+        }
+        if (kn < K) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                cc[t] = cn[t];
+                vv[t] = vn[t];
+            }
+        }
+        k = kn;
+    }
+    da = acc_value(hs[0], hc[0]);
+    db = acc_value(hs[1], hc[1]);
+}
+
 // PREFETCH: 0 = row_part; 1 = row_walk_prefetch; 2 = row_walk_async (ring
 // given, after the band in shared memory).
 template <typename VT, typename BT, int PREFETCH = 0>

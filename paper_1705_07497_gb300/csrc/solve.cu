@@ -506,7 +506,7 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int fwd_warps, fwd_unroll, op_ctas;
+    int fwd_warps, fwd_unroll, op_ctas, op_pixels;
 };
 std::mutex g_tune_mutex;
 std::map<TuneKey, TuneVal> g_tune_cache;  // choices already measured in this process, by geometry
@@ -524,7 +524,7 @@ std::map<TuneKey, TuneVal> g_tune_cache;  // choices already measured in this pr
 // is being captured; a choice pinned with ct_set_tuning stays.
 int tune_single(ct_matrix* M, cudaStream_t st)
 {
-    if (M->fourier || (M->fwd_warps > 0 && M->fwd_unroll > 0 && M->op_ctas > 0)) return CT_OK;
+    if (M->fourier || (M->fwd_warps > 0 && M->fwd_unroll > 0 && M->op_ctas > 0 && M->op_pixels > 0)) return CT_OK;
     const TuneKey key{M->g.n, M->g.n_angles_total, M->g.keep_every, M->g.n_bins, M->flags};
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -533,6 +533,7 @@ int tune_single(ct_matrix* M, cudaStream_t st)
             if (M->fwd_warps <= 0) M->fwd_warps = it->second.fwd_warps;
             if (M->fwd_unroll <= 0) M->fwd_unroll = it->second.fwd_unroll;
             if (M->op_ctas <= 0) M->op_ctas = it->second.op_ctas;
+            if (M->op_pixels <= 0) M->op_pixels = it->second.op_pixels;
             return CT_OK;
         }
     }
@@ -551,7 +552,7 @@ int tune_single(ct_matrix* M, cudaStream_t st)
         cudaEventDestroy(e0);
         return cuda_fail(ce, "cudaEventCreate", __FILE__, __LINE__);
     }
-    const int pin_w = M->fwd_warps, pin_u = M->fwd_unroll, pin_c = M->op_ctas;
+    const int pin_w = M->fwd_warps, pin_u = M->fwd_unroll, pin_c = M->op_ctas, pin_p = M->op_pixels;
     const int rpow = P.vk == ValKind::F16 ? 2 : 0;
     const int reps = 3;
     int rc = CT_OK;
@@ -576,34 +577,40 @@ int tune_single(ct_matrix* M, cudaStream_t st)
     }
     M->fwd_warps = bw;
     M->fwd_unroll = bu;
-    int bc = pin_c;
-    if (bc <= 0 && rc == CT_OK) {
+    // the fused A^T kernel: (CTAs per SM, pixel rows per lane)
+    const bool chunked = M->h_band_chunk.size() > 2;
+    int bc = pin_c > 0 ? pin_c : (chunked ? 5 : 7), bp = pin_p > 0 ? pin_p : 1;
+    if ((pin_c <= 0 || pin_p <= 0) && rc == CT_OK) {
         OpEpilogue ep = P.base;
         ep.mode = 1;
         ep.out = w.q;
         ep.in = w.p;
         first = true;
-        const bool chunked = M->h_band_chunk.size() > 2;
-        const int cands[3] = {chunked ? 5 : 7, chunked ? 3 : 4, chunked ? 0 : 3};
-        for (int cv : cands) {
-            if (cv == 0) continue;
-            if (rc != CT_OK) break;
+        const int cands[4][2] = {{chunked ? 5 : 7, 1}, {chunked ? 3 : 4, 1}, {chunked ? 0 : 3, 1}, {chunked ? 0 : 7, 2}};
+        for (const auto& cand : cands) {
+            const int cv = cand[0], pv = cand[1];
+            if (cv == 0 || rc != CT_OK) continue;
+            if ((pin_c > 0 && cv != pin_c) || (pin_p > 0 && pv != pin_p)) continue;
             M->op_ctas = cv;
+            M->op_pixels = pv;
             float ms = 0.0f;
             rc = time_launches([&]() { return launch_adjoint_op_df(M, P.vk, w.y, ep, st); }, reps, e0, e1, st, &ms);
             if (rc == CT_OK && (first || ms < best)) {
                 best = ms;
                 bc = cv;
+                bp = pv;
                 first = false;
             }
         }
     }
-    M->op_ctas = bc > 0 ? bc : (M->h_band_chunk.size() > 2 ? 5 : 7);
+    M->op_ctas = bc;
+    M->op_pixels = bp;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != CT_OK) return rc;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    if (pin_w <= 0 && pin_u <= 0 && pin_c <= 0) g_tune_cache[key] = TuneVal{M->fwd_warps, M->fwd_unroll, M->op_ctas};
+    if (pin_w <= 0 && pin_u <= 0 && pin_c <= 0 && pin_p <= 0)
+        g_tune_cache[key] = TuneVal{M->fwd_warps, M->fwd_unroll, M->op_ctas, M->op_pixels};
     return CT_OK;
 }
 

@@ -47,6 +47,8 @@ constexpr int kAdjMinBlocksChunked = 5;             // the same when the band is
 constexpr int kAdjFewBlocks = 4;                    // the fused kernel's alternative budgets (more registers)
 constexpr int kAdjFewBlocksChunked = 3;
 constexpr int kAdjAsyncBlocks = 3;                  // single-chunk band with the asynchronous-copy ring
+constexpr int kOp2Threads = 128;                    // two pixel rows per lane: four warps per tile
+constexpr int kOp2Blocks = 7;
 
 // Offset of the asynchronous-copy ring after a band of `slots` double-float values.
 __host__ __device__ inline size_t ring_offset(int slots) { return ((size_t)slots * sizeof(float2) + 15) & ~(size_t)15; }
@@ -122,6 +124,57 @@ __global__ void __launch_bounds__(kAdjWarps * 32, MINB)
         __syncthreads();
     }
     op_finish<MODE>(a, s0, c0, s1, c1);
+}
+
+// The same product and epilogue with two pixel rows per lane: a CTA of four
+// warps per tile, warp w taking pixel slices 2w and 2w + 1, so that at seven
+// CTAs per SM (72 registers per thread) a 512 x 512 image's 1024 tiles run in
+// one wave with two rows in flight per lane.  Every row sum, epilogue and
+// reduction is grouped as in band_op_kernel (grid_reduce_last_pair), so both
+// give the same bits.  Single-chunk bands only.
+template <typename VT, int MODE>
+__global__ void __launch_bounds__(kOp2Threads, kOp2Blocks)
+    band_op2_kernel(BandView bv, const VT* __restrict__ val, const float2* __restrict__ y, OpEpilogue a)
+{
+    if (a.gate && *a.gate) return;
+    if (MODE != 2 && !a.cg->active) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* band = reinterpret_cast<float2*>(smem);
+    const int ntiles = bv.tn * bv.tn;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float s0a = 0.0f, c0a = 0.0f, s1a = 0.0f, c1a = 0.0f, s0b = 0.0f, c0b = 0.0f, s1b = 0.0f, c1b = 0.0f;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        stage_band(bv, tile, y, band);
+        const int64_t ta = (int64_t)tile * kTilePix + (2 * w) * kSliceRows + lane, tb = ta + kSliceRows;
+        float2 da, db;
+        row_pair_walk<VT>(bv.col16, val, bv.sp[ta >> 5] + lane * kChunk, (bv.len[ta] + kChunk - 1) / kChunk,
+                          bv.sp[tb >> 5] + lane * kChunk, (bv.len[tb] + kChunk - 1) / kChunk,
+                          BandGather<float2>{band}, da, db);
+        int i, j;
+        tiled_coords(ta, bv.tn, i, j);
+        if (i < bv.n && j < bv.n) {
+            op_epilogue<MODE>(a, bv.n, bv.tn, ta, i, j, da, s0a, c0a, s1a, c1a);
+        } else {
+            a.out[ta] = df_zero();
+            if (MODE == 2) a.p_out[ta] = df_zero();
+        }
+        tiled_coords(tb, bv.tn, i, j);
+        if (i < bv.n && j < bv.n) {
+            op_epilogue<MODE>(a, bv.n, bv.tn, tb, i, j, db, s0b, c0b, s1b, c1b);
+        } else {
+            a.out[tb] = df_zero();
+            if (MODE == 2) a.p_out[tb] = df_zero();
+        }
+        __syncthreads();
+    }
+    float2 va[2] = {acc_value(s0a, c0a), acc_value(s1a, c1a)};
+    float2 vb[2] = {acc_value(s0b, c0b), acc_value(s1b, c1b)};
+    double tot[2];
+    if (grid_reduce_last_pair<2>(va, vb, a.partials, a.counter, tot)) {
+        if (MODE == 1) cg_after_pq(*a.cg, tot[0]);
+        if (MODE == 2) cg_after_residual(*a.cg, tot[0], tot[1], a.tol);
+        if (MODE == 3) a.cg->rr = tot[0];
+    }
 }
 
 // Surrogate operator (Sec. 3.2, Eq. def_sparse_surr): (T p)_x = sum_d s(d)
@@ -258,9 +311,20 @@ int launch_band_op_t(const ct_matrix* M, const VT* val, const float2* y, const O
 // copy two chunks ahead into shared memory.  Every form accumulates each row
 // in the same order, so every result bit is the same.
 template <typename VT, int MODE>
+int launch_band_op2(const ct_matrix* M, const VT* val, const float2* y, const OpEpilogue& ep, cudaStream_t st)
+{
+    const size_t smem = band_smem(M, sizeof(float2));
+    CT_CHECK(allow_smem(band_op2_kernel<VT, MODE>, smem));
+    band_op2_kernel<VT, MODE><<<band_grid(M), kOp2Threads, smem, st>>>(band_view(M), val, y, ep);
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+template <typename VT, int MODE>
 int launch_band_op(const ct_matrix* M, const VT* val, const float2* y, const OpEpilogue& ep, cudaStream_t st)
 {
     const int ctas = M->op_ctas;
+    if (M->op_pixels == 2 && !band_chunked(M)) return launch_band_op2<VT, MODE>(M, val, y, ep, st);
     if (band_chunked(M)) {
         if (ctas == kAdjFewBlocksChunked) return launch_band_op_t<VT, MODE, true, kAdjFewBlocksChunked>(M, val, y, ep, st);
         return launch_band_op_t<VT, MODE, true, kAdjMinBlocksChunked>(M, val, y, ep, st);

@@ -146,6 +146,7 @@ class Tuning(ctypes.Structure):
         ("fwd_warps", ctypes.c_int32),
         ("fwd_unroll", ctypes.c_int32),
         ("op_ctas", ctypes.c_int32),
+        ("op_pixels", ctypes.c_int32),
         ("spmm_unroll", ctypes.c_int32),
     ]
 

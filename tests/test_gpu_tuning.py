@@ -37,10 +37,11 @@ def test_every_single_slice_launch_shape_gives_the_same_bits(dev, geom, flags, c
     x = torch.tensor(inputs.random_vector(M.cols, 31), dtype=torch.float32, device=dev)
     rhs = torch.tensor(inputs.random_vector(M.cols, 32), dtype=torch.float32, device=dev)
     ref_y = ref_u = None
+    ops = [(c, 1) for c in ctas] + ([(7, 2)] if 7 in ctas else [])
     for shape in SINGLE:
-        for c in ctas:
-            ct.ct_set_tuning(M.handle, 1, op_ctas=c, **shape)
-            assert ct.ct_get_tuning(M.handle, 1) == dict(shape, op_ctas=c, spmm_unroll=0)
+        for c, px in ops:
+            ct.ct_set_tuning(M.handle, 1, op_ctas=c, op_pixels=px, **shape)
+            assert ct.ct_get_tuning(M.handle, 1) == dict(shape, op_ctas=c, op_pixels=px, spmm_unroll=0)
             y = torch.empty(M.rows, device=dev)
             M.forward(x, y)
             u = torch.zeros(M.cols, device=dev)
@@ -60,6 +61,7 @@ def test_tuner_picks_listed_shapes_and_caches_them_by_geometry(dev):
     ct.ct_tune(M.handle, 1)
     t = ct.ct_get_tuning(M.handle, 1)
     assert t["fwd_warps"] in (4, 8) and t["fwd_unroll"] in (2, 4, 8, 16) and t["op_ctas"] in (7, 4, 3)
+    assert t["op_pixels"] in (1, 2)
     # a second handle of the same geometry takes the cached choice; the
     # first solve fills it in
     M2 = ct.Matrix(*geom)
@@ -93,4 +95,6 @@ def test_batched_tuning_gives_the_same_bits_and_rejects_single_fields(dev):
         ct.ct_set_tuning(M.handle, 1, op_ctas=5)  # this matrix stages its band in one chunk
     with pytest.raises(ct.CtError):
         ct.ct_set_tuning(M.handle, 1, op_ctas=6)
+    with pytest.raises(ct.CtError):
+        ct.ct_set_tuning(M.handle, 1, op_ctas=4, op_pixels=2)
     M.close()
