@@ -69,8 +69,13 @@ enum {
     CT_VAL_FP16_ROWSCALE = 1, /* A = diag(s) Q: Q in FP16 (|Q| <= 1), s FP32 per
                                  row; A^T is applied as Q^T (s .* y), so the
                                  quantised normal operator stays symmetric     */
-    CT_KEEP_FP32_COPY = 4     /* with FP16 storage, also keep FP32 values for
+    CT_KEEP_FP32_COPY = 4,    /* with FP16 storage, also keep FP32 values for
                                  residual refreshes (ct_cg_params.refresh_every) */
+    CT_F64_FP64_PIPE = 8      /* ct_forward_f64, ct_adjoint_f64 and ct_normal_f64
+                                 gather and accumulate in FP64 (one FP64 FMA per
+                                 entry) instead of the default double-float
+                                 kernels on the FP32 pipes; several times slower
+                                 on this part, whose FP64 pipe is narrow        */
 };
 
 typedef struct {
@@ -113,9 +118,14 @@ int ct_adjoint(ct_matrix_t A, const float *y, float *x, int32_t batch, void *cud
 /* FP64-vector forms of ct_forward / ct_adjoint for callers that keep their
  * vectors in FP64 (the differentiable reconstruction of the Python layer).
  * Same layout and batching; device pointers only (CT_ERR_ARG otherwise).  The
- * matrix values are those of the storage form; products gather and
- * accumulate in FP64 (one FP64 FMA per entry: slower than ct_forward, but
- * derivatives of the unrolled reconstruction need the accuracy). */
+ * matrix values are those of the storage form.  Each FP64 input value is
+ * split into a double-float pair (hi, lo) = (fl32(v), fl32(v - hi)), which
+ * holds it to 2^-48 relative; the product runs in the solvers' double-float
+ * kernels (error-free products, compensated sums) and each output pair is
+ * summed back to FP64: about 1e-14 relative error per output, which is what
+ * the derivatives of the unrolled reconstruction need.  A handle built with
+ * CT_F64_FP64_PIPE gathers and accumulates in FP64 instead (one FP64 FMA per
+ * entry).  Uses workspace buffers of the handle, allocated on first use. */
 int ct_forward_f64(ct_matrix_t A, const double *x, double *y, int32_t batch, void *cuda_stream);
 int ct_adjoint_f64(ct_matrix_t A, const double *y, double *x, int32_t batch, void *cuda_stream);
 

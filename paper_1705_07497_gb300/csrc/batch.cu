@@ -986,6 +986,15 @@ int grid_blocks(const ct_matrix* M, int64_t len)
 
 }  // namespace
 
+int batched_product_df(const ct_matrix* M, int which, const float2* in, float2* out, int32_t B, int rpow,
+                       cudaStream_t st)
+{
+    const ValKind vk = (M->flags & CT_VAL_FP16_ROWSCALE) ? ValKind::F16 : ValKind::F32;
+    BProd a{(vk == ValKind::F16 && which == 0 && rpow > 0) ? M->row_scale : nullptr, rpow, make_float2(1.0f, 0.0f),
+            nullptr, nullptr};
+    return launch_spmm(M, which, vk, in, out, B, a, st);
+}
+
 int batched_forward_adjoint(const ct_matrix* M, int which, const float* in, float* out, int32_t B,
                             cudaStream_t st)
 {

@@ -107,7 +107,7 @@ int ct_build_matrix(const ct_geometry* g, uint32_t flags, ct_matrix_t* out)
     const int64_t n_kept = (g->n_angles_total + g->keep_every - 1) / g->keep_every;
     if (n_kept * g->n_bins >= ((int64_t)1 << 31))
         return fail(CT_ERR_ARG, "kept angles * bins must be below 2^31");
-    const uint32_t known = CT_VAL_FP16_ROWSCALE | CT_KEEP_FP32_COPY;
+    const uint32_t known = CT_VAL_FP16_ROWSCALE | CT_KEEP_FP32_COPY | CT_F64_FP64_PIPE;
     if (flags & ~known) return fail(CT_ERR_ARG, "unknown flag bits");
     if ((flags & CT_KEEP_FP32_COPY) && !(flags & CT_VAL_FP16_ROWSCALE))
         return fail(CT_ERR_ARG, "CT_KEEP_FP32_COPY needs CT_VAL_FP16_ROWSCALE");

@@ -113,6 +113,10 @@ struct Workspace {
     float2* y = nullptr;                   // sinogram temp [rows][batch]
     double* f64_y = nullptr;               // ct_normal_f64: the sinogram temp [rows][batch]
     int64_t f64_y_len = 0;
+    // FP64-vector products in double-float (the default): the split input,
+    // the product, and (ct_normal_f64) the second product, [len][batch]
+    float2 *f64_a = nullptr, *f64_b = nullptr, *f64_c = nullptr;
+    int64_t f64_a_len = 0, f64_b_len = 0, f64_c_len = 0;
     float2* pub_y2 = nullptr;              // ct_adjoint with FP16 storage: s .* y
     int64_t pub_y2_len = 0;
     float* pub_x = nullptr;                // ct_forward: the caller's image in tile order
@@ -256,6 +260,12 @@ int grid_for(const ct_matrix* M, int64_t work_items, int items_per_block, int ma
 // which = 0: y = A x; which = 1: x = A^T y (FP32 vectors, double-float accumulation).
 int batched_forward_adjoint(const ct_matrix* M, int which, const float* in, float* out, int32_t B,
                             cudaStream_t st);
+// Batched double-float products in the internal layouts ([npad][B] tiled
+// images, [rows][B] sinograms): which = 0: out = s^rpow .* (A in) (rpow 0
+// without FP16 storage); which = 1: out = A^T in (with FP16 storage Q^T in:
+// the caller scales the sinogram).
+int batched_product_df(const ct_matrix* M, int which, const float2* in, float2* out, int32_t B, int rpow,
+                       cudaStream_t st);
 int cg_solve_batched(ct_matrix* M, const ct_cg_params* P, const float* rhs, float* u, int32_t B,
                      ct_cg_stats* stats, cudaStream_t st);
 // Bregman updates of one or more runs, outer_iters times: one captured graph

@@ -349,6 +349,9 @@ void free_workspace(Workspace& w)
     cudaFree(w.stage_b);
     cudaFree(w.pub_x);
     cudaFree(w.f64_y);
+    cudaFree(w.f64_a);
+    cudaFree(w.f64_b);
+    cudaFree(w.f64_c);
     cudaFree(w.partials);
     cudaFree(w.counter);
     cudaFree(w.cg);

@@ -5,6 +5,8 @@
 // kernels the solvers use (solver_ops.cu for one slice, batch.cu for a
 // batch); the caller's row-major image is moved to and from the internal tile
 // order on the way.
+#include <algorithm>
+
 #include "ct_internal.cuh"
 #include "dfloat.cuh"
 #include "layout.cuh"
@@ -24,11 +26,11 @@ __global__ void to_tiles_kernel(const float* __restrict__ in, float* __restrict_
     }
 }
 
-// FP64-vector products for the differentiable path: FP64 gathers and FP64
-// accumulation (one FMA per entry on the FP64 pipe).  The derivative of the
-// unrolled reconstruction amplifies rounding far more than the reconstruction
-// itself, so this path trades speed for FP64 accuracy; the solvers use the
-// double-float kernels.
+// FP64-vector products on the FP64 pipe (handles built with
+// CT_F64_FP64_PIPE): FP64 gathers and FP64 accumulation, one FMA per entry.
+// The default path (below) splits the FP64 vectors into double-float pairs
+// and runs the solvers' kernels on the FP32 pipes, with the same accuracy in
+// the derivatives of the unrolled reconstruction and several times the speed.
 template <typename VT>
 __device__ __forceinline__ double val64(const VT* v, int64_t k);
 template <>
@@ -187,11 +189,149 @@ __global__ void normal_epilogue_f64_kernel(const double* __restrict__ x, double*
     }
 }
 
+// ---- FP64 vectors through the double-float kernels (the default) ----
+//
+// An FP64 value v becomes the pair (hi, lo) = (fl32(v), fl32(v - hi)), which
+// holds v to 2^-48 relative; the products then run on the FP32 pipes exactly
+// as the solvers' (error-free products of the FP32 matrix values with both
+// parts, compensated sums), and an output pair goes back as hi + lo in FP64.
+__device__ __forceinline__ float2 split_f64(double v)
+{
+    const float hi = __double2float_rn(v);
+    return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+__device__ __forceinline__ double join_f64(float2 p) { return (double)p.x + (double)p.y; }
+
+// Caller's row-major FP64 image [n*n][B] -> double-float pairs in tile order [npad][B].
+__global__ void f64_image_to_df_kernel(const double* __restrict__ in, float2* __restrict__ out, int n, int tn, int B)
+{
+    const int64_t len = padded_pixels(n) * B;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = e / B;
+        const int b = (int)(e - t * B);
+        int i, j;
+        tiled_coords(t, tn, i, j);
+        out[e] = (i < n && j < n) ? split_f64(in[((int64_t)i * n + j) * B + b]) : make_float2(0.0f, 0.0f);
+    }
+}
+
+// FP64 sinogram [rows][B] -> double-float pairs, times the row scale s when
+// given (FP16 storage: A^T y = Q^T (s .* y); the product s y is formed in FP64).
+__global__ void f64_rows_to_df_kernel(const double* __restrict__ in, const float* __restrict__ scale,
+                                      float2* __restrict__ out, int64_t rows, int B)
+{
+    const int64_t len = rows * B;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+        const double v = in[e];
+        out[e] = split_f64(scale ? v * (double)scale[e / B] : v);
+    }
+}
+
+__global__ void df_rows_to_f64_kernel(const float2* __restrict__ in, double* __restrict__ out, int64_t len)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = join_f64(in[e]);
+}
+
+// Double-float image in tile order [npad][B] -> FP64 row-major [n*n][B];
+// with x given, out = alpha * in + lambda * grad^T grad x instead (the
+// operator epilogue of ct_normal_f64, on the caller's FP64 x).
+__global__ void df_image_to_f64_kernel(const float2* __restrict__ in, double* __restrict__ out, int n, int tn, int B,
+                                       const double* __restrict__ x, double alpha, double lam)
+{
+    const int64_t total = (int64_t)n * n * B;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = k / B;
+        const int b = (int)(k - p * B);
+        const int i = (int)(p / n), j = (int)(p - (int64_t)i * n);
+        const double v = join_f64(in[tiled_index(i, j, tn) * B + b]);
+        if (!x) {
+            out[k] = v;
+            continue;
+        }
+        const double c = x[k];
+        double lap = 0.0;
+        if (j > 0) lap += c - x[k - B];
+        if (j < n - 1) lap += c - x[k + B];
+        if (i > 0) lap += c - x[k - (int64_t)n * B];
+        if (i < n - 1) lap += c - x[k + (int64_t)n * B];
+        out[k] = alpha * v + lam * lap;
+    }
+}
+
+int ensure_f64_buffer(float2*& buf, int64_t& have, int64_t need)
+{
+    if (have >= need) return CT_OK;
+    cudaFree(buf);
+    buf = nullptr;
+    have = 0;
+    const cudaError_t e = cudaMalloc((void**)&buf, (size_t)need * sizeof(float2));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(double-float FP64-product buffer)", __FILE__, __LINE__);
+    have = need;
+    return CT_OK;
+}
+
+// Double-float product on internal layouts: which = 0: out = s^rpow .* (A in)
+// ([npad][B] -> [rows][B]); which = 1: out = A^T in ([rows][B] -> [npad][B];
+// with FP16 storage Q^T in).
+int product_df_internal(const ct_matrix* M, int which, const float2* in, float2* out, int32_t B, int rpow,
+                        cudaStream_t st)
+{
+    const ValKind vk = (M->flags & CT_VAL_FP16_ROWSCALE) ? ValKind::F16 : ValKind::F32;
+    if (B > 1) return batched_product_df(M, which, in, out, B, which == 0 ? rpow : 0, st);
+    if (which == 0) return launch_forward_df(M, vk, in, out, vk == ValKind::F16 ? rpow : 0, nullptr, nullptr, st);
+    return launch_adjoint_df(M, vk, in, out, 1.0, st);
+}
+
+int product_f64_df(const ct_matrix* M, int which, const double* in, double* out, int32_t B, cudaStream_t st)
+{
+    Workspace& w = const_cast<ct_matrix*>(M)->ws;
+    const bool f16 = (M->flags & CT_VAL_FP16_ROWSCALE) != 0;
+    CT_CHECK(ensure_f64_buffer(w.f64_a, w.f64_a_len, std::max<int64_t>(M->npad, M->rows) * B));
+    CT_CHECK(ensure_f64_buffer(w.f64_b, w.f64_b_len, std::max<int64_t>(M->npad, M->rows) * B));
+    if (which == 0) {
+        f64_image_to_df_kernel<<<grid_for(M, M->npad * B, 256, 8), 256, 0, st>>>(in, w.f64_a, M->g.n, M->tn, B);
+        CT_CUDA(cudaGetLastError());
+        CT_CHECK(product_df_internal(M, 0, w.f64_a, w.f64_b, B, 1, st));
+        df_rows_to_f64_kernel<<<grid_for(M, M->rows * B, 256, 8), 256, 0, st>>>(w.f64_b, out, M->rows * B);
+    } else {
+        f64_rows_to_df_kernel<<<grid_for(M, M->rows * B, 256, 8), 256, 0, st>>>(in, f16 ? M->row_scale : nullptr,
+                                                                              w.f64_a, M->rows, B);
+        CT_CUDA(cudaGetLastError());
+        CT_CHECK(product_df_internal(M, 1, w.f64_a, w.f64_b, B, 0, st));
+        df_image_to_f64_kernel<<<grid_for(M, (int64_t)M->g.n * M->g.n * B, 256, 8), 256, 0, st>>>(
+            w.f64_b, out, M->g.n, M->tn, B, nullptr, 0.0, 0.0);
+    }
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+// ct_normal_f64 in double-float: x split once, A x with s^2 (FP16 storage:
+// A^T A = Q^T diag(s^2) Q), A^T of that, then the epilogue back in FP64.
+int normal_f64_df(const ct_matrix* M, double alpha, double lam, const double* x, double* out, int32_t B,
+                  cudaStream_t st)
+{
+    Workspace& w = const_cast<ct_matrix*>(M)->ws;
+    CT_CHECK(ensure_f64_buffer(w.f64_a, w.f64_a_len, std::max<int64_t>(M->npad, M->rows) * B));
+    CT_CHECK(ensure_f64_buffer(w.f64_b, w.f64_b_len, std::max<int64_t>(M->npad, M->rows) * B));
+    CT_CHECK(ensure_f64_buffer(w.f64_c, w.f64_c_len, M->npad * (int64_t)B));
+    f64_image_to_df_kernel<<<grid_for(M, M->npad * B, 256, 8), 256, 0, st>>>(x, w.f64_a, M->g.n, M->tn, B);
+    CT_CUDA(cudaGetLastError());
+    CT_CHECK(product_df_internal(M, 0, w.f64_a, w.f64_b, B, 2, st));
+    CT_CHECK(product_df_internal(M, 1, w.f64_b, w.f64_c, B, 0, st));
+    df_image_to_f64_kernel<<<grid_for(M, (int64_t)M->g.n * M->g.n * B, 256, 8), 256, 0, st>>>(
+        w.f64_c, out, M->g.n, M->tn, B, x, alpha, lam);
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
 }  // namespace
 
 int normal_f64(const ct_matrix* M, double alpha, double lam, const double* x, double* out, int32_t B,
                cudaStream_t st)
 {
+    if (!(M->flags & CT_F64_FP64_PIPE)) return normal_f64_df(M, alpha, lam, x, out, B, st);
     ct_matrix* Mm = const_cast<ct_matrix*>(M);
     Workspace& w = Mm->ws;
     const int64_t need = M->rows * (int64_t)B;
@@ -257,11 +397,13 @@ int launch_adjoint(const ct_matrix* M, ValKind vk, const float* y, float* x, int
 
 int launch_forward_f64(const ct_matrix* M, ValKind, const double* x, double* y, int32_t batch, cudaStream_t st)
 {
+    if (!(M->flags & CT_F64_FP64_PIPE)) return product_f64_df(M, 0, x, y, batch, st);
     return product_f64(M, 0, x, y, batch, st);
 }
 
 int launch_adjoint_f64(const ct_matrix* M, ValKind, const double* y, double* x, int32_t batch, cudaStream_t st)
 {
+    if (!(M->flags & CT_F64_FP64_PIPE)) return product_f64_df(M, 1, y, x, batch, st);
     return product_f64(M, 1, y, x, batch, st);
 }
 

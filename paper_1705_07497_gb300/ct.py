@@ -31,6 +31,7 @@ CT_ERR_UNSUPPORTED = -7
 CT_VAL_FP32 = 0
 CT_VAL_FP16_ROWSCALE = 1
 CT_KEEP_FP32_COPY = 4
+CT_F64_FP64_PIPE = 8
 
 CT_FOURIER_FUSED = 0
 CT_FOURIER_GRIDDING = 1
