@@ -259,12 +259,15 @@ int ct_split_bregman_ragged(int32_t count, const ct_matrix_t *A, const float *co
 
 /* Launch tuning of the batched products (no counterpart in the paper).  The
  * batched sparse products (batch >= 2) come in variants that differ only in
- * how many staged matrix entries each lane keeps in flight (4 or 8); they
- * compute bit-identical results.  By default the first batched solve with a
- * given batch size on a handle times the variants on its own data (a few
- * launches of the forward product, synchronising the stream once, never
- * inside a stream capture) and keeps the fastest.  ct_set_spmm_unroll pins
- * the choice for a batch size (4 or 8; 0 returns it to automatic);
+ * how many staged matrix entries each lane keeps in flight (4, 8, or 16 for
+ * batches below 64 slices, where a lane takes one slice; the fused solver
+ * kernels take 8 for 16); they compute bit-identical results.  By default
+ * the first batched solve, or the first batched ct_forward_f64 /
+ * ct_normal_f64, with a given batch size on a handle times the variants on
+ * its own data (a few launches of the forward product, synchronising the
+ * stream once, never inside a stream capture) and keeps the fastest.
+ * ct_set_spmm_unroll pins the choice for a batch size (4, 8 or 16; 0 returns
+ * it to automatic);
  * ct_get_spmm_unroll reports it (0 = not chosen yet).
  * Errors: CT_ERR_ARG (batch < 2, other unroll values, NULL output). */
 int ct_set_spmm_unroll(ct_matrix_t A, int32_t batch, int32_t unroll);
@@ -297,7 +300,7 @@ int ct_set_wait_limit(int64_t polls, int32_t hold_first);
  *   op_pixels    one slice, the same kernel: pixel rows per lane, 1, or 2
  *                (four warps per image tile, seven CTAs per SM; single-chunk
  *                bands only, with op_ctas 0 or 7)
- *   spmm_unroll  batches of 2 or more: staged entries in flight, 4 or 8
+ *   spmm_unroll  batches of 2 or more: staged entries in flight, 4, 8 or 16
  * By default the first solve on a handle (batch 1: ct_cg_solve,
  * ct_split_bregman, ct_chambolle_pock, and the single-slice groups of
  * ct_split_bregman_ragged; batch B: the batched solves) times the candidates

@@ -766,6 +766,34 @@ int spmm_unroll(const ct_matrix* M, int B)
     return it != M->spmm_unroll.end() && it->second > 0 ? it->second : 8;
 }
 
+// Resident blocks per SM of a kernel at 256 threads (queried once per kernel).
+template <auto Kernel>
+int resident_blocks()
+{
+    static int occ = 0;
+    if (occ == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, Kernel, 256, 0) != cudaSuccess || v < 1) {
+            cudaGetLastError();
+            v = 8;
+        }
+        occ = v;
+    }
+    return occ;
+}
+
+// Blocks of a product launch: the row blocks of g (capped at what the SMs
+// hold at once, so that a small batch runs in one wave and the blocks loop
+// over the rows) times the slice chunks.  Every row is summed by the same
+// lanes in the same order whatever the count, so results do not depend on it.
+template <auto Kernel>
+int spmm_blocks(const ct_matrix* M, const Grid2& g)
+{
+    const int64_t cap = (int64_t)(M->sm_count > 0 ? M->sm_count : 148) * resident_blocks<Kernel>();
+    const int64_t rb = std::max<int64_t>(1, std::min<int64_t>(g.rb, cap));
+    return (int)(rb * g.chunks);
+}
+
 // which = 0: rows of A (rays); which = 1: rows of A^T (internal pixels).
 template <typename XT, typename YT>
 int launch_spmm(const ct_matrix* M, int which, ValKind vk, const XT* x, YT* y, int B, BProd a, cudaStream_t st,
@@ -782,17 +810,20 @@ int launch_spmm(const ct_matrix* M, int which, ValKind vk, const XT* x, YT* y, i
     // keep them L2-resident (the A^T products gather within a tile's band)
     const bool half = spl == 2 && which == 0;
     const Grid2 g = make_grid(M, C.rows, B, spl, half);
-    const int blocks = g.rb * g.chunks;
-    const bool u4 = (unroll ? unroll : spmm_unroll(M, B)) == 4;
-#define CT_DF(VT, VAL, U, SPL, H) \
-    spmm_df_kernel<VT, XT, YT, U, SPL, H><<<blocks, 256, 0, st>>>(m, cm, VAL, x, y, B, a, om)
+    const int uu = unroll ? unroll : spmm_unroll(M, B);
+    const bool u4 = uu == 4, u16 = uu == 16;  // 16: one slice per lane only
+#define CT_DF(VT, VAL, U, SPL, H)                                                                   \
+    spmm_df_kernel<VT, XT, YT, U, SPL, H><<<spmm_blocks<spmm_df_kernel<VT, XT, YT, U, SPL, H>>(M, g), 256, 0, \
+                                            st>>>(m, cm, VAL, x, y, B, a, om)
     if (vk == ValKind::F16) {
         if (half) {
             if (u4) CT_DF(__half, C.qval, 4, 2, true); else CT_DF(__half, C.qval, 8, 2, true);
         } else if (spl == 2) {
             if (u4) CT_DF(__half, C.qval, 4, 2, false); else CT_DF(__half, C.qval, 8, 2, false);
         } else {
-            if (u4) CT_DF(__half, C.qval, 4, 1, false); else CT_DF(__half, C.qval, 8, 1, false);
+            if (u4) CT_DF(__half, C.qval, 4, 1, false);
+            else if (u16) CT_DF(__half, C.qval, 16, 1, false);
+            else CT_DF(__half, C.qval, 8, 1, false);
         }
     } else {
         if (half) {
@@ -800,7 +831,9 @@ int launch_spmm(const ct_matrix* M, int which, ValKind vk, const XT* x, YT* y, i
         } else if (spl == 2) {
             if (u4) CT_DF(float, C.val, 4, 2, false); else CT_DF(float, C.val, 8, 2, false);
         } else {
-            if (u4) CT_DF(float, C.val, 4, 1, false); else CT_DF(float, C.val, 8, 1, false);
+            if (u4) CT_DF(float, C.val, 4, 1, false);
+            else if (u16) CT_DF(float, C.val, 16, 1, false);
+            else CT_DF(float, C.val, 8, 1, false);
         }
     }
 #undef CT_DF
@@ -827,10 +860,12 @@ int tune_spmm(ct_matrix* M, ValKind vk, int B, const float2* x, float2* y, cudaS
         return cuda_fail(ec, "cudaEventCreate", __FILE__, __LINE__);
     }
     BProd a{vk == ValKind::F16 ? M->row_scale : nullptr, 1, make_float2(1.0f, 0.0f), nullptr, nullptr};
-    const int cand[2] = {4, 8};
+    // 16 staged entries in flight only where a lane takes one slice
+    const int cand[3] = {4, 8, 16};
+    const int ncand = slices_per_lane(B) == 1 ? 3 : 2;
     float best_ms = 0.0f;
     int best = 8, rc = CT_OK;
-    for (int c = 0; c < 2 && rc == CT_OK; ++c) {
+    for (int c = 0; c < ncand && rc == CT_OK; ++c) {
         rc = launch_spmm(M, 0, vk, x, y, B, a, st, false, cand[c]);  // warm-up
         cudaError_t e = cudaEventRecord(e0, st);
         for (int r = 0; r < 3 && rc == CT_OK && e == cudaSuccess; ++r)
@@ -990,6 +1025,9 @@ int batched_product_df(const ct_matrix* M, int which, const float2* in, float2* 
                        cudaStream_t st)
 {
     const ValKind vk = (M->flags & CT_VAL_FP16_ROWSCALE) ? ValKind::F16 : ValKind::F32;
+    // the first forward product of this batch size on the handle picks the
+    // staged-entry unroll (timed on these buffers; out is rewritten below)
+    if (which == 0) CT_CHECK(tune_spmm(const_cast<ct_matrix*>(M), vk, B, in, out, st));
     BProd a{(vk == ValKind::F16 && which == 0 && rpow > 0) ? M->row_scale : nullptr, rpow, make_float2(1.0f, 0.0f),
             nullptr, nullptr};
     return launch_spmm(M, which, vk, in, out, B, a, st);

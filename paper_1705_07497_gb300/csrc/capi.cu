@@ -436,7 +436,8 @@ int ct_set_spmm_unroll(ct_matrix_t A, int32_t batch, int32_t unroll)
     CT_CHECK(check_handle(A));
     CT_CHECK(no_fourier(A, "ct_set_spmm_unroll"));
     if (batch < 2) return fail(CT_ERR_ARG, "batch must be >= 2 (batch 1 does not use the batched products)");
-    if (unroll != 0 && unroll != 4 && unroll != 8) return fail(CT_ERR_ARG, "unroll must be 0, 4 or 8");
+    if (unroll != 0 && unroll != 4 && unroll != 8 && unroll != 16)
+        return fail(CT_ERR_ARG, "unroll must be 0, 4, 8 or 16");
     if (unroll == 0)
         A->spmm_unroll.erase(batch);
     else

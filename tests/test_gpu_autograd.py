@@ -83,6 +83,29 @@ def test_f64_products_match_oracle(dev, flags):
         assert np.linalg.norm(y.cpu().numpy() - want) <= 1e-12 * np.linalg.norm(want)
 
 
+def test_batched_f64_product_variants_are_bit_identical(dev):
+    """Double-float FP64-vector products over 3 slices: every staged-entry
+    unroll gives the same bits, and the first product tunes it."""
+    geom = (64, 90, 3, 91)
+    x = torch.tensor(inputs.random_vector(4096 * 3, 76).reshape(4096, 3), dtype=torch.float64, device=dev)
+    ys = []
+    for unroll in (4, 8, 16, 0):
+        M = ct.Matrix(*geom)
+        if unroll:
+            M.set_spmm_unroll(3, unroll)
+        y = torch.empty((M.rows, 3), dtype=torch.float64, device=dev)
+        M.forward(x, y)
+        xa = torch.empty_like(x)
+        M.adjoint(y, xa)
+        torch.cuda.synchronize()
+        if not unroll:
+            assert M.spmm_unroll(3) in (4, 8, 16)
+        ys.append((y.cpu(), xa.cpu()))
+        M.close()
+    for y, xa in ys[1:]:
+        assert torch.equal(y, ys[0][0]) and torch.equal(xa, ys[0][1])
+
+
 def _sb_oracle(A, f, n, outer, inner):
     return tv.split_bregman(A, f, (n, n), 1.0, 1.0, outer, inner)["u"].ravel()
 

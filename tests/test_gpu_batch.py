@@ -272,14 +272,14 @@ def test_batched_512_fp16_256_slices_first_update(dev):
 
 
 def test_spmm_unroll_variants_are_bit_identical_and_tuned(dev):
-    """The batched products' launch variants (4 or 8 staged entries in flight)
-    give the same bits; without a pinned choice the first batched solve times
-    them and keeps one."""
+    """The batched products' launch variants (4, 8 or 16 staged entries in
+    flight) give the same bits; without a pinned choice the first batched
+    solve times them and keeps one."""
     ref = oracle_A(*GEOM64)
     truths, F = _data(GEOM64, [11, 12, 13, 14, 15], ref)
     Fg = t32(F, dev)
     outs = []
-    for unroll in (4, 8):
+    for unroll in (4, 8, 16):
         M = ct.Matrix(*GEOM64)
         M.set_spmm_unroll(5, unroll)
         assert M.spmm_unroll(5) == unroll
@@ -287,12 +287,12 @@ def test_spmm_unroll_variants_are_bit_identical_and_tuned(dev):
         M.split_bregman(Fg, u, 1.0, 0.1, 6, 10)
         outs.append(u.cpu())
         M.close()
-    assert torch.equal(outs[0], outs[1])
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
     M = ct.Matrix(*GEOM64)
     assert M.spmm_unroll(5) == 0
     u = torch.zeros((M.cols, 5), device=dev)
     M.split_bregman(Fg, u, 1.0, 0.1, 6, 10)
-    assert M.spmm_unroll(5) in (4, 8)
+    assert M.spmm_unroll(5) in (4, 8, 16)
     assert torch.equal(u.cpu(), outs[0])
     M.close()
 
