@@ -167,6 +167,24 @@ def test_fp16_products_match_dequantised_oracle(dev, batch):
     assert rel(xg.cpu().numpy(), A16.T @ y) <= 1e-5
 
 
+@pytest.mark.parametrize("flags", [FP16, FP16 | ct.CT_F64_FP64_PIPE], ids=["double-float", "fp64-pipe"])
+@pytest.mark.parametrize("batch", [1, 5])
+def test_fp16_f64_products_match_dequantised_oracle(dev, batch, flags):
+    """FP64-vector products of an FP16 handle (A = diag(s) Q: the forward
+    scales its rows by s, the adjoint applies Q^T to s .* y) against the
+    dequantised oracle, on both product paths."""
+    A16, _, _ = oracle_A16(*GEOM64)
+    M = gpu_A(GEOM64, flags)
+    x = inputs.random_vector(M.cols * batch, 65).reshape(M.cols, batch)
+    y = inputs.random_vector(M.rows * batch, 66).reshape(M.rows, batch)
+    yg = torch.empty((M.rows, batch), dtype=torch.float64, device=dev)
+    xg = torch.empty((M.cols, batch), dtype=torch.float64, device=dev)
+    M.forward(torch.tensor(x, device=dev), yg)
+    M.adjoint(torch.tensor(y, device=dev), xg)
+    assert rel(yg.cpu().numpy(), A16 @ x) <= 1e-12
+    assert rel(xg.cpu().numpy(), A16.T @ y) <= 1e-12
+
+
 @pytest.mark.parametrize("batch", [1, 3])
 def test_fp16_split_bregman(dev, batch):
     """Kernel error against the dequantised oracle, storage error against FP64."""
